@@ -1,0 +1,108 @@
+"""Pins of the oracle's whole time step against what the physics of planar
+Couette flow fixes: equilibrium fixed point, exact mass conservation with
+diffuse walls (Eqs. diffuse, diffuse_nw), the mirror symmetry of Sec. II, the
+free-molecular closed form (delta -> 0) and the Navier-Stokes limit
+(P_xy = -mu du_y/dx with mu from Eq. tau, delta large)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+
+SQ2 = math.sqrt(2.0)
+
+
+@pytest.mark.parametrize("Q,A,p0", [(4, 0.0, 1.0), (5, math.sqrt(0.9), 1.0), (6, 0.5, 1.2)])
+def test_rest_maxwellian_is_a_fixed_point(Q, A, p0):
+    o = Oracle(dict(Nx=16, Qx=Q, Qy=Q, stretch_A=A, p0=p0, delta=2.0))
+    f0 = o.f.copy()
+    res = o.run(40)
+    assert np.max(res) < 1e-15
+    assert np.max(np.abs(o.f - f0)) < 1e-13
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.7, 20.0])
+@pytest.mark.parametrize("A", [0.0, math.sqrt(0.9)])
+def test_mass_is_conserved(delta, A):
+    """Telescoping fluxes, zero wall mass flux and a collision that keeps n
+    (N >= 3) conserve sum_s J_s deta n_s to round-off."""
+    o = Oracle(dict(Nx=24, Qx=4, Qy=5, stretch_A=A, delta=delta, T_left=0.6, T_right=1.4,
+                    u_left=-0.2, u_right=0.3, omega=0.7))
+    m0 = o.total_mass()
+    o.run(150)
+    assert abs(o.total_mass() - m0) < 2e-14
+
+
+def test_wall_density_balances_the_mass_flux():
+    """With an outgoing flux the wall density n_w of Eq. diffuse_nw is such
+    that the rate of change of mass vanishes: d/dt sum J deta n = 0."""
+    o = Oracle(dict(Nx=16, Qx=5, Qy=4, delta=1.0, T_left=0.8, T_right=1.3, u_left=0.1, u_right=-0.2))
+    o.run(30)
+    L, nw = o.rhs()
+    dndt = np.sum(o.w[:, None] * L[0], axis=0)
+    assert abs(np.sum(o.J * o.deta * dndt)) < 1e-13
+    assert np.all(nw > 0)
+
+
+def test_mirror_symmetry():
+    """phi(-x, -p_x, -p_y) = phi(x, p_x, p_y) for walls moving at -u_w, +u_w
+    with equal temperatures (Sec. II)."""
+    Qx, Qy, Nx = 5, 6, 20
+    o = Oracle(dict(Nx=Nx, Qx=Qx, Qy=Qy, stretch_A=0.8, delta=1.5, u_left=-0.25, u_right=0.25))
+    o.run(200)
+    f = o.f.reshape(2, 2, Qx, Qy, Nx)
+    mirrored = f[:, ::-1, :, ::-1, ::-1]          # -p_x swaps halves, -p_y reverses j, -x reverses s
+    assert np.max(np.abs(f - mirrored)) < 1e-12 * np.max(np.abs(f))
+
+
+@pytest.mark.parametrize("TL,TR,uL,uR", [(1.0, 1.0, -0.1, 0.1), (0.8, 1.2, -0.1, 0.15), (0.5, 2.0, 0.05, 0.3)])
+def test_free_molecular_closed_form(TL, TR, uL, uR):
+    """delta = 0: each half of the velocity set carries its wall's Maxwellian,
+    n_L sqrt(T_L) = n_R sqrt(T_R) (zero mass flux) and (n_L + n_R)/2 = 1, so
+    P_xy = -(u_R - u_L) 2 sqrt(T_L T_R) / ((sqrt T_L + sqrt T_R) sqrt(2 pi))."""
+    o = Oracle(dict(Nx=12, Qx=4, Qy=4, delta=0.0, T_left=TL, T_right=TR, u_left=uL, u_right=uR))
+    k, r = o.run_to_steady(1e-14, 400000)
+    assert r < 1e-14
+    m = o.moments()
+    sL, sR = math.sqrt(TL), math.sqrt(TR)
+    pxy = -(uR - uL) * 2 * sL * sR / ((sL + sR) * math.sqrt(2 * math.pi))
+    np.testing.assert_allclose(m[0], 1.0, atol=1e-10)
+    np.testing.assert_allclose(m[7], pxy, atol=1e-10)
+    _, nw = o.rhs()
+    np.testing.assert_allclose(nw, [2 * sR / (sL + sR), 2 * sL / (sL + sR)], atol=1e-10)
+    # mean wall-parallel velocity (n_L u_L + n_R u_R)/2
+    uy = (uL * 2 * sR / (sL + sR) + uR * 2 * sL / (sL + sR)) / 2
+    np.testing.assert_allclose(m[2], uy, atol=1e-10)
+
+
+def test_shear_number_free_molecular():
+    """Eq. Pi with equal walls at u_w = sqrt(2) v_ref: Pi = -T_xy/(2 P_ref) -> 1/sqrt(pi) as delta -> 0."""
+    uw = SQ2
+    o = Oracle(dict(Nx=8, Qx=4, Qy=7, delta=0.0, u_left=-uw, u_right=uw))
+    o.run_to_steady(1e-14, 400000)
+    pi_num = -o.moments()[7] / (2.0 * 1.0)
+    np.testing.assert_allclose(pi_num, 1 / math.sqrt(math.pi), rtol=1e-10)
+
+
+def test_navier_stokes_limit():
+    """delta = 100: the bulk shear stress follows Newton's law with the
+    viscosity of Eq. tau, mu = T^omega / (delta sqrt 2) (L = v_ref = 1)."""
+    uw, delta, omega = 0.05, 100.0, 0.5
+    o = Oracle(dict(Nx=32, Qx=5, Qy=5, delta=delta, u_left=-uw, u_right=uw, omega=omega))
+    f = np.zeros((2, o.V, o.Nx))
+    for s in range(o.Nx):   # start near the answer: local Maxwellian with a linear profile
+        gx, gy = o.equilibrium_factors(0.0, 1.8 * uw * o.x[s], 1.0)
+        g = np.outer(gx, gy).ravel()
+        f[0, :, s] = g
+        f[1, :, s] = g
+    o.set_state(f)
+    k, r = o.run_to_steady(1e-11, 60000)
+    assert r < 1e-11
+    m = o.moments()
+    dudx = np.gradient(m[2], o.x)
+    mu = m[3] ** omega / (delta * SQ2)
+    bulk = slice(8, 24)
+    np.testing.assert_allclose(m[7][bulk], (-mu * dudx)[bulk], rtol=2e-4)
+    # and Pi -> 1/delta (Eq. Pi with u_w -> the slip-free velocity jump) to O(1/delta)
+    assert abs(-m[7][16] / (2 * uw) * delta * SQ2 - 1) < 0.05
