@@ -1,0 +1,272 @@
+#!/usr/bin/env python
+"""Benchmark: cell-velocity updates per second of the half-range LB Couette
+time step on the single-large-solve workload (Nx = 2048 stretched nodes,
+2Qx x Qy = 32 x 20 velocities, delta in {0.1, 1, 10, 100}: four solves per
+step, FP32 state with FP64 moment sums), one JSON line on stdout.
+
+A step is one TVD RK-3 step (three fused stage launches) of all four solves.
+Timing: W untimed warm-up steps, then K steps timed with CUDA events on the
+launching stream, an L2 flush (a 256 MiB write, not timed) between steps,
+max over ranks. N > 1 runs N independent replicas (one batch per rank).
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-velocity updates/s"
+FALLBACK_HBM_GBS = 6800.0
+BYTES_PER_UPDATE_FP32 = 64   # 16 state values per cell-velocity step
+BYTES_PER_UPDATE_FP64 = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(precision="fp32"):
+    return {"workload": "single large solve: Nx=2048 tanh-stretched (spacing ratio 10), "
+                        "HHLB(15;16)xHLB(19;20) = 640 velocities, delta in {0.1,1,10,100}, "
+                        "u_w=+-0.1*sqrt(2kT/m), omega=0.66, Pr=2/3",
+            "solves_per_step": 4, "Nx": 2048, "velocities": 640, "state": precision,
+            "l2": "flushed between timed steps (256 MiB write)", "data": "synthetic"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if "Active" in val and "Not" not in val:
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if k in d and isinstance(d[k], (int, float)):
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def cpu_baseline(seconds_target=12.0):
+    """The FP64 oracle as it stands, one host core, on a bounded sample: whole
+    RK-3 steps of the delta = 1 solve of the same workload."""
+    from oracle.oracle import Oracle
+    from paper_1810_07803_gb300 import workloads
+    o = Oracle(workloads.c2(1.0, precision="fp64"))
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds_target:
+        o.run(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": o.V * o.Nx * n / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{n} RK-3 steps of the delta=1 solve (Nx=2048, 640 velocities), FP64, 1 thread"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from oracle.oracle import Oracle
+    from paper_1810_07803_gb300 import workloads
+    solves = [Oracle(workloads.c2(d, precision="fp64")) for d in workloads.C2_DELTAS]
+    for k in range(args.warmup):
+        solves[k % 4].run(1)
+    times = []
+    for k in range(args.steps):
+        o = solves[k % 4]
+        t0 = time.perf_counter()
+        o.run(1)
+        times.append(time.perf_counter() - t0)
+    per_step = sum(times) / len(times)
+    value = solves[0].V * solves[0].Nx / per_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(workload_config("fp64"), solves_per_step=1,
+                                                 sample="each step: one RK-3 step of one of the four solves"),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} single-solve RK-3 steps, rotating over the four deltas"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(solvers, steps, warmup, flush):
+    import torch
+    for _ in range(warmup):
+        for s in solvers:
+            s.step(1)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record()
+        for s in solvers:
+            s.step(1)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps   # ms per step
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1810_07803_gb300 import build, lbc, workloads
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1810_07803_gb300", "liblbc.so")):
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    solvers = [lbc.Solver(workloads.c2(d, precision="fp32")) for d in workloads.C2_DELTAS]
+    V, Nx = solvers[0].V, solvers[0].Nx
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = time_steps(solvers, args.steps, args.warmup, flush)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = len(solvers) * V * Nx
+    value = units * world / (ms / 1e3)
+
+    # end to end through the public API: host state in, host moments out, every step
+    import numpy as np
+    host_states = [s.get_state() for s in solvers]
+    e2e_steps = min(args.steps, 10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for s, hs in zip(solvers, host_states):
+            s.set_state(hs)
+            s.step(1)
+            s.moments()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = sum(hs.nbytes for hs in host_states)
+    d2h = len(solvers) * lbc.NMOM * Nx * 8
+
+    fp64 = None
+    if not args.no_fp64:
+        s64 = [lbc.Solver(workloads.c2(d, precision="fp64")) for d in workloads.C2_DELTAS]
+        ms64 = time_steps(s64, max(3, args.steps // 10), 2, flush)
+        fp64 = {"value": len(s64) * V * Nx * world / (ms64 / 1e3), "ms_per_step": ms64,
+                "note": "same workload, FP64 state and arithmetic, one solve per launch"}
+        for s in s64:
+            s.close()
+
+    peak, peak_kind = measured_hbm_peak()
+    launches_per_step = 3 * len(solvers)
+    achieved = BYTES_PER_UPDATE_FP32 * units / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config("fp32"),
+        "e2e": {"value": units * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "path": "per step and solve: lbc_set_state(host f64) + lbc_step(1) + lbc_moments(host)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "stage_kernel<float>", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": BYTES_PER_UPDATE_FP32 * V * Nx / 3},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if fp64:
+        line["fp64_plain"] = fp64
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    for s in solvers:
+        s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

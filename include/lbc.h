@@ -1,0 +1,163 @@
+/*
+ * lbc.h -- C ABI of the GB300 half-range lattice Boltzmann Couette solver.
+ *
+ * The solver integrates the reduced Shakhov-model Boltzmann equation for planar
+ * Couette flow (Ambrus, Sharipov & Sofonea, arXiv:1810.07803, Sec. II,
+ * Eq. boltz_red) with the mixed-quadrature lattice Boltzmann model
+ * HHLB(Nx;Qx) x HLB(Ny;Qy) of Sec. III: half-range Gauss-Hermite abscissas on
+ * p_x (each half-space separately), full-range Gauss-Hermite on p_y, the
+ * equilibrium replaced by its Hermite truncations (Eqs. gx, gy), diffuse walls
+ * with the zero-mass-flux density (Eqs. diffuse, diffuse_nw), relaxation time
+ * from the viscosity law (Eqs. mu, tau), WENO-5 advection on the
+ * tanh-stretched grid (Eq. stretch) and TVD RK-3 in time.
+ *
+ * Units: m = k_B = 1; lengths in L (walls at x = -1/2, +1/2); temperatures in
+ * T_ref; velocities and momenta in v_ref = sqrt(k_B T_ref / m); times in
+ * L / v_ref; densities in n_ref (the initial, and mean, density).
+ *
+ * Velocity set: index v = a * Qy + j with a in [0, 2Qx), j in [0, Qy).
+ * a < Qx: p_x = +p0 z_a; a >= Qx: p_x = -p0 z_{a-Qx} (the paper's
+ * p_{x,i+Qx} = -p_{x,i}); p_y = p0 y_j; quadrature weight w_a w_j, where z, w
+ * is the half-range rule of order Qx and y, w the full-range rule of order Qy.
+ *
+ * State: the reduced distributions phi and chi (Sec. II) divided by the
+ * quadrature weights, ft = phi_v / (w_a w_j), so that an equilibrium is O(1)
+ * at every velocity. Host-side state arrays are float64, row-major
+ * [2][V][Nx] (field 0 = phi, field 1 = chi; V = 2 Qx Qy).
+ *
+ * Errors: every call returns an lbc_status; nothing throws across the ABI.
+ * lbc_last_error() gives a thread-local message for the last failure. A failed
+ * call leaves the solver unchanged, except LBC_ENONFINITE (the state held a
+ * NaN or Inf), after which the solver refuses further steps.
+ *
+ * Threads and streams: a solver may be used from one host thread at a time.
+ * All device work is enqueued on the CUDA stream given at creation; calls
+ * that return host data synchronise that stream.
+ *
+ * Ownership: the solver owns all of its device memory (allocated with
+ * cudaMallocAsync on its stream at lbc_create, freed by lbc_destroy). The
+ * caller owns every host array passed in; lbc_params is copied at creation.
+ */
+#ifndef LBC_H
+#define LBC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbc_solver lbc_solver;
+
+typedef enum {
+    LBC_OK = 0,
+    LBC_EINVAL = 1,      /* invalid argument (message says which) */
+    LBC_ENOMEM = 2,      /* device allocation failed */
+    LBC_ECUDA = 3,       /* a CUDA runtime call failed */
+    LBC_ENOTCONV = 4,    /* lbc_run_to_steady hit max_steps */
+    LBC_ENONFINITE = 5,  /* NaN/Inf in the state; the solver is poisoned */
+    LBC_ETIMEOUT = 6     /* a bounded device wait gave up */
+} lbc_status;
+
+typedef enum { LBC_MU_POWER = 0, LBC_MU_TABLE = 1 } lbc_mu_law;
+typedef enum { LBC_FP64 = 0, LBC_FP32_STATE = 1 } lbc_precision;
+
+#define LBC_NMOM 10
+/* Rows of lbc_moments' output: */
+enum { LBC_M_N = 0, LBC_M_UX, LBC_M_UY, LBC_M_T, LBC_M_PXX, LBC_M_PYY, LBC_M_PZZ,
+       LBC_M_PXY, LBC_M_QX, LBC_M_QY };
+
+typedef struct {
+    double delta;            /* rarefaction parameter (Eq. delta); 0 = collisionless */
+    double u_left, u_right;  /* wall velocities along y (v_ref units) */
+    double T_left, T_right;  /* wall temperatures (T_ref units), > 0 */
+    double Pr;               /* Prandtl number of the Shakhov model (Sec. II) */
+    lbc_mu_law mu_law;       /* LBC_MU_POWER: mu = T^omega (Eq. mu) */
+    double omega;            /* viscosity index */
+    const double *tab_T, *tab_mu, *tab_Pr;  /* LBC_MU_TABLE (Eqs. mun, interp); tab_n entries */
+    int tab_n;
+    int Nx;                  /* grid nodes across the full channel, >= 8 */
+    double stretch_A;        /* Eq. stretch parameter A in [0, 1); 0 = uniform grid */
+    int Qx;                  /* half-range quadrature order per half (2 Qx values of p_x) */
+    int Qy;                  /* full-range quadrature order */
+    int Nexp_x, Nexp_y;      /* expansion orders N < Q of Eqs. gx, gy; 0 = Q - 1 */
+    double p0;               /* momentum scale of both quadratures; 0 = 1 */
+    double cfl;              /* CFL number of the time step; 0 = 0.5 */
+    double dt;               /* explicit time step; 0 = automatic (see lbc_create) */
+    lbc_precision precision; /* LBC_FP64, or float32 state with float64 moment sums */
+} lbc_params;
+
+/*
+ * Creates a solver for one Couette problem and sets the rest Maxwellian
+ * n = 1, u = 0, T = 1 at every node.
+ *   params: copied. Requires 1 <= Qx <= 64, 1 <= Qy <= 64, 0 <= N < Q (and
+ *           N >= 2 on both axes, so the equilibrium has a temperature),
+ *           Nx >= 8, delta >= 0, T_w > 0, 0 <= stretch_A < 1, p0 > 0.
+ *   Automatic time step: dt = min(cfl * min_s(J_s deta) / max|p_x|, tau_min / 2),
+ *   with tau_min the smallest relaxation time (Eq. tau) of the initial state
+ *   and of the two walls at n = 1.
+ *   cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ *   out: receives the handle; unchanged on failure.
+ * Errors: LBC_EINVAL, LBC_ENOMEM, LBC_ECUDA.
+ */
+lbc_status lbc_create(const lbc_params *params, void *cuda_stream, lbc_solver **out);
+
+/* Advances nsteps >= 0 RK-3 steps (three fused advect+collide stages each).
+ * Enqueued only; returns before the GPU finishes. */
+lbc_status lbc_step(lbc_solver *s, long nsteps);
+
+/*
+ * Steps until the per-step residual r_n = max_{field,v,s} w_v |ft^{n+1} - ft^n|
+ * falls below `residual` (the paper states no criterion; this is the reading),
+ * or max_steps more steps were taken. The state is left at the first step with
+ * r < residual. steps_done / final_residual (either may be NULL) receive the
+ * number of steps taken by this call and the last step's residual.
+ * Errors: LBC_ENOTCONV (max_steps reached; state advanced by max_steps),
+ * LBC_ENONFINITE, LBC_ECUDA, LBC_EINVAL.
+ */
+lbc_status lbc_run_to_steady(lbc_solver *s, double residual, long max_steps,
+                             long *steps_done, double *final_residual);
+
+/*
+ * Moments of the current state (Sec. II definitions), FP64, per node:
+ *   out: caller-owned [LBC_NMOM][Nx], rows n, u_x, u_y, T, P_xx, P_yy, P_zz,
+ *        P_xy, q_x, q_y (the paper's T_ij is the pressure tensor P_ij).
+ *   x:   caller-owned [Nx] node positions, or NULL.
+ * Synchronises the solver's stream. Errors: LBC_ECUDA, LBC_EINVAL.
+ */
+lbc_status lbc_moments(lbc_solver *s, double *out, double *x);
+
+/* Copies the weight-divided state to / from caller-owned host memory
+ * [2][V][Nx] float64. set_state converts to the solver's precision and
+ * recomputes the stage moments. Synchronise the solver's stream. */
+lbc_status lbc_get_state(lbc_solver *s, double *state);
+lbc_status lbc_set_state(lbc_solver *s, const double *state);
+
+/* Sizes and constants of a created solver (any pointer may be NULL). */
+lbc_status lbc_info(const lbc_solver *s, int *Nx, int *V, double *dt, long *steps_taken);
+
+/* Frees all device memory of the solver (stream-ordered). NULL is a no-op. */
+void lbc_destroy(lbc_solver *s);
+
+/* Thread-local description of the last error ("" if none). */
+const char *lbc_last_error(void);
+
+/*
+ * Host-side building blocks (no GPU needed), for users that prepare inputs:
+ *
+ * lbc_quadrature: the Q-point Gauss rule of Sec. III in FP64.
+ *   half_range != 0: weight exp(-z^2/2)/sqrt(2 pi) on [0, inf) (nodes > 0,
+ *   weights sum to 1/2); else the full-range rule on the real line (weights sum
+ *   to 1). nodes/weights: caller-owned [Q], ascending nodes. 1 <= Q <= 64.
+ *
+ * lbc_equilibrium: the weight-divided discrete equilibrium factors of Eqs. gx
+ *   and gy at (u_x, u_y, T) for the orders and p0 of `params`:
+ *   gx[2 Qx] (indexed like a), gy[Qy]; phi_eq/(w_a w_j) = n gx[a] gy[j],
+ *   chi_eq = T phi_eq. Same algorithm as the device path, in FP64.
+ */
+lbc_status lbc_quadrature(int Q, int half_range, double *nodes, double *weights);
+lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, double T,
+                           double *gx, double *gy);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBC_H */

@@ -1,0 +1,189 @@
+"""Python binding of liblbc.so (include/lbc.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA kernels behind the C ABI; there is no
+Python or CPU fallback. If the library has not been built, `lib()` raises.
+PyTorch, when present, supplies the CUDA stream (torch.cuda.current_stream()).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbc.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "lbc.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENONFINITE, ETIMEOUT = range(7)
+STATUS_NAMES = ["LBC_OK", "LBC_EINVAL", "LBC_ENOMEM", "LBC_ECUDA", "LBC_ENOTCONV", "LBC_ENONFINITE", "LBC_ETIMEOUT"]
+FP64, FP32_STATE = 0, 1
+NMOM = 10
+MOMENT_NAMES = ("n", "u_x", "u_y", "T", "P_xx", "P_yy", "P_zz", "P_xy", "q_x", "q_y")
+
+
+class LbcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("delta", C.c_double), ("u_left", C.c_double), ("u_right", C.c_double),
+        ("T_left", C.c_double), ("T_right", C.c_double), ("Pr", C.c_double),
+        ("mu_law", C.c_int), ("omega", C.c_double),
+        ("tab_T", C.c_void_p), ("tab_mu", C.c_void_p), ("tab_Pr", C.c_void_p), ("tab_n", C.c_int),
+        ("Nx", C.c_int), ("stretch_A", C.c_double), ("Qx", C.c_int), ("Qy", C.c_int),
+        ("Nexp_x", C.c_int), ("Nexp_y", C.c_int), ("p0", C.c_double), ("cfl", C.c_double),
+        ("dt", C.c_double), ("precision", C.c_int),
+    ]
+
+
+DEFAULTS = dict(delta=1.0, u_left=0.0, u_right=0.0, T_left=1.0, T_right=1.0, Pr=2.0 / 3.0,
+                omega=0.5, Nx=64, stretch_A=0.0, Qx=4, Qy=4, Nexp_x=0, Nexp_y=0, p0=1.0,
+                cfl=0.5, dt=0.0, precision="fp64")
+
+
+def make_params(d: dict) -> Params:
+    p = dict(DEFAULTS)
+    p.update(d)
+    prec = p["precision"]
+    prec = {"fp64": FP64, "fp32": FP32_STATE}.get(prec, prec)
+    return Params(delta=p["delta"], u_left=p["u_left"], u_right=p["u_right"], T_left=p["T_left"],
+                  T_right=p["T_right"], Pr=p["Pr"], mu_law=0, omega=p["omega"], tab_T=None, tab_mu=None,
+                  tab_Pr=None, tab_n=0, Nx=int(p["Nx"]), stretch_A=p["stretch_A"], Qx=int(p["Qx"]),
+                  Qy=int(p["Qy"]), Nexp_x=int(p["Nexp_x"]), Nexp_y=int(p["Nexp_y"]), p0=p["p0"],
+                  cfl=p["cfl"], dt=p["dt"], precision=int(prec))
+
+
+_lib = None
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/lbc.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(lbc_\w+)\s*\(", text, re.M)))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1810_07803_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        dp = C.POINTER(C.c_double)
+        vp = C.c_void_p
+        L.lbc_create.argtypes = [C.POINTER(Params), vp, C.POINTER(vp)]
+        L.lbc_step.argtypes = [vp, C.c_long]
+        L.lbc_run_to_steady.argtypes = [vp, C.c_double, C.c_long, C.POINTER(C.c_long), dp]
+        L.lbc_moments.argtypes = [vp, dp, dp]
+        L.lbc_get_state.argtypes = [vp, dp]
+        L.lbc_set_state.argtypes = [vp, dp]
+        L.lbc_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp, C.POINTER(C.c_long)]
+        L.lbc_destroy.argtypes = [vp]
+        L.lbc_destroy.restype = None
+        L.lbc_last_error.restype = C.c_char_p
+        L.lbc_quadrature.argtypes = [C.c_int, C.c_int, dp, dp]
+        L.lbc_equilibrium.argtypes = [C.POINTER(Params), C.c_double, C.c_double, C.c_double, dp, dp]
+        for name in declared_functions():
+            if name not in ("lbc_destroy", "lbc_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise LbcError(status, lib().lbc_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def quadrature(Q: int, half_range: bool):
+    z = np.zeros(Q)
+    w = np.zeros(Q)
+    _check(lib().lbc_quadrature(Q, 1 if half_range else 0, _dptr(z), _dptr(w)))
+    return z, w
+
+
+def equilibrium(params: dict, ux: float, uy: float, T: float):
+    p = make_params(params)
+    gx = np.zeros(2 * p.Qx)
+    gy = np.zeros(p.Qy)
+    _check(lib().lbc_equilibrium(C.byref(p), ux, uy, T, _dptr(gx), _dptr(gy)))
+    return gx, gy
+
+
+def current_stream_handle():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+class Solver:
+    """One Couette problem on the GPU (see include/lbc.h)."""
+
+    def __init__(self, params: dict, stream=None):
+        self.params = dict(DEFAULTS)
+        self.params.update(params)
+        self._p = make_params(self.params)
+        h = C.c_void_p()
+        st = stream if stream is not None else current_stream_handle()
+        _check(lib().lbc_create(C.byref(self._p), C.c_void_p(st) if st else None, C.byref(h)))
+        self._h = h
+        nx, nv, dt, steps = C.c_int(), C.c_int(), C.c_double(), C.c_long()
+        _check(lib().lbc_info(self._h, C.byref(nx), C.byref(nv), C.byref(dt), C.byref(steps)))
+        self.Nx, self.V, self.dt = nx.value, nv.value, dt.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbc_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def steps(self) -> int:
+        steps = C.c_long()
+        _check(lib().lbc_info(self._h, None, None, None, C.byref(steps)))
+        return steps.value
+
+    def step(self, nsteps: int = 1):
+        _check(lib().lbc_step(self._h, int(nsteps)))
+
+    def run_to_steady(self, residual: float, max_steps: int):
+        """Returns (steps taken, last residual); raises LbcError(ENOTCONV) past max_steps."""
+        done = C.c_long()
+        res = C.c_double()
+        _check(lib().lbc_run_to_steady(self._h, residual, int(max_steps), C.byref(done), C.byref(res)))
+        return done.value, res.value
+
+    def moments(self):
+        out = np.zeros((NMOM, self.Nx))
+        x = np.zeros(self.Nx)
+        _check(lib().lbc_moments(self._h, _dptr(out), _dptr(x)))
+        self.x = x
+        return out
+
+    def get_state(self) -> np.ndarray:
+        f = np.zeros((2, self.V, self.Nx))
+        _check(lib().lbc_get_state(self._h, _dptr(f)))
+        return f
+
+    def set_state(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(2, self.V, self.Nx)
+        _check(lib().lbc_set_state(self._h, _dptr(f)))
