@@ -1,16 +1,27 @@
 // Fused RK-3 stage kernel of the half-range LB Couette solver (sm_103a).
 //
-// One CTA owns a tile of 32 nodes x one chunk of the velocity set, both fields.
-// Per stage it: (1) sums the raw moment partials of its nodes written by the
-// previous stage and turns them into n, u, T, P, q (Sec. II); (2) builds the
-// discrete equilibrium factors g_x, g_y of every node (Eqs. gx, gy) with one
-// warp per node; (3) on a wall tile, computes the wall density n_w from the
-// outgoing WENO-5 wall flux (Eqs. diffuse, diffuse_nw); (4) streams its
-// velocity rows: WENO-5 faces (upwind by sign p_x), Shakhov target (Sec. II),
-// relaxation with 1/tau from Eq. tau, TVD RK-3 combination, store; (5) reduces
-// the new stage's raw moments over its velocities for the next stage; on the
-// last stage also the residual max w |f^{n+1} - f^n|.
+// One CTA owns a tile of 31 nodes (lane l: node c0 + l and the face on its
+// left, so each lane computes one WENO-5 face per row) x one chunk of the
+// velocity set, both fields. Per stage it:
+//  (1) reads its nodes' stage data (moments, 1/tau, Shakhov prefactor) and
+//      discrete equilibrium factors g_x, g_y (Eqs. gx, gy), built by the
+//      previous stage (or at set-up);
+//  (2) on a tile whose stencil reaches a wall, computes the wall density n_w
+//      from the outgoing WENO-5 wall flux (Eqs. diffuse, diffuse_nw);
+//  (3) streams the chunk's velocity rows through a TMA pipeline (kPipe stages
+//      of kSubV rows, mbarrier completion): WENO-5 faces upwind by sign p_x,
+//      Shakhov target (Sec. II) with 1/tau of Eq. tau, TVD RK-3 combination,
+//      store, and the new stage's raw moments over the chunk's velocities;
+//  (4) publishes the per-chunk moment partials; the last chunk CTA of the tile
+//      to finish turns them into the next stage's tile data (moments in FP64,
+//      equilibrium factors by the stable Gauss-sum projection). On the last
+//      stage it also folds the residual max w |f^{n+1} - f^n|.
+// The state is the deviation d = ft - ft_rest from the weight-divided rest
+// Maxwellian (n = 1, u = 0, T = 1): WENO-5, the ghost extrapolation and the RK
+// combination are affine-invariant, so they act on d unchanged, and the FP32
+// path keeps ~1e-8 absolute resolution for near-equilibrium flows.
 #include <cstdint>
+#include <type_traits>
 
 #include "lbc_device.h"
 
@@ -18,39 +29,138 @@ namespace lbc {
 
 namespace {
 
-__device__ __forceinline__ double warp_sum(double v)
+constexpr long kSpinLimit = 1L << 22;   // bounded mbarrier wait (try_wait suspends per call)
+
+template <typename R> struct Tabs;
+template <> struct Tabs<double> {
+    __device__ static const double *vel(const DevTables &T) { return T.d_vel; }
+    __device__ static const double *hz(const DevTables &T) { return T.hz; }
+    __device__ static const double *He(const DevTables &T) { return T.He; }
+    __device__ static const double *alpha(const DevTables &T) { return T.alpha; }
+    __device__ static const double *Yk(const DevTables &T) { return T.Yk; }
+    __device__ static const double *Wk(const DevTables &T) { return T.Wk; }
+    __device__ static const double *ijd(const DevTables &T) { return T.inv_jdeta; }
+    __device__ static double sbeta(const DevTables &T, int l) { return T.sbeta[l]; }
+    __device__ static double isbeta(const DevTables &T, int l) { return 1.0 / T.sbeta[l]; }
+    __device__ static double inv_l(const DevTables &, int l) { return 1.0 / l; }
+};
+template <> struct Tabs<float> {
+    __device__ static const float *vel(const DevTables &T) { return T.f_vel; }
+    __device__ static const float *hz(const DevTables &T) { return T.f_hz; }
+    __device__ static const float *He(const DevTables &T) { return T.f_He; }
+    __device__ static const float *alpha(const DevTables &T) { return T.f_alpha; }
+    __device__ static const float *Yk(const DevTables &T) { return T.f_Yk; }
+    __device__ static const float *Wk(const DevTables &T) { return T.f_Wk; }
+    __device__ static const float *ijd(const DevTables &T) { return T.f_inv_jdeta; }
+    __device__ static float sbeta(const DevTables &T, int l) { return T.f_sbeta[l]; }
+    __device__ static float isbeta(const DevTables &T, int l) { return T.f_isbeta[l]; }
+    __device__ static float inv_l(const DevTables &T, int l) { return T.f_inv_l[l]; }
+};
+
+// ---- compensated arithmetic (error-free transformations of Knuth and Dekker) ----
+template <typename R>
+__device__ __forceinline__ void two_sum(R a, R b, R &s, R &e)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    s = a + b;
+    R bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
 }
 
-// WENO-5 (Jiang & Shu) face value between c and d, upwind cell c.
+// Sum with a compensation term in FP32 (TwoSum of Knuth); plain in FP64.
+template <typename R>
+struct CSum {
+    R s = R(0), c = R(0);
+    __device__ __forceinline__ void add(R x)
+    {
+        if constexpr (std::is_same<R, float>::value) {
+            R t, e;
+            two_sum(s, x, t, e);
+            s = t;
+            c += e;
+        } else {
+            s += x;
+        }
+    }
+    __device__ __forceinline__ R value() const { return s + c; }
+};
+
+// Dot product with a compensated accumulator in FP32 (Ogita, Rump & Oishi's
+// Dot2); plain FMA chain in FP64.
+template <typename R>
+struct Dot {
+    R s = R(0), c = R(0);
+    __device__ __forceinline__ void add(R x, R y)
+    {
+        if constexpr (std::is_same<R, float>::value) {
+            R p = x * y, ep = fmaf(x, y, -p), t, es;
+            two_sum(s, p, t, es);
+            s = t;
+            c += ep + es;
+        } else {
+            s = fma(x, y, s);
+        }
+    }
+    __device__ __forceinline__ R value() const { return s + c; }
+};
+
+template <typename R> __device__ __forceinline__ R rcp(R x);
+template <> __device__ __forceinline__ float rcp<float>(float x)
+{
+    float r;   // hardware reciprocal approximation (MUFU), adequate for WENO weights in FP32
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
+template <typename R> __device__ __forceinline__ R fdiv(R a, R b);
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
+
+// WENO-5 (Jiang & Shu) face value between c and d with upwind cell c.
 template <typename R>
 __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
 {
     const R eps = R(1e-6);
-    R q0 = (R(2) * a - R(7) * b + R(11) * c) * R(1.0 / 6.0);
-    R q1 = (-b + R(5) * c + R(2) * d) * R(1.0 / 6.0);
-    R q2 = (R(2) * c + R(5) * d - e) * R(1.0 / 6.0);
+    R q0 = R(2) * a - R(7) * b + R(11) * c;
+    R q1 = -b + R(5) * c + R(2) * d;
+    R q2 = R(2) * c + R(5) * d - e;
     R t0 = a - R(2) * b + c, t1 = a - R(4) * b + R(3) * c;
     R t2 = b - R(2) * c + d, t3 = b - d;
     R t4 = c - R(2) * d + e, t5 = R(3) * c - R(4) * d + e;
-    R b0 = R(13.0 / 12.0) * t0 * t0 + R(0.25) * t1 * t1;
-    R b1 = R(13.0 / 12.0) * t2 * t2 + R(0.25) * t3 * t3;
-    R b2 = R(13.0 / 12.0) * t4 * t4 + R(0.25) * t5 * t5;
-    R e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
-    e0 *= e0; e1 *= e1; e2 *= e2;
-    // alpha_k = d_k / e_k: multiply through by e0 e1 e2 to need one division
-    R a0 = R(0.1) * e1 * e2, a1 = R(0.6) * e0 * e2, a2 = R(0.3) * e0 * e1;
-    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    R e0 = eps + R(13.0 / 12.0) * t0 * t0 + R(0.25) * t1 * t1;
+    R e1 = eps + R(13.0 / 12.0) * t2 * t2 + R(0.25) * t3 * t3;
+    R e2 = eps + R(13.0 / 12.0) * t4 * t4 + R(0.25) * t5 * t5;
+    // nonlinear weights d_k / (eps + beta_k)^2 (each bounded by d_k / eps^2)
+    R a0 = R(0.1) * rcp<R>(e0 * e0), a1 = R(0.6) * rcp<R>(e1 * e1), a2 = R(0.3) * rcp<R>(e2 * e2);
+    return fdiv<R>(a0 * q0 + a1 * q1 + a2 * q2, R(6) * (a0 + a1 + a2));
 }
 
-// Moments (n, u_x, u_y, T, P_xx, P_yy, P_zz, P_xy, q_x, q_y) from raw sums about shift (sx, sy).
+// Raw sums of the rest Maxwellian about shift (sx, sy), from its power sums P_ab.
+__device__ void rest_raw(const double *P, double sx, double sy, double *r)
+{
+    const double P00 = P[0], P10 = P[1], P01 = P[2], P20 = P[3], P11 = P[4], P02 = P[5];
+    const double P30 = P[6], P21 = P[7], P12 = P[8], P03 = P[9];
+    r[R_S0] = P00;
+    r[R_SX] = P10 - sx * P00;
+    r[R_SY] = P01 - sy * P00;
+    r[R_SXX] = P20 - 2 * sx * P10 + sx * sx * P00;
+    r[R_SXY] = P11 - sx * P01 - sy * P10 + sx * sy * P00;
+    r[R_SYY] = P02 - 2 * sy * P01 + sy * sy * P00;
+    r[R_CZ] = P00;                       // chi_rest = T_rest phi_rest, T_rest = 1
+    double a3 = P30 - 3 * sx * P20 + 3 * sx * sx * P10 - sx * sx * sx * P00;
+    double ab2 = P12 - 2 * sy * P11 + sy * sy * P10 - sx * P02 + 2 * sx * sy * P01 - sx * sy * sy * P00;
+    double b3 = P03 - 3 * sy * P02 + 3 * sy * sy * P01 - sy * sy * sy * P00;
+    double ba2 = P21 - 2 * sx * P11 + sx * sx * P01 - sy * P20 + 2 * sx * sy * P10 - sy * sx * sx * P00;
+    r[R_R3X] = a3 + ab2;
+    r[R_R3Y] = b3 + ba2;
+    r[R_GX] = P10 - sx * P00;
+    r[R_GY] = P01 - sy * P00;
+}
+
+// n, u_x, u_y, T, P_xx, P_yy, P_zz, P_xy, q_x, q_y from raw sums about (sx, sy).
 __device__ void raw_to_moments(const double *r, double sx, double sy, double *m)
 {
-    double n = r[R_S0];
-    double bx = r[R_SX] / n, by = r[R_SY] / n;
+    double n = r[R_S0], in = 1.0 / n;
+    double bx = r[R_SX] * in, by = r[R_SY] * in;
     double pxx = r[R_SXX] - n * bx * bx;
     double pxy = r[R_SXY] - n * bx * by;
     double pyy = r[R_SYY] - n * by * by;
@@ -61,154 +171,281 @@ __device__ void raw_to_moments(const double *r, double sx, double sy, double *m)
     m[0] = n;
     m[1] = sx + bx;
     m[2] = sy + by;
-    m[3] = (pxx + pyy + pzz) / (3.0 * n);
+    m[3] = (pxx + pyy + pzz) * in * (1.0 / 3.0);
     m[4] = pxx; m[5] = pyy; m[6] = pzz; m[7] = pxy;
     m[8] = 0.5 * hx + 0.5 * (r[R_GX] - bx * pzz);
     m[9] = 0.5 * hy + 0.5 * (r[R_GY] - by * pzz);
 }
 
-// Velocity v -> (p_x, p_y, w, a, j).
-__device__ __forceinline__ void velocity(const DevTables &T, int v, double &px, double &py, double &w, int &a, int &j)
+// ---- TMA and mbarrier (inline PTX) ----
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
-    a = v / T.Qy;
-    j = v - a * T.Qy;
-    int i = a < T.Qx ? a : a - T.Qx;
-    px = (a < T.Qx ? 1.0 : -1.0) * T.p0 * T.zx[i];
-    py = T.p0 * T.yy[j];
-    w = T.wx[i] * T.wy[j];
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Warp-cooperative discrete equilibrium of one node: gx[2Qx], gy[Qy] (see the
-// host version for the algorithm). cbuf: per-warp scratch [2 (Nxe+1)].
-template <typename R>
-__device__ void warp_equilibrium(const DevTables &T, double ux, double uy, double Tc, R *gx, R *gy,
-                                 double *cbuf)
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    const int lane = threadIdx.x & 31, N = T.Nxe;
-    double Tp = Tc / (T.p0 * T.p0), up = ux / T.p0, sT = sqrt(Tp), a = up / sT;
-    double zt[2], rp[2], rm[2], hprev[2], h[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        int k = lane + 32 * q;
-        bool ok = k < T.K;
-        double Y = ok ? T.Yk[k] : 0.0, W = ok ? T.Wk[k] : 0.0;
-        zt[q] = sT * Y;
-        rp[q] = W * exp(a * Y - 0.5 * a * a);
-        rm[q] = W * exp(-a * Y - 0.5 * a * a);
-        hprev[q] = 0.0;
-        h[q] = 1.0 / T.sbeta[0];
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (long i = 0; i < kSpinLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
     }
-    for (int l = 0; l <= N; ++l) {
-        double vp = rp[0] * h[0] + rp[1] * h[1];
-        double vm = rm[0] * h[0] + rm[1] * h[1];
-        vp = warp_sum(vp);
-        vm = warp_sum(vm);
-        if (lane == 0) { cbuf[l] = vp; cbuf[N + 1 + l] = vm; }
-        double al = T.alpha[l], sb = T.sbeta[l], sb1 = T.sbeta[l + 1];
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---- tile stage data ----
+template <typename R>
+struct EqScratch {
+    size_t raw, sc, warp, per_warp, total;
+    __host__ __device__ EqScratch(int K, int N)
+    {
+        raw = 0;
+        sc = raw + (size_t)kLanes * kNumRaw * sizeof(double);
+        warp = sc + (size_t)kLanes * 8 * sizeof(R);
+        per_warp = ((size_t)K * 16 + 2 * K + 2 * (N + 1)) * sizeof(R);
+        per_warp = (per_warp + 15) / 16 * 16;
+        total = warp + kWarps * per_warp;
+    }
+};
+
+// Stage data of one tile of buffer `buf` (block-wide, all threads): sums the
+// per-chunk raw moment partials, turns them into moments in FP64 (adding the
+// rest state's share), and builds the discrete equilibrium factors of Eqs. gx,
+// gy at every node of the tile (algorithm: see equilibrium_host). Writes
+// eqm[buf] for the tile's nodes and the tile's block of eqg[buf].
+template <typename R>
+__device__ void tile_equilibrium(const DevTables &T, const DevState &S, int buf, int tile, unsigned char *scratch)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, c0 = tile * kTile;
+    const int N = T.Nxe, K = T.K, G = 2 * T.Qx + T.Qy;
+    const EqScratch<R> L(K, N);
+    double *raw = reinterpret_cast<double *>(scratch + L.raw);   // [32][kNumRaw]
+    R *sc = reinterpret_cast<R *>(scratch + L.sc);               // [32][8]: sT a a^2/2 uy' T'-1
+    R *H = reinterpret_cast<R *>(scratch + L.warp + warp * L.per_warp);   // [K][16]
+    R *rpm = H + K * 16;                                                  // [2][K]
+    R *cpm = rpm + 2 * K;                                                 // [2][N+1]
+    const R *part = static_cast<const R *>(S.part[buf]);
+    const R *shift = static_cast<const R *>(S.shift[buf]);
+    R *eqm = static_cast<R *>(S.eqm[buf]);
+    R *eqg = static_cast<R *>(S.eqg[buf]) + (size_t)tile * G * kLanes;
+
+    for (int idx = tid; idx < kLanes * kNumRaw; idx += kThreads) {
+        const int c = idx & 31, m = idx >> 5, s = c0 + c;
+        CSum<R> acc;
+        if (c < kTile && s < T.Nx)
+            for (int ch = 0; ch < T.nchunk; ++ch) acc.add(__ldcg(&part[((size_t)ch * kNumRaw + m) * T.Nxp + s]));
+        raw[c * kNumRaw + m] = (double)acc.value();
+    }
+    __syncthreads();
+    if (tid < kLanes) {
+        const int s = c0 + tid;
+        double m[10];
+        if (tid < kTile && s < T.Nx) {
+            double sx = (double)__ldcg(&shift[s]), sy = (double)__ldcg(&shift[T.Nxp + s]), rr[kNumRaw];
+            rest_raw(T.restP, sx, sy, rr);
+            for (int k = 0; k < kNumRaw; ++k) rr[k] += raw[tid * kNumRaw + k];
+            raw_to_moments(rr, sx, sy, m);
+            // a NaN/Inf anywhere in the node's populations reaches its moments
+            if (!isfinite(m[0]) || !isfinite(m[3]) || !isfinite(m[8]) || !isfinite(m[9]) || !(m[0] > 0.0) ||
+                !(m[3] > 0.0))
+                S.ctl->nonfinite = 1;
+        } else {
+            m[0] = 1.0; m[1] = m[2] = 0.0; m[3] = 1.0; m[8] = m[9] = 0.0;
+        }
+        const R n = R(m[0]), ux = R(m[1]), uy = R(m[2]), Tc = R(m[3]);
+        const R nu = n * R(T.delta * 1.4142135623730951) * pow(Tc, R(1.0 - T.omega));   // 1/tau, Eq. tau
+        const R cS = R(1.0 - T.Pr) / (n * Tc * Tc);                                     // Shakhov prefactor
+        if (tid < kTile && s < T.Nx) {
+            R *e = eqm + (size_t)s * kEqM;
+            e[0] = n; e[1] = ux; e[2] = uy; e[3] = Tc; e[4] = R(m[8]); e[5] = R(m[9]);
+            e[6] = nu; e[7] = cS; e[8] = R(1) / (R(5) * Tc);
+        }
+        const R ip0 = R(1.0 / T.p0), Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
+        R *x = sc + tid * 8;
+        x[0] = sT; x[1] = a; x[2] = R(0.5) * a * a; x[3] = uy * ip0; x[4] = Tp - R(1);
+    }
+    __syncthreads();
+
+    const R *alpha = Tabs<R>::alpha(T), *Yk = Tabs<R>::Yk(T), *Wk = Tabs<R>::Wk(T);
+    const R *hz = Tabs<R>::hz(T), *He = Tabs<R>::He(T);
+    const R h0 = R(1.0 / T.sbeta[0]);
+    for (int c = warp; c < kTile; c += kWarps) {
+        const R *x = sc + c * 8;
+        const R sT = x[0], a = x[1], ha = x[2], uq = x[3], tm1 = x[4];
+        // lanes over projection nodes k: weights r_k^{+-} and the recurrence state
+        R zt[2], h[2], hp[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            double hn = ((zt[q] - al) * h[q] - sb * hprev[q]) / sb1;
-            hprev[q] = h[q];
-            h[q] = hn;
+            int k = lane + 32 * q;
+            R Y = k < K ? Yk[k] : R(0);
+            zt[q] = sT * Y;
+            if (k < K) {
+                rpm[k] = Wk[k] * exp(a * Y - ha);
+                rpm[K + k] = Wk[k] * exp(-a * Y - ha);
+            }
+            h[q] = h0;
+            hp[q] = R(0);
         }
-    }
-    __syncwarp();
-    for (int i = lane; i < 2 * T.Qx; i += 32) {
-        int ii = i < T.Qx ? i : i - T.Qx;
-        const double *c = cbuf + (i < T.Qx ? 0 : N + 1);
-        double s = 0.0;
-        for (int l = 0; l <= N; ++l) s += T.hz[l * T.Qx + ii] * c[l];
-        gx[i] = R(s);
-    }
-    double uq = uy / T.p0;
-    for (int jj = lane; jj < T.Qy; jj += 32) {
-        double bm = 1.0, b = uq;
-        double s = T.He[jj];                      // l = 0
-        if (T.Nye >= 1) s += T.He[T.Qy + jj] * b;
-        for (int l = 1; l < T.Nye; ++l) {
-            double bn = (uq * b + (Tp - 1.0) * bm) / (l + 1.0);
-            bm = b;
-            b = bn;
-            s += T.He[(l + 1) * T.Qy + jj] * b;
+        for (int lb = 0; lb <= N; lb += 16) {
+            const int le = min(N, lb + 15);
+            for (int l = lb; l <= le; ++l) {
+                const R al = alpha[l], sb = Tabs<R>::sbeta(T, l), isb1 = Tabs<R>::isbeta(T, l + 1);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    int k = lane + 32 * q;
+                    if (k < K) H[k * 16 + (l - lb)] = h[q];
+                    R hn = ((zt[q] - al) * h[q] - sb * hp[q]) * isb1;
+                    hp[q] = h[q];
+                    h[q] = hn;
+                }
+            }
+            __syncwarp();
+            // lanes 0-15: c^+_l, lanes 16-31: c^-_l, l = lb + (lane % 16)
+            const int l = lb + (lane & 15), sgn = lane >> 4;
+            if (l <= le) {
+                Dot<R> d;
+                for (int k = 0; k < K; ++k) d.add(rpm[sgn * K + k], H[k * 16 + (lane & 15)]);
+                cpm[sgn * (N + 1) + l] = d.value();
+            }
+            __syncwarp();
         }
-        gy[jj] = R(s);
+        for (int i = lane; i < 2 * T.Qx; i += 32) {
+            const int ii = i < T.Qx ? i : i - T.Qx;
+            const R *cc = cpm + (i < T.Qx ? 0 : N + 1);
+            Dot<R> d;
+            for (int l = 0; l <= N; ++l) d.add(hz[l * T.Qx + ii], cc[l]);
+            eqg[(size_t)i * kLanes + c] = d.value();
+        }
+        // g_y: b_{l+1} = (u' b_l + (T'-1) b_{l-1}) / (l+1), g_y,j = sum_l He_l(y_j) b_l
+        for (int jj = lane; jj < T.Qy; jj += 32) {
+            R bm = R(1), b = uq;
+            Dot<R> d;
+            d.add(He[jj], R(1));
+            if (T.Nye >= 1) d.add(He[T.Qy + jj], b);
+            for (int l = 1; l < T.Nye; ++l) {
+                R bn = (uq * b + tm1 * bm) * Tabs<R>::inv_l(T, l + 1);
+                bm = b;
+                b = bn;
+                d.add(He[(l + 1) * T.Qy + jj], b);
+            }
+            eqg[(size_t)(2 * T.Qx + jj) * kLanes + c] = d.value();
+        }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
-// Outgoing WENO-5 wall face of phi at the left (px < 0) or right (px > 0) wall,
-// with two ghost nodes by cubic extrapolation in eta from the four nearest nodes.
+// Outgoing WENO-5 wall face of a deviation row at the left (px < 0) or right
+// (px > 0) wall; two ghost nodes by cubic extrapolation in eta.
 template <typename R>
 __device__ __forceinline__ R outgoing_wall_face(const R *row, int Nx, bool right)
 {
-    if (right) {
-        R f1 = row[Nx - 1], f2 = row[Nx - 2], f3 = row[Nx - 3], f4 = row[Nx - 4];
-        R g1 = R(4) * f1 - R(6) * f2 + R(4) * f3 - f4;
-        R g2 = R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
-        return weno5<R>(f3, f2, f1, g1, g2);
-    }
-    R f1 = row[0], f2 = row[1], f3 = row[2], f4 = row[3];
+    R f1, f2, f3, f4;
+    if (right) { f1 = row[Nx - 1]; f2 = row[Nx - 2]; f3 = row[Nx - 3]; f4 = row[Nx - 4]; }
+    else       { f1 = row[0];      f2 = row[1];      f3 = row[2];      f4 = row[3]; }
     R g1 = R(4) * f1 - R(6) * f2 + R(4) * f3 - f4;
     R g2 = R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
     return weno5<R>(f3, f2, f1, g1, g2);
 }
 
-template <typename R>
-struct StageSmem {
-    double raw[kTileCells][kNumRaw + 1];
-    double mom[kTileCells][12];     // n ux uy T qx qy nu cS (+pad)
-    double cbuf[kWarps][2 * kMaxQ + 2];
-    double red[kWarps][kNumRaw][kTileCells];
-    double wsum[kWarps];
-    double nw[2];
-    R row[kWarps][2][kTileCells + 8];
-    R gx[kTileCells][2 * kMaxQ];
-    R gy[kTileCells][kMaxQ];
-};
-
-__device__ __forceinline__ double collision_rate(const DevTables &T, double n, double Tc)
-{
-    return n * T.delta * 1.4142135623730951 * pow(Tc, 1.0 - T.omega);
-}
-
+// n_w of one wall (Eq. diffuse_nw) from the stage-input deviation, all threads;
+// the flux is accumulated in FP64 so the wall mass balance holds to round-off.
 template <typename R>
 __device__ void block_wall_density(const DevTables &T, const R *phi, bool right, double *wsum, double *out)
 {
-    // outgoing velocities: right wall p_x > 0 -> a < Qx; left wall p_x < 0 -> a >= Qx
-    const int half = T.Qx * T.Qy;
-    const int vbeg = right ? 0 : half;
+    const int half = T.Qx * T.Qy, vbeg = right ? 0 : half;
+    const R *vel = Tabs<R>::vel(T);
     double acc = 0.0;
     for (int v = vbeg + threadIdx.x; v < vbeg + half; v += blockDim.x) {
-        double px, py, w;
-        int a, j;
-        velocity(T, v, px, py, w, a, j);
-        R face = outgoing_wall_face<R>(phi + (size_t)v * T.Nxp, T.Nx, right);
-        acc += px * w * (double)face;
+        R f = outgoing_wall_face<R>(phi + (size_t)v * T.Nxp, T.Nx, right);
+        acc += (double)(vel[VC_PX * T.V + v] * vel[VC_W * T.V + v] * f);
     }
-    acc = warp_sum(acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) wsum[warp] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kWarps; ++w) s += wsum[w];
+        double s = right ? T.restOutR : T.restOutL;
+        for (int k = 0; k < kWarps; ++k) s += wsum[k];
         *out = -s / (right ? T.inR : T.inL);
     }
     __syncthreads();
 }
 
+// Per-velocity data staged in shared memory for the chunk: p_x, p_y, w, ft_rest,
+// incoming wall values (phi, chi; left, right) minus ft_rest at the current n_w,
+// and the indices a, j.
+enum { VR_PX = 0, VR_PY, VR_W, VR_FR, VR_INL0, VR_INL1, VR_INR0, VR_INR1, VR_A, VR_J, kVRow };
+
+// Dynamic shared memory layout of the stage kernel. The pipeline region is
+// reused after the main loop for the moment reduction and the tile stage data.
+template <typename R>
+struct Layout {
+    size_t bar, pipe, fin, f0, g, vrow, misc, total;
+    __host__ __device__ Layout(int Qx, int Qy, int N, int K, int vchunk)
+    {
+        size_t o = 0;
+        bar = o;  o = al(o + kPipe * sizeof(uint64_t));
+        pipe = o;
+        fin = o;
+        f0 = fin + (size_t)kPipe * 2 * kSubV * kRowLen * sizeof(R);
+        size_t pipe_bytes = f0 + (size_t)kPipe * 2 * kSubV * kF0Len * sizeof(R) - pipe;
+        size_t red_bytes = (size_t)kWarps * kNumRaw * kLanes * sizeof(R);
+        size_t eq_bytes = EqScratch<R>(K, N).total;
+        size_t m = pipe_bytes > red_bytes ? pipe_bytes : red_bytes;
+        m = m > eq_bytes ? m : eq_bytes;
+        o = al(o + m);
+        g = o;    o = al(o + (size_t)(2 * Qx + Qy) * kLanes * sizeof(R));
+        vrow = o; o = al(o + (size_t)vchunk * kVRow * sizeof(R));
+        misc = o; o = al(o + 16 * sizeof(double));
+        total = o + 128;   // slack for aligning the dynamic base
+    }
+    __host__ __device__ static size_t al(size_t x) { return (x + 127) / 128 * 128; }
+};
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-stage_kernel(DevTables T, DevState S, int stage, int rel, double stop_eps)
+stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateMaps M, int stage, int rel,
+             double stop_eps)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    StageSmem<R> &sm = *reinterpret_cast<StageSmem<R> *>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // TMA destinations want 128-byte aligned shared memory: align the base explicitly
+    unsigned char *smem = smem_dyn + ((128 - (smem_addr(smem_dyn) & 127)) & 127);
+    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.K, T.vchunk);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][2][kSubV][kRowLen]
+    R *s_f0 = reinterpret_cast<R *>(smem + L.f0);         // [kPipe][2][kSubV][kF0Len]
+    R *s_g = reinterpret_cast<R *>(smem + L.g);           // [2Qx + Qy][kLanes]
+    double *s_misc = reinterpret_cast<double *>(smem + L.misc);   // wsum[8], nwL, nwR, flag
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c0 = blockIdx.x * kTileCells;
-    const int chunk = blockIdx.y;
+    const int tile = blockIdx.x, c0 = tile * kTile, chunk = blockIdx.y;
     const int in = stage, out = (stage + 1) % 3;
     const long long step = S.ctl->base + rel;
+    const int V = T.V, G = 2 * T.Qx + T.Qy;
 
     // ---- early stop (run-to-steady): every block takes the same decision ----
     if (stop_eps > 0.0) {
@@ -223,191 +460,286 @@ stage_kernel(DevTables T, DevState S, int stage, int rel, double stop_eps)
     }
     if (stage == 0 && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) S.resid[step % kResidRing] = 0ull;
 
-    const R *Fin = static_cast<const R *>(S.F[in]);
-    const R *F0 = static_cast<const R *>(S.F[0]);
-    R *Fout = static_cast<R *>(S.F[out]);
-    const size_t fstride = (size_t)T.V * T.Nxp;
-
-    // ---- (1) stage-input moments of the tile's nodes ----
-    for (int idx = tid; idx < kTileCells * kNumRaw; idx += kThreads) {
-        int c = idx % kTileCells, m = idx / kTileCells, s = c0 + c;
-        double acc = 0.0;
-        if (s < T.Nx)
-            for (int ch = 0; ch < T.nchunk; ++ch) acc += S.part[in][((size_t)ch * kNumRaw + m) * T.Nxp + s];
-        sm.raw[c][m] = acc;
-    }
-    __syncthreads();
-    if (tid < kTileCells) {
-        int s = c0 + tid;
-        double m[10];
-        if (s < T.Nx) {
-            raw_to_moments(sm.raw[tid], S.shift[in][s], S.shift[in][T.Nxp + s], m);
-        } else {
-            m[0] = 1.0; m[1] = m[2] = 0.0; m[3] = 1.0; m[8] = m[9] = 0.0;
-        }
-        sm.mom[tid][0] = m[0]; sm.mom[tid][1] = m[1]; sm.mom[tid][2] = m[2]; sm.mom[tid][3] = m[3];
-        sm.mom[tid][4] = m[8]; sm.mom[tid][5] = m[9];
-        sm.mom[tid][6] = collision_rate(T, m[0], m[3]);
-        sm.mom[tid][7] = (1.0 - T.Pr) / (m[0] * m[3] * m[3]);
-    }
-    __syncthreads();
-
-    // ---- (2) discrete equilibrium of each node: one warp per node ----
-    for (int c = warp; c < kTileCells; c += kWarps)
-        warp_equilibrium<R>(T, sm.mom[c][1], sm.mom[c][2], sm.mom[c][3], sm.gx[c], sm.gy[c], sm.cbuf[warp]);
-
-    // ---- (3) wall densities (tiles whose 3-node halo reaches a wall) ----
-    const bool needL = c0 == 0;
-    const bool needR = c0 + kTileCells + 3 > T.Nx;
-    if (needL) block_wall_density<R>(T, Fin, false, sm.wsum, &sm.nw[0]);
-    if (needR) block_wall_density<R>(T, Fin, true, sm.wsum, &sm.nw[1]);
-    __syncthreads();
-
-    // ---- (4) stream the chunk's velocity rows ----
-    const double ca = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
-    const double cb = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
-    const int s = c0 + lane;
-    const bool active = s < T.Nx;
-    const double n_c = sm.mom[lane][0], ux_c = sm.mom[lane][1], uy_c = sm.mom[lane][2];
-    const double T_c = sm.mom[lane][3], qx_c = sm.mom[lane][4], qy_c = sm.mom[lane][5];
-    const double nu_c = sm.mom[lane][6], cS_c = sm.mom[lane][7];
-    const double ijd = active ? T.inv_jdeta[s] : 0.0;
-    const double nwL = needL ? sm.nw[0] : 0.0;
-    const double nwR = needR ? sm.nw[1] : 0.0;
-
-    double acc[kNumRaw];
-#pragma unroll
-    for (int m = 0; m < kNumRaw; ++m) acc[m] = 0.0;
-    double res = 0.0;
-    bool bad = false;
-
     const int vbeg = chunk * T.vchunk;
-    const int vend = min(T.V, vbeg + T.vchunk);
-    for (int v = vbeg + warp; v < vend; v += kWarps) {
-        double px, py, w;
-        int a, j;
-        velocity(T, v, px, py, w, a, j);
-        double fo[2];
-        for (int fld = 0; fld < 2; ++fld) {
-            const R *row = Fin + fld * fstride + (size_t)v * T.Nxp;
-            R *buf = sm.row[warp][fld];
-            // buffer index b <-> node c0 - 3 + b, b in [0, 38)
-            for (int b = lane; b < kTileCells + 6; b += 32) {
-                int sn = c0 - 3 + b;
-                buf[b] = (sn >= 0 && sn < T.Nx) ? row[sn] : R(0);
-            }
-            __syncwarp();
-            if (lane < 2) {
-                if (c0 == 0) {            // left ghosts: nodes -1 (b = 2), -2 (b = 1)
-                    int b = 2 - lane;
-                    R g;
-                    if (px > 0) {
-                        g = R(nwL * T.fwL[v] * (fld ? T.TL : 1.0));
-                    } else {
-                        R f1 = buf[3], f2 = buf[4], f3 = buf[5], f4 = buf[6];
-                        g = lane == 0 ? R(4) * f1 - R(6) * f2 + R(4) * f3 - f4
-                                      : R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
-                    }
-                    buf[b] = g;
-                }
-                int bR = T.Nx - c0 + 3 + lane;   // right ghosts: nodes Nx (lane 0), Nx+1 (lane 1)
-                if (bR < kTileCells + 6) {
-                    R g;
-                    if (px < 0) {
-                        g = R(nwR * T.fwR[v] * (fld ? T.TR : 1.0));
-                    } else {
-                        int bl = T.Nx - 1 - c0 + 3;
-                        R f1 = buf[bl], f2 = buf[bl - 1], f3 = buf[bl - 2], f4 = buf[bl - 3];
-                        g = lane == 0 ? R(4) * f1 - R(6) * f2 + R(4) * f3 - f4
-                                      : R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
-                    }
-                    buf[bR] = g;
-                }
-            }
-            __syncwarp();
-            // face k = c0 + lane (left of node s); buffer index of node k is lane + 3
-            auto face = [&](int k, int bk) -> R {
-                if (px > 0) {
-                    if (k == 0) return R(nwL * T.fwL[v] * (fld ? T.TL : 1.0));
-                    return weno5<R>(buf[bk - 3], buf[bk - 2], buf[bk - 1], buf[bk], buf[bk + 1]);
-                }
-                if (k == T.Nx) return R(nwR * T.fwR[v] * (fld ? T.TR : 1.0));
-                return weno5<R>(buf[bk + 2], buf[bk + 1], buf[bk], buf[bk - 1], buf[bk - 2]);
-            };
-            R fl = face(c0 + lane, lane + 3);
-            R fr = __shfl_down_sync(0xffffffffu, fl, 1);
-            if (lane == 31) fr = face(c0 + 32, 35);
-            __syncwarp();
-            double f = (double)buf[lane + 3];
-            double adv = -px * ((double)fr - (double)fl) * ijd;
-            double feq = n_c * (double)sm.gx[lane][a] * (double)sm.gy[lane][j];
-            double xx = px - ux_c, xy = py - uy_c;
-            double qxi = qx_c * xx + qy_c * xy;
-            double x2 = (xx * xx + xy * xy) / (5.0 * T_c);
-            double tgt = fld ? T_c * feq * (1.0 + cS_c * (x2 - 0.4) * qxi)
-                             : feq * (1.0 + cS_c * (x2 - 0.8) * qxi);
-            double L = adv - nu_c * (f - tgt);
-            double fn = f + T.dt * L;
-            double f0v = 0.0;
-            if (stage > 0 && active) {
-                f0v = (double)F0[fld * fstride + (size_t)v * T.Nxp + s];
-                fn = ca * f0v + cb * fn;
-            }
-            R fnr = R(fn);
-            if (active) {
-                Fout[fld * fstride + (size_t)v * T.Nxp + s] = fnr;
-                if (!isfinite((double)fnr)) bad = true;
-                if (stage == 2) res = fmax(res, w * fabs((double)fnr - f0v));
-            }
-            fo[fld] = (double)fnr;
+    const int vend = min(V, vbeg + T.vchunk);
+    const int nsub = (vend - vbeg + kSubV - 1) / kSubV;
+    const uint32_t tx_bytes =
+        (uint32_t)((2 * kSubV * kRowLen + (stage > 0 ? 2 * kSubV * kF0Len : 0)) * sizeof(R));
+    const CUtensorMap *in_map = &M.in[in];
+    // TMA x coordinates must be 16-byte aligned: start the boxes at multiples of 4 nodes
+    const int x0 = ((c0 - 3) >> 2) << 2, off = c0 - 3 - x0;     // node s <-> column s - x0
+    const int xf = (c0 >> 2) << 2, offf = c0 - xf;
+
+    auto issue = [&](int sub) {
+        int p = sub % kPipe, v0 = vbeg + sub * kSubV;
+        R *fin = s_fin + (size_t)p * 2 * kSubV * kRowLen;
+        mbar_expect_tx(&bar[p], tx_bytes);
+        tma_load_2d(fin, in_map, x0, v0, &bar[p]);
+        tma_load_2d(fin + kSubV * kRowLen, in_map, x0, V + v0, &bar[p]);
+        if (stage > 0) {
+            R *f0 = s_f0 + (size_t)p * 2 * kSubV * kF0Len;
+            tma_load_2d(f0, &M.f0, xf, v0, &bar[p]);
+            tma_load_2d(f0 + kSubV * kF0Len, &M.f0, xf, V + v0, &bar[p]);
         }
-        if (active) {
-            double xs = px - ux_c, ys = py - uy_c;
-            double fw = w * fo[0], gw = w * fo[1];
-            double e2 = xs * xs + ys * ys;
-            acc[R_S0] += fw;
-            acc[R_SX] += xs * fw;
-            acc[R_SY] += ys * fw;
-            acc[R_SXX] += xs * xs * fw;
-            acc[R_SXY] += xs * ys * fw;
-            acc[R_SYY] += ys * ys * fw;
-            acc[R_CZ] += gw;
-            acc[R_R3X] += e2 * xs * fw;
-            acc[R_R3Y] += e2 * ys * fw;
-            acc[R_GX] += xs * gw;
-            acc[R_GY] += ys * gw;
-        }
+    };
+
+    if (tid == 0) {
+        for (int p = 0; p < kPipe; ++p) mbar_init(&bar[p], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int sub = 0; sub < min(kPipe, nsub); ++sub) issue(sub);
+
+    const R *Fin = static_cast<const R *>(S.F[in]);
+    R *Fout = static_cast<R *>(S.F[out]);
+    const size_t fstride = (size_t)V * T.Nxp;
+
+    // ---- (1) the tile's stage data (overlaps the first loads) ----
+    {
+        const R *src = static_cast<const R *>(S.eqg[in]) + (size_t)tile * G * kLanes;
+        for (int idx = tid; idx < G * kLanes; idx += kThreads) s_g[idx] = src[idx];
+    }
+    const int s = c0 + lane;
+    const bool active = lane < kTile && s < T.Nx;
+    R n_c = R(1), ux_c = R(0), uy_c = R(0), T_c = R(1), qx_c = R(0), qy_c = R(0), nu_c = R(0), cS_c = R(0),
+      i5T = R(0.2), ijd = R(0);
+    if (active) {
+        const R *e = static_cast<const R *>(S.eqm[in]) + (size_t)s * kEqM;
+        n_c = e[0]; ux_c = e[1]; uy_c = e[2]; T_c = e[3]; qx_c = e[4]; qy_c = e[5];
+        nu_c = e[6]; cS_c = e[7]; i5T = e[8];
+        ijd = Tabs<R>::ijd(T)[s];
     }
 
-    // ---- (5) reduce the new stage's raw moments and the residual ----
-#pragma unroll
-    for (int m = 0; m < kNumRaw; ++m) sm.red[warp][m][lane] = acc[m];
+    // ---- (2) wall densities (tiles whose stencil reaches a wall) ----
+    const bool needL = c0 == 0;
+    const bool needR = c0 + 33 >= T.Nx;
+    if (needL) block_wall_density<R>(T, Fin, false, s_misc, &s_misc[8]);
+    if (needR) block_wall_density<R>(T, Fin, true, s_misc, &s_misc[9]);
     __syncthreads();
-    for (int idx = tid; idx < kTileCells * kNumRaw; idx += kThreads) {
-        int c = idx % kTileCells, m = idx / kTileCells, sn = c0 + c;
-        double t = 0.0;
-        for (int w2 = 0; w2 < kWarps; ++w2) t += sm.red[w2][m][c];
-        if (sn < T.Nx) S.part[out][((size_t)chunk * kNumRaw + m) * T.Nxp + sn] = t;
+
+    // ---- (3) stream the chunk's velocity rows ----
+    const R ca = R(stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0));
+    const R cb = R(stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0));
+    const R dt = R(T.dt);
+    R *s_vrow = reinterpret_cast<R *>(smem + L.vrow);   // [vchunk][kVRow]
+    {
+        const R nwL = R(needL ? s_misc[8] : 0.0), nwR = R(needR ? s_misc[9] : 0.0);
+        const R *vel = Tabs<R>::vel(T);
+        for (int k = tid; k < vend - vbeg; k += kThreads) {
+            const int v = vbeg + k;
+            R *x = s_vrow + k * kVRow;
+            const R fr = vel[VC_FR * V + v];
+            x[VR_PX] = vel[VC_PX * V + v];
+            x[VR_PY] = vel[VC_PY * V + v];
+            x[VR_W] = vel[VC_W * V + v];
+            x[VR_FR] = fr;
+            x[VR_INL0] = nwL * vel[VC_FWL * V + v] - fr;
+            x[VR_INL1] = nwL * vel[VC_FWLT * V + v] - fr;
+            x[VR_INR0] = nwR * vel[VC_FWR * V + v] - fr;
+            x[VR_INR1] = nwR * vel[VC_FWRT * V + v] - fr;
+            x[VR_A] = R(T.vel_aj[v]);       // small integers, exact in either precision
+            x[VR_J] = R(T.vel_aj[V + v]);
+        }
+    }
+    __syncthreads();
+    const bool wall = needL || needR;
+    const int ck = lane + 3 + off;          // column of node c0 + lane
+
+    R acc[kNumRaw];
+#pragma unroll
+    for (int m = 0; m < kNumRaw; ++m) acc[m] = R(0);
+    R res = R(0);
+    bool timed_out = false;
+
+    for (int sub = 0; sub < nsub; ++sub) {
+        const int p = sub % kPipe;
+        if (!mbar_wait(&bar[p], (uint32_t)((sub / kPipe) & 1))) timed_out = true;
+        if (__syncthreads_or(timed_out)) {
+            timed_out = true;
+            break;
+        }
+        R *fin = s_fin + (size_t)p * 2 * kSubV * kRowLen;
+        const R *f0 = s_f0 + (size_t)p * 2 * kSubV * kF0Len;
+        // the warp's two velocities (rows warp and warp + kWarps) are processed
+        // together: four independent WENO-5 chains per lane
+        constexpr int NQ = kSubV / kWarps;
+        int kq[NQ];
+        bool ok[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            kq[q] = sub * kSubV + warp + kWarps * q;
+            ok[q] = vbeg + kq[q] < vend;
+            if (!ok[q]) kq[q] = sub * kSubV + warp;   // duplicate a valid row; results are discarded
+        }
+        if (wall) {
+            // ghost nodes: lanes 0-15 -> (velocity, field, side, node)
+            if (lane < 8 * NQ) {
+                const int q = lane >> 3, fld = (lane >> 2) & 1, side = (lane >> 1) & 1, gi = lane & 1;
+                const int r = warp + kWarps * q;
+                const R *x = s_vrow + kq[q] * kVRow;
+                const bool pos = (int)x[VR_A] < T.Qx;
+                R *row = fin + (size_t)(fld * kSubV + r) * kRowLen;
+                if (ok[q] && side == 0 && needL) {        // nodes -1 (gi 0), -2 (gi 1)
+                    R g;
+                    if (pos) g = x[VR_INL0 + fld];
+                    else {
+                        const int cz = -x0;      // column of node 0
+                        R f1 = row[cz], f2 = row[cz + 1], f3 = row[cz + 2], f4 = row[cz + 3];
+                        g = gi == 0 ? R(4) * f1 - R(6) * f2 + R(4) * f3 - f4
+                                    : R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
+                    }
+                    row[-1 - gi - x0] = g;
+                } else if (ok[q] && side == 1 && needR) { // nodes Nx (gi 0), Nx+1 (gi 1)
+                    R g;
+                    if (!pos) g = x[VR_INR0 + fld];
+                    else {
+                        const int cl = T.Nx - 1 - x0;
+                        R f1 = row[cl], f2 = row[cl - 1], f3 = row[cl - 2], f4 = row[cl - 3];
+                        g = gi == 0 ? R(4) * f1 - R(6) * f2 + R(4) * f3 - f4
+                                    : R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
+                    }
+                    const int colR = T.Nx + gi - x0;   // beyond the box only if never referenced
+                    if (colR < kRowLen) row[colR] = g;
+                }
+            }
+            __syncwarp();
+        }
+        R fl[NQ][2], dd[NQ][2];
+        bool posq[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const R *x = s_vrow + kq[q] * kVRow;
+            posq[q] = (int)x[VR_A] < T.Qx;
+            const int base = posq[q] ? ck - 3 : ck + 2, st = posq[q] ? 1 : -1;   // upwind stencil order
+#pragma unroll
+            for (int fld = 0; fld < 2; ++fld) {
+                const R *row = fin + (size_t)(fld * kSubV + warp + kWarps * q) * kRowLen;
+                // face c0 + lane (left of node c0 + lane)
+                fl[q][fld] = weno5<R>(row[base], row[base + st], row[base + 2 * st], row[base + 3 * st],
+                                      row[base + 4 * st]);
+                dd[q][fld] = row[ck];
+                if (wall) {
+                    if (posq[q] && s == 0) fl[q][fld] = x[VR_INL0 + fld];
+                    if (!posq[q] && s == T.Nx) fl[q][fld] = x[VR_INR0 + fld];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const R *x = s_vrow + kq[q] * kVRow;
+            const int a = (int)x[VR_A], j = (int)x[VR_J], r = warp + kWarps * q, v = vbeg + kq[q];
+            const R px = x[VR_PX], py = x[VR_PY], w = x[VR_W], fr = x[VR_FR];
+            const R feq = n_c * s_g[a * kLanes + lane] * s_g[(2 * T.Qx + j) * kLanes + lane];
+            const R xx = px - ux_c, xy = py - uy_c;
+            const R qxi = qx_c * xx + qy_c * xy;
+            const R x2 = (xx * xx + xy * xy) * i5T;
+            R fo[2];
+#pragma unroll
+            for (int fld = 0; fld < 2; ++fld) {
+                const R frt = __shfl_down_sync(0xffffffffu, fl[q][fld], 1);
+                const R d = dd[q][fld];
+                const R adv = -px * (frt - fl[q][fld]) * ijd;
+                // Shakhov target minus the rest state
+                const R tgt = fld ? T_c * feq * (R(1) + cS_c * (x2 - R(0.4)) * qxi) - fr
+                                  : feq * (R(1) + cS_c * (x2 - R(0.8)) * qxi) - fr;
+                R dn = d + dt * (adv - nu_c * (d - tgt));
+                if (stage > 0) {
+                    const R d0 = f0[(fld * kSubV + r) * kF0Len + lane + offf];
+                    dn = ca * d0 + cb * dn;
+                    if (stage == 2 && active && ok[q]) res = fmax(res, w * fabs(dn - d0));
+                }
+                if (active && ok[q]) Fout[fld * fstride + (size_t)v * T.Nxp + s] = dn;
+                fo[fld] = dn;
+            }
+            if (active && ok[q]) {
+                const R fw = w * fo[0], gw = w * fo[1];
+                const R e2 = xx * xx + xy * xy;
+                acc[R_S0] += fw;
+                acc[R_SX] += xx * fw;
+                acc[R_SY] += xy * fw;
+                acc[R_SXX] += xx * xx * fw;
+                acc[R_SXY] += xx * xy * fw;
+                acc[R_SYY] += xy * xy * fw;
+                acc[R_CZ] += gw;
+                acc[R_R3X] += e2 * xx * fw;
+                acc[R_R3Y] += e2 * xy * fw;
+                acc[R_GX] += xx * gw;
+                acc[R_GY] += xy * gw;
+            }
+        }
+        // order this thread's generic accesses to buffer p before the next TMA write into it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();   // every warp is done with buffer p
+        if (tid == 0 && sub + kPipe < nsub) issue(sub + kPipe);
+    }
+
+    if (timed_out) {
+        // give up: record it, let in-flight copies land (bounded), then leave
+        if (tid == 0) {
+            atomicExch(&S.ctl->timeout, 1);
+            for (int p = 0; p < kPipe; ++p) {
+                mbar_wait(&bar[p], 0);
+                mbar_wait(&bar[p], 1);
+            }
+        }
+        return;
+    }
+
+    // ---- (4) publish the chunk's raw moment partials and the residual ----
+    R *s_red = reinterpret_cast<R *>(smem + L.pipe);   // [kWarps][kNumRaw][kLanes]
+#pragma unroll
+    for (int m = 0; m < kNumRaw; ++m) s_red[(warp * kNumRaw + m) * kLanes + lane] = acc[m];
+    __syncthreads();
+    R *part = static_cast<R *>(S.part[out]);
+    for (int idx = tid; idx < kLanes * kNumRaw; idx += kThreads) {
+        const int c = idx & 31, m = idx >> 5, sn = c0 + c;
+        CSum<R> t;
+        for (int w2 = 0; w2 < kWarps; ++w2) t.add(s_red[(w2 * kNumRaw + m) * kLanes + c]);
+        if (c < kTile && sn < T.Nx) part[((size_t)chunk * kNumRaw + m) * T.Nxp + sn] = t.value();
     }
     if (chunk == 0 && active) {
-        S.shift[out][s] = ux_c;
-        S.shift[out][T.Nxp + s] = uy_c;
+        R *sh = static_cast<R *>(S.shift[out]);
+        sh[s] = ux_c;
+        sh[T.Nxp + s] = uy_c;
     }
-    if (bad) S.ctl->nonfinite = 1;
     if (stage == 2) {
-        for (int o = 16; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
-        if (lane == 0 && res > 0.0) atomicMax(&S.resid[step % kResidRing], (unsigned long long)__double_as_longlong(res));
+        R rr = res;
+        for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+        if (lane == 0 && rr > R(0))
+            atomicMax(&S.resid[step % kResidRing], (unsigned long long)__double_as_longlong((double)rr));
+    }
+
+    // ---- the last chunk CTA of this tile builds the next stage's tile data ----
+    __threadfence();
+    __syncthreads();
+    int *flag = reinterpret_cast<int *>(&s_misc[10]);
+    if (tid == 0) *flag = atomicAdd(&S.count[out][tile], 1) == T.nchunk - 1;
+    __syncthreads();
+    if (*flag) {
+        __threadfence();
+        tile_equilibrium<R>(T, S, out, tile, smem + L.pipe);
+        if (tid == 0) S.count[out][tile] = 0;
     }
 }
 
-// Raw moment sums (shift 0) of state buffer `buf`.
+// Stage data of every tile of buffer `buf` (after set-up or lbc_set_state).
+template <typename R>
+__global__ void __launch_bounds__(kThreads) tile_equilibrium_kernel(DevTables T, DevState S, int buf)
+{
+    extern __shared__ __align__(16) unsigned char smem_eq[];
+    tile_equilibrium<R>(T, S, buf, blockIdx.x, smem_eq);
+}
+
+// Raw moment sums (shift 0) of the deviation in buffer `buf`, per velocity chunk.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) moments_partial_kernel(DevTables T, DevState S, int buf)
 {
-    __shared__ double red[kWarps][kNumRaw][kTileCells];
+    __shared__ double red[kWarps][kNumRaw][kLanes];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c0 = blockIdx.x * kTileCells, chunk = blockIdx.y, s = c0 + lane;
-    const bool active = s < T.Nx;
+    const int c0 = blockIdx.x * kTile, chunk = blockIdx.y, s = c0 + lane;
+    const bool active = lane < kTile && s < T.Nx;
     const R *F = static_cast<const R *>(S.F[buf]);
     const size_t fstride = (size_t)T.V * T.Nxp;
     double acc[kNumRaw];
@@ -415,12 +747,10 @@ __global__ void __launch_bounds__(kThreads) moments_partial_kernel(DevTables T, 
     for (int m = 0; m < kNumRaw; ++m) acc[m] = 0.0;
     const int vbeg = chunk * T.vchunk, vend = min(T.V, vbeg + T.vchunk);
     for (int v = vbeg + warp; v < vend && active; v += kWarps) {
-        double px, py, w;
-        int a, j;
-        velocity(T, v, px, py, w, a, j);
-        double fw = w * (double)F[(size_t)v * T.Nxp + s];
-        double gw = w * (double)F[fstride + (size_t)v * T.Nxp + s];
-        double e2 = px * px + py * py;
+        const double px = T.d_vel[VC_PX * T.V + v], py = T.d_vel[VC_PY * T.V + v], w = T.d_vel[VC_W * T.V + v];
+        const double fw = w * (double)F[(size_t)v * T.Nxp + s];
+        const double gw = w * (double)F[fstride + (size_t)v * T.Nxp + s];
+        const double e2 = px * px + py * py;
         acc[R_S0] += fw; acc[R_SX] += px * fw; acc[R_SY] += py * fw;
         acc[R_SXX] += px * px * fw; acc[R_SXY] += px * py * fw; acc[R_SYY] += py * py * fw;
         acc[R_CZ] += gw; acc[R_R3X] += e2 * px * fw; acc[R_R3Y] += e2 * py * fw;
@@ -429,42 +759,37 @@ __global__ void __launch_bounds__(kThreads) moments_partial_kernel(DevTables T, 
 #pragma unroll
     for (int m = 0; m < kNumRaw; ++m) red[warp][m][lane] = acc[m];
     __syncthreads();
-    for (int idx = tid; idx < kTileCells * kNumRaw; idx += kThreads) {
-        int c = idx % kTileCells, m = idx / kTileCells, sn = c0 + c;
+    R *part = static_cast<R *>(S.part[buf]);
+    for (int idx = tid; idx < kLanes * kNumRaw; idx += kThreads) {
+        const int c = idx & 31, m = idx >> 5, sn = c0 + c;
         double t = 0.0;
         for (int w2 = 0; w2 < kWarps; ++w2) t += red[w2][m][c];
-        if (sn < T.Nx) S.part[buf][((size_t)chunk * kNumRaw + m) * T.Nxp + sn] = t;
+        if (c < kTile && sn < T.Nx) part[((size_t)chunk * kNumRaw + m) * T.Nxp + sn] = R(t);
     }
     if (chunk == 0 && active) {
-        S.shift[buf][s] = 0.0;
-        S.shift[buf][T.Nxp + s] = 0.0;
+        R *sh = static_cast<R *>(S.shift[buf]);
+        sh[s] = R(0);
+        sh[T.Nxp + s] = R(0);
     }
 }
 
 template <typename R>
-__global__ void init_rest_kernel(DevTables T, DevState S)
-{
-    R *F = static_cast<R *>(S.F[0]);
-    const size_t n = (size_t)T.V * T.Nxp;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * n; i += (size_t)gridDim.x * blockDim.x) {
-        size_t k = i % n;
-        int v = (int)(k / T.Nxp), s = (int)(k % T.Nxp);
-        F[i] = s < T.Nx ? R(T.frest[v]) : R(0);
-    }
-}
-
 __global__ void finalize_moments_kernel(DevTables T, DevState S, int buf)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= T.Nx) return;
+    const R *part = static_cast<const R *>(S.part[buf]);
+    const R *shift = static_cast<const R *>(S.shift[buf]);
+    const double sx = (double)shift[s], sy = (double)shift[T.Nxp + s];
     double r[kNumRaw];
+    rest_raw(T.restP, sx, sy, r);
     for (int m = 0; m < kNumRaw; ++m) {
         double acc = 0.0;
-        for (int ch = 0; ch < T.nchunk; ++ch) acc += S.part[buf][((size_t)ch * kNumRaw + m) * T.Nxp + s];
-        r[m] = acc;
+        for (int ch = 0; ch < T.nchunk; ++ch) acc += (double)part[((size_t)ch * kNumRaw + m) * T.Nxp + s];
+        r[m] += acc;
     }
     double mo[10];
-    raw_to_moments(r, S.shift[buf][s], S.shift[buf][T.Nxp + s], mo);
+    raw_to_moments(r, sx, sy, mo);
     for (int k = 0; k < LBC_NMOM; ++k) S.mom_out[(size_t)k * T.Nxp + s] = mo[k];
 }
 
@@ -474,6 +799,7 @@ __global__ void ctl_set_kernel(Ctl *ctl, long long base, long long check_from, i
     ctl->check_from = check_from;
     ctl->stopped = stopped;
     ctl->nonfinite = 0;
+    ctl->timeout = 0;
 }
 
 __global__ void ctl_bump_kernel(Ctl *ctl, long long k) { ctl->base += k; }
@@ -481,18 +807,41 @@ __global__ void ctl_bump_kernel(Ctl *ctl, long long k) { ctl->base += k; }
 }  // namespace
 
 template <typename R>
-cudaError_t configure_kernels()
+size_t stage_smem_bytes(int Qx, int Qy, int N, int K, int vchunk)
 {
-    return cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(StageSmem<R>));
+    return Layout<R>(Qx, Qy, N, K, vchunk).total;
 }
 
 template <typename R>
-cudaError_t launch_stage(const DevTables &T, const DevState &S, int stage, int rel, double stop_eps, cudaStream_t st)
+cudaError_t stage_kernel_attributes(cudaFuncAttributes *fa)
 {
-    size_t smem = sizeof(StageSmem<R>);
+    return cudaFuncGetAttributes(fa, stage_kernel<R>);
+}
+
+template <typename R>
+cudaError_t configure_kernels()
+{
+    const Layout<R> L(kMaxQ, kMaxQ, kMaxQ - 1, kMaxQ, kMaxVChunk);
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(tile_equilibrium_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)EqScratch<R>(kMaxQ, kMaxQ - 1).total);
+}
+
+template <typename R>
+cudaError_t launch_stage(const DevTables &T, const DevState &S, const StateMaps &M, int stage, int rel,
+                         double stop_eps, cudaStream_t st)
+{
+    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.K, T.vchunk);
     dim3 grid(T.ntile, T.nchunk);
-    stage_kernel<R><<<grid, kThreads, smem, st>>>(T, S, stage, rel, stop_eps);
+    stage_kernel<R><<<grid, kThreads, L.total, st>>>(T, S, M, stage, rel, stop_eps);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int buf, cudaStream_t st)
+{
+    tile_equilibrium_kernel<R><<<T.ntile, kThreads, EqScratch<R>(T.K, T.Nxe).total, st>>>(T, S, buf);
     return cudaGetLastError();
 }
 
@@ -505,15 +854,9 @@ cudaError_t launch_moments_partial(const DevTables &T, const DevState &S, int bu
 }
 
 template <typename R>
-cudaError_t launch_init_rest(const DevTables &T, const DevState &S, cudaStream_t st)
-{
-    init_rest_kernel<R><<<304, 256, 0, st>>>(T, S);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_finalize_moments(const DevTables &T, const DevState &S, int buf, cudaStream_t st)
 {
-    finalize_moments_kernel<<<(T.Nx + 127) / 128, 128, 0, st>>>(T, S, buf);
+    finalize_moments_kernel<R><<<(T.Nx + 127) / 128, 128, 0, st>>>(T, S, buf);
     return cudaGetLastError();
 }
 
@@ -529,13 +872,16 @@ cudaError_t launch_ctl_bump(Ctl *ctl, long long k, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template cudaError_t configure_kernels<double>();
-template cudaError_t configure_kernels<float>();
-template cudaError_t launch_stage<double>(const DevTables &, const DevState &, int, int, double, cudaStream_t);
-template cudaError_t launch_stage<float>(const DevTables &, const DevState &, int, int, double, cudaStream_t);
-template cudaError_t launch_moments_partial<double>(const DevTables &, const DevState &, int, cudaStream_t);
-template cudaError_t launch_moments_partial<float>(const DevTables &, const DevState &, int, cudaStream_t);
-template cudaError_t launch_init_rest<double>(const DevTables &, const DevState &, cudaStream_t);
-template cudaError_t launch_init_rest<float>(const DevTables &, const DevState &, cudaStream_t);
+#define LBC_INSTANTIATE(R)                                                                                      \
+    template size_t stage_smem_bytes<R>(int, int, int, int, int);                                                    \
+    template cudaError_t stage_kernel_attributes<R>(cudaFuncAttributes *);                                      \
+    template cudaError_t configure_kernels<R>();                                                                \
+    template cudaError_t launch_stage<R>(const DevTables &, const DevState &, const StateMaps &, int, int, double, \
+                                         cudaStream_t);                                                         \
+    template cudaError_t launch_tile_equilibrium<R>(const DevTables &, const DevState &, int, cudaStream_t);     \
+    template cudaError_t launch_moments_partial<R>(const DevTables &, const DevState &, int, cudaStream_t);      \
+    template cudaError_t launch_finalize_moments<R>(const DevTables &, const DevState &, int, cudaStream_t);
+LBC_INSTANTIATE(float)
+LBC_INSTANTIATE(double)
 
 }  // namespace lbc
