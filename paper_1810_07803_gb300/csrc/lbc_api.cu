@@ -106,7 +106,7 @@ int num_sms()
 }
 
 // CTAs of the stage kernel resident per SM, from registers and shared memory.
-int resident_ctas(bool fp32, int Qx, int Qy, int N, int K, int vchunk)
+int resident_ctas(bool fp32, int Qx, int Qy, int N, int Ny, int K, int vchunk)
 {
     cudaFuncAttributes fa;
     cudaError_t e = fp32 ? stage_kernel_attributes<float>(&fa) : stage_kernel_attributes<double>(&fa);
@@ -114,7 +114,8 @@ int resident_ctas(bool fp32, int Qx, int Qy, int N, int K, int vchunk)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    size_t smem = fp32 ? stage_smem_bytes<float>(Qx, Qy, N, K, vchunk) : stage_smem_bytes<double>(Qx, Qy, N, K, vchunk);
+    size_t smem = fp32 ? stage_smem_bytes<float>(Qx, Qy, N, Ny, K, vchunk)
+                       : stage_smem_bytes<double>(Qx, Qy, N, Ny, K, vchunk);
     int by_regs = e == cudaSuccess && fa.numRegs > 0 ? regs_sm / (fa.numRegs * kThreads) : 2;
     int by_smem = smem_sm > 0 ? (int)(smem_sm / (smem + 1024)) : 2;
     return std::max(1, std::min(by_regs, by_smem));
@@ -281,7 +282,7 @@ lbc_status lbc_create(const lbc_params *params, void *cuda_stream, lbc_solver **
         double best = 1e300;
         for (int nsub = 1; nsub <= subs; ++nsub) {
             int vch = nsub * kSubV, nch = (V + vch - 1) / vch;
-            const int slots = std::max(1, sms * resident_ctas(s->fp32, p.Qx, p.Qy, Nxe, t.K, vch));
+            const int slots = std::max(1, sms * resident_ctas(s->fp32, p.Qx, p.Qy, Nxe, Nye, t.K, vch));
             double waves = std::ceil((double)T.ntile * nch / slots);
             double cost = waves * (vch + 24.0);
             if (cost < best - 1e-9) { best = cost; T.vchunk = vch; T.nchunk = nch; }

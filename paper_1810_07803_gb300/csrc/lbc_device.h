@@ -75,7 +75,7 @@ struct StateMaps {
 };
 
 template <typename R>
-size_t stage_smem_bytes(int Qx, int Qy, int N, int K, int vchunk);
+size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk);
 template <typename R>
 cudaError_t stage_kernel_attributes(cudaFuncAttributes *fa);
 template <typename R>

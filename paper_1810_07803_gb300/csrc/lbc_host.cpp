@@ -203,7 +203,7 @@ bool build_tables(int Qx, int Qy, int Nxe, int Nye, double p0, HostTables &t, st
     t.V = 2 * Qx * Qy;
     // Projection rule: exact for degree < 2K; the Gaussian's modulation needs
     // a margin of nodes beyond the (N+1)/2 that polynomials of degree N need.
-    t.K = std::min(kMaxQ, (Nxe + 2) / 2 + 14);
+    t.K = projection_nodes(Nxe);
     int nrec = std::max(Qx, t.K) + 1;
     if (!half_range_recurrence(nrec, t.alpha, t.sbeta)) { err = "half-range recurrence failed"; return false; }
     if (!gauss_from_recurrence(Qx, t.alpha, t.sbeta, t.zx, t.wx)) { err = "half-range rule failed"; return false; }

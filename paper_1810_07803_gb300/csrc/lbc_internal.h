@@ -9,6 +9,10 @@
 namespace lbc {
 
 constexpr int kMaxQ = 64;          // largest quadrature order accepted
+// nodes of the half-range rule that projects the equilibrium: exact for degree
+// < 2K; (N+1)/2 nodes for the polynomial part plus a margin for exp(a y)
+constexpr int projection_nodes(int N) { return (N + 2) / 2 + 14; }
+constexpr int kMaxK = projection_nodes(kMaxQ - 1);
 constexpr int kNumRaw = 11;        // raw moment sums accumulated per node
 constexpr int kResidRing = 4096;   // per-step residual slots kept on the device
 

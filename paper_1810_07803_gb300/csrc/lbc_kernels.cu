@@ -115,6 +115,97 @@ template <typename R> __device__ __forceinline__ R fdiv(R a, R b);
 template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
 
+// ---- packed FP32 pairs (sm_100+ f32x2 arithmetic): the two reduced
+// distributions phi and chi go through identical arithmetic, so the FP32 path
+// carries them as one packed pair per velocity ----
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 mk2(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ f2 bc2(float x) { return mk2(x, x); }
+__device__ __forceinline__ void un2(f2 a, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ f2 operator+(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 operator-(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 operator*(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)   // a b + c
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;   // hardware reciprocal approximation (MUFU)
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ f2 rcp2(f2 a)
+{
+    float lo, hi;
+    un2(a, lo, hi);
+    return mk2(rcp_approx(lo), rcp_approx(hi));
+}
+__device__ __forceinline__ f2 max2(f2 a, f2 b)
+{
+    float al, ah, bl, bh;
+    un2(a, al, ah);
+    un2(b, bl, bh);
+    return mk2(fmaxf(al, bl), fmaxf(ah, bh));
+}
+
+// WENO-5 (Jiang & Shu) on a packed pair, face between c and d, upwind cell c.
+// Nonlinear weights in product form, d_k prod_{m != k} E_m / sum, with the
+// E_m = (eps + beta_m)^2 first scaled by 1/max E_m (no overflow, two
+// reciprocals per pair instead of four per value).
+__device__ __forceinline__ f2 weno5_2(f2 a, f2 b, f2 c, f2 d, f2 e)
+{
+    const f2 two = bc2(2.f), three = bc2(3.f), four = bc2(4.f), five = bc2(5.f);
+    const f2 q0 = fma2(bc2(11.f), c, fma2(bc2(-7.f), b, two * a));
+    const f2 q1 = fma2(two, d, fma2(five, c, bc2(0.f) - b));
+    const f2 q2 = fma2(five, d, two * c) - e;
+    const f2 t0 = fma2(bc2(-2.f), b, a + c), t1 = fma2(three, c, fma2(bc2(-4.f), b, a));
+    const f2 t2 = fma2(bc2(-2.f), c, b + d), t3 = b - d;
+    const f2 t4 = fma2(bc2(-2.f), d, c + e), t5 = fma2(bc2(-4.f), d, fma2(three, c, e));
+    const f2 k1312 = bc2(13.f / 12.f), k025 = bc2(0.25f), eps = bc2(1e-6f);
+    f2 e0 = fma2(k1312, t0 * t0, fma2(k025, t1 * t1, eps));
+    f2 e1 = fma2(k1312, t2 * t2, fma2(k025, t3 * t3, eps));
+    f2 e2 = fma2(k1312, t4 * t4, fma2(k025, t5 * t5, eps));
+    e0 = e0 * e0;
+    e1 = e1 * e1;
+    e2 = e2 * e2;
+    const f2 s = rcp2(max2(e0, max2(e1, e2)));
+    e0 = e0 * s;
+    e1 = e1 * s;
+    e2 = e2 * s;
+    const f2 a0 = bc2(0.1f) * (e1 * e2), a1 = bc2(0.6f) * (e0 * e2), a2 = bc2(0.3f) * (e0 * e1);
+    const f2 num = fma2(a0, q0, fma2(a1, q1, a2 * q2));
+    const f2 den = bc2(6.f) * (a0 + a1 + a2);
+    return num * rcp2(den);
+}
+
 // WENO-5 (Jiang & Shu) face value between c and d with upwind cell c.
 template <typename R>
 __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
@@ -218,143 +309,205 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 }
 
 // ---- tile stage data ----
+// orders per block of the tabulated recurrence (bounded by shared memory at Q = 64)
+template <typename R> struct OrderBlock { static constexpr int value = sizeof(R) == 4 ? 8 : 4; };
+
 template <typename R>
 struct EqScratch {
-    size_t raw, sc, warp, per_warp, total;
-    __host__ __device__ EqScratch(int K, int N)
+    size_t raw, mo, sc, rpm, bb, cb, H, total;
+    int cstride;
+    __host__ __device__ EqScratch(int K, int N, int Ny)
     {
+        cstride = 2 * (N + 1) + 1;   // odd stride: conflict-free rows per node
         raw = 0;
-        sc = raw + (size_t)kLanes * kNumRaw * sizeof(double);
-        warp = sc + (size_t)kLanes * 8 * sizeof(R);
-        per_warp = ((size_t)K * 16 + 2 * K + 2 * (N + 1)) * sizeof(R);
-        per_warp = (per_warp + 15) / 16 * 16;
-        total = warp + kWarps * per_warp;
+        mo = raw + (size_t)kLanes * kNumRaw * sizeof(R);
+        sc = mo + (size_t)kLanes * 12 * sizeof(R);
+        rpm = sc + (size_t)kLanes * 8 * sizeof(R);
+        bb = rpm + (size_t)kLanes * 2 * K * sizeof(R);
+        cb = bb + (size_t)kLanes * (Ny + 1) * sizeof(R);
+        H = cb + (size_t)kLanes * cstride * sizeof(R);
+        total = H + (size_t)OrderBlock<R>::value * kTile * K * sizeof(R);
     }
 };
 
+// Moments from raw sums about (sx, sy), in the state precision (FP32 path: the
+// partials are FP32 and the equilibrium is built in FP32, so FP64 here would not
+// change the result; FP64 path: FP64 throughout).
+template <typename R>
+__device__ void raw_to_moments_r(const R *r, R sx, R sy, R *m)
+{
+    R n = r[R_S0], in = R(1) / n;
+    R bx = r[R_SX] * in, by = r[R_SY] * in;
+    R pxx = r[R_SXX] - n * bx * bx;
+    R pxy = r[R_SXY] - n * bx * by;
+    R pyy = r[R_SYY] - n * by * by;
+    R pzz = r[R_CZ];
+    R r2 = r[R_SXX] + r[R_SYY], b2 = bx * bx + by * by;
+    R hx = r[R_R3X] - bx * r2 - R(2) * (bx * r[R_SXX] + by * r[R_SXY]) + R(2) * n * bx * b2;
+    R hy = r[R_R3Y] - by * r2 - R(2) * (bx * r[R_SXY] + by * r[R_SYY]) + R(2) * n * by * b2;
+    m[0] = n;
+    m[1] = sx + bx;
+    m[2] = sy + by;
+    m[3] = (pxx + pyy + pzz) * in * R(1.0 / 3.0);
+    m[8] = R(0.5) * hx + R(0.5) * (r[R_GX] - bx * pzz);
+    m[9] = R(0.5) * hy + R(0.5) * (r[R_GY] - by * pzz);
+}
+
 // Stage data of one tile of buffer `buf` (block-wide, all threads): sums the
-// per-chunk raw moment partials, turns them into moments in FP64 (adding the
-// rest state's share), and builds the discrete equilibrium factors of Eqs. gx,
-// gy at every node of the tile (algorithm: see equilibrium_host). Writes
-// eqm[buf] for the tile's nodes and the tile's block of eqg[buf].
+// per-chunk raw moment partials, turns them into moments (adding the rest
+// state's share), and builds the discrete equilibrium factors of Eqs. gx, gy
+// at every node of the tile (algorithm: see equilibrium_host). Writes eqm[buf]
+// for the tile's nodes and the tile's block of eqg[buf].
+// The last CTA of a tile runs this at the end of a stage, so it is organised
+// for latency: every phase spreads over all threads of the block (recurrences
+// per (node, projection node), dot products per (node, order), factors per
+// (node, velocity)).
 template <typename R>
 __device__ void tile_equilibrium(const DevTables &T, const DevState &S, int buf, int tile, unsigned char *scratch)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, c0 = tile * kTile;
-    const int N = T.Nxe, K = T.K, G = 2 * T.Qx + T.Qy;
-    const EqScratch<R> L(K, N);
-    double *raw = reinterpret_cast<double *>(scratch + L.raw);   // [32][kNumRaw]
-    R *sc = reinterpret_cast<R *>(scratch + L.sc);               // [32][8]: sT a a^2/2 uy' T'-1
-    R *H = reinterpret_cast<R *>(scratch + L.warp + warp * L.per_warp);   // [K][16]
-    R *rpm = H + K * 16;                                                  // [2][K]
-    R *cpm = rpm + 2 * K;                                                 // [2][N+1]
+    const int tid = threadIdx.x, c0 = tile * kTile;
+    const int N = T.Nxe, K = T.K, G = 2 * T.Qx + T.Qy, Ny = T.Nye;
+    const EqScratch<R> L(K, N, Ny);
+    R *raw = reinterpret_cast<R *>(scratch + L.raw);    // [32][kNumRaw]
+    R *mo = reinterpret_cast<R *>(scratch + L.mo);      // [32][12]
+    R *sc = reinterpret_cast<R *>(scratch + L.sc);      // [32][8]: sT a a^2/2
+    R *rpm = reinterpret_cast<R *>(scratch + L.rpm);    // [31][2][K]
+    R *bb = reinterpret_cast<R *>(scratch + L.bb);      // [31][Ny+1]   Hermite coefficients of g_y
+    R *cb = reinterpret_cast<R *>(scratch + L.cb);      // [31][cstride] c^+_l, c^-_l
+    R *H = reinterpret_cast<R *>(scratch + L.H);        // [kLB][31 K]  h_l(sqrt(T') Y_k)
+    constexpr int kLB = OrderBlock<R>::value;
     const R *part = static_cast<const R *>(S.part[buf]);
     const R *shift = static_cast<const R *>(S.shift[buf]);
     R *eqm = static_cast<R *>(S.eqm[buf]);
     R *eqg = static_cast<R *>(S.eqg[buf]) + (size_t)tile * G * kLanes;
 
+    // raw sums of the deviation, all chunks
     for (int idx = tid; idx < kLanes * kNumRaw; idx += kThreads) {
         const int c = idx & 31, m = idx >> 5, s = c0 + c;
         CSum<R> acc;
-        if (c < kTile && s < T.Nx)
-            for (int ch = 0; ch < T.nchunk; ++ch) acc.add(__ldcg(&part[((size_t)ch * kNumRaw + m) * T.Nxp + s]));
-        raw[c * kNumRaw + m] = (double)acc.value();
+        if (c < kTile && s < T.Nx) {
+            const R *pp = part + (size_t)m * T.Nxp + s;
+            const size_t cs = (size_t)kNumRaw * T.Nxp;
+            int ch = 0;
+            for (; ch + 4 <= T.nchunk; ch += 4) {   // four loads in flight
+                R v0 = __ldcg(pp + ch * cs), v1 = __ldcg(pp + (ch + 1) * cs);
+                R v2 = __ldcg(pp + (ch + 2) * cs), v3 = __ldcg(pp + (ch + 3) * cs);
+                acc.add(v0); acc.add(v1); acc.add(v2); acc.add(v3);
+            }
+            for (; ch < T.nchunk; ++ch) acc.add(__ldcg(pp + ch * cs));
+        }
+        raw[c * kNumRaw + m] = acc.value();
     }
     __syncthreads();
+    // moments, relaxation data and per-node scalars (thread per node)
     if (tid < kLanes) {
-        const int s = c0 + tid;
-        double m[10];
-        if (tid < kTile && s < T.Nx) {
-            double sx = (double)__ldcg(&shift[s]), sy = (double)__ldcg(&shift[T.Nxp + s]), rr[kNumRaw];
-            rest_raw(T.restP, sx, sy, rr);
-            for (int k = 0; k < kNumRaw; ++k) rr[k] += raw[tid * kNumRaw + k];
-            raw_to_moments(rr, sx, sy, m);
+        const int c = tid, s = c0 + c;
+        const bool live = c < kTile && s < T.Nx;
+        R m[10];
+        if (live) {
+            const R sx = __ldcg(&shift[s]), sy = __ldcg(&shift[T.Nxp + s]);
+            double rd[kNumRaw];
+            rest_raw(T.restP, (double)sx, (double)sy, rd);
+            R rr[kNumRaw];
+            for (int k = 0; k < kNumRaw; ++k) rr[k] = R(rd[k]) + raw[c * kNumRaw + k];
+            raw_to_moments_r<R>(rr, sx, sy, m);
             // a NaN/Inf anywhere in the node's populations reaches its moments
-            if (!isfinite(m[0]) || !isfinite(m[3]) || !isfinite(m[8]) || !isfinite(m[9]) || !(m[0] > 0.0) ||
-                !(m[3] > 0.0))
+            if (!isfinite(m[0]) || !isfinite(m[3]) || !isfinite(m[8]) || !isfinite(m[9]) || !(m[0] > R(0)) ||
+                !(m[3] > R(0)))
                 S.ctl->nonfinite = 1;
         } else {
-            m[0] = 1.0; m[1] = m[2] = 0.0; m[3] = 1.0; m[8] = m[9] = 0.0;
+            m[0] = R(1); m[1] = m[2] = R(0); m[3] = R(1); m[8] = m[9] = R(0);
         }
-        const R n = R(m[0]), ux = R(m[1]), uy = R(m[2]), Tc = R(m[3]);
+        const R n = m[0], ux = m[1], uy = m[2], Tc = m[3];
         const R nu = n * R(T.delta * 1.4142135623730951) * pow(Tc, R(1.0 - T.omega));   // 1/tau, Eq. tau
         const R cS = R(1.0 - T.Pr) / (n * Tc * Tc);                                     // Shakhov prefactor
-        if (tid < kTile && s < T.Nx) {
+        if (live) {
             R *e = eqm + (size_t)s * kEqM;
-            e[0] = n; e[1] = ux; e[2] = uy; e[3] = Tc; e[4] = R(m[8]); e[5] = R(m[9]);
+            e[0] = n; e[1] = ux; e[2] = uy; e[3] = Tc; e[4] = m[8]; e[5] = m[9];
             e[6] = nu; e[7] = cS; e[8] = R(1) / (R(5) * Tc);
         }
         const R ip0 = R(1.0 / T.p0), Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
-        R *x = sc + tid * 8;
-        x[0] = sT; x[1] = a; x[2] = R(0.5) * a * a; x[3] = uy * ip0; x[4] = Tp - R(1);
+        R *x = sc + c * 8;
+        x[0] = sT; x[1] = a; x[2] = R(0.5) * a * a;
+        // g_y coefficients b_l = E[He_l(u' + sqrt(T') Y)] / l!: b_{l+1} = (u' b_l + (T'-1) b_{l-1}) / (l+1)
+        if (c < kTile) {
+            const R uq = uy * ip0, tm1 = Tp - R(1);
+            R *b = bb + c * (Ny + 1);
+            R bm = R(1), bl = uq;
+            b[0] = R(1);
+            if (Ny >= 1) b[1] = uq;
+            for (int l = 1; l < Ny; ++l) {
+                const R bn = (uq * bl + tm1 * bm) * Tabs<R>::inv_l(T, l + 1);
+                bm = bl;
+                bl = bn;
+                b[l + 1] = bn;
+            }
+        }
     }
     __syncthreads();
-
-    const R *alpha = Tabs<R>::alpha(T), *Yk = Tabs<R>::Yk(T), *Wk = Tabs<R>::Wk(T);
-    const R *hz = Tabs<R>::hz(T), *He = Tabs<R>::He(T);
-    const R h0 = R(1.0 / T.sbeta[0]);
-    for (int c = warp; c < kTile; c += kWarps) {
+    // weights r_k^{+-} = W_k exp(+-a Y_k - a^2/2) of every (node, projection node)
+    const R *Yk = Tabs<R>::Yk(T), *Wk = Tabs<R>::Wk(T);
+    for (int idx = tid; idx < kTile * K; idx += kThreads) {
+        const int c = idx / K, k = idx - c * K;
         const R *x = sc + c * 8;
-        const R sT = x[0], a = x[1], ha = x[2], uq = x[3], tm1 = x[4];
-        // lanes over projection nodes k: weights r_k^{+-} and the recurrence state
-        R zt[2], h[2], hp[2];
+        const R Y = Yk[k], W = Wk[k];
+        rpm[(c * 2) * K + k] = W * exp(x[1] * Y - x[2]);
+        rpm[(c * 2 + 1) * K + k] = W * exp(-x[1] * Y - x[2]);
+    }
+    // projection coefficients c^{+-}_l = sum_k r_k^{+-} h_l(sqrt(T') Y_k), in blocks of kLB orders:
+    // recurrence state per (node, projection node) kept in registers across blocks
+    constexpr int kItems = (kTile * kMaxK + kThreads - 1) / kThreads;
+    R zt[kItems], h[kItems], hp[kItems];
+    const R *alpha = Tabs<R>::alpha(T);
+    const R h0 = R(1.0 / T.sbeta[0]);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            int k = lane + 32 * q;
-            R Y = k < K ? Yk[k] : R(0);
-            zt[q] = sT * Y;
-            if (k < K) {
-                rpm[k] = Wk[k] * exp(a * Y - ha);
-                rpm[K + k] = Wk[k] * exp(-a * Y - ha);
-            }
-            h[q] = h0;
-            hp[q] = R(0);
-        }
-        for (int lb = 0; lb <= N; lb += 16) {
-            const int le = min(N, lb + 15);
-            for (int l = lb; l <= le; ++l) {
-                const R al = alpha[l], sb = Tabs<R>::sbeta(T, l), isb1 = Tabs<R>::isbeta(T, l + 1);
+    for (int it = 0; it < kItems; ++it) {
+        const int idx = tid + it * kThreads;
+        const int c = idx / K, k = idx - c * K;
+        zt[it] = R(0);
+        if (idx < kTile * K) zt[it] = sc[c * 8] * Yk[k];
+        h[it] = h0;
+        hp[it] = R(0);
+    }
+    for (int lb = 0; lb <= N; lb += kLB) {
+        const int le = min(N, lb + kLB - 1);
+        for (int l = lb; l <= le; ++l) {
+            const R al = alpha[l], sb = Tabs<R>::sbeta(T, l), isb1 = Tabs<R>::isbeta(T, l + 1);
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    int k = lane + 32 * q;
-                    if (k < K) H[k * 16 + (l - lb)] = h[q];
-                    R hn = ((zt[q] - al) * h[q] - sb * hp[q]) * isb1;
-                    hp[q] = h[q];
-                    h[q] = hn;
-                }
+            for (int it = 0; it < kItems; ++it) {
+                const int idx = tid + it * kThreads;
+                if (idx < kTile * K) H[(l - lb) * kTile * K + idx] = h[it];
+                const R hn = ((zt[it] - al) * h[it] - sb * hp[it]) * isb1;
+                hp[it] = h[it];
+                h[it] = hn;
             }
-            __syncwarp();
-            // lanes 0-15: c^+_l, lanes 16-31: c^-_l, l = lb + (lane % 16)
-            const int l = lb + (lane & 15), sgn = lane >> 4;
-            if (l <= le) {
-                Dot<R> d;
-                for (int k = 0; k < K; ++k) d.add(rpm[sgn * K + k], H[k * 16 + (lane & 15)]);
-                cpm[sgn * (N + 1) + l] = d.value();
-            }
-            __syncwarp();
         }
-        for (int i = lane; i < 2 * T.Qx; i += 32) {
+        __syncthreads();
+        const int nl = le - lb + 1;
+        for (int idx = tid; idx < kTile * 2 * nl; idx += kThreads) {
+            const int c = idx / (2 * nl), rem = idx - c * 2 * nl, sgn = rem / nl, jl = rem - sgn * nl;
+            const R *r = rpm + (c * 2 + sgn) * K, *hh = H + jl * kTile * K + c * K;
+            Dot<R> d;
+            for (int k = 0; k < K; ++k) d.add(r[k], hh[k]);
+            cb[c * L.cstride + sgn * (N + 1) + lb + jl] = d.value();
+        }
+        __syncthreads();
+    }
+    // factors: g_x/w at (node, a), g_y/w at (node, j); node fastest for coalesced stores
+    const R *hz = Tabs<R>::hz(T), *He = Tabs<R>::He(T);
+    for (int idx = tid; idx < G * kTile; idx += kThreads) {
+        const int i = idx / kTile, c = idx - i * kTile;
+        Dot<R> d;
+        if (i < 2 * T.Qx) {
             const int ii = i < T.Qx ? i : i - T.Qx;
-            const R *cc = cpm + (i < T.Qx ? 0 : N + 1);
-            Dot<R> d;
+            const R *cc = cb + c * L.cstride + (i < T.Qx ? 0 : N + 1);
             for (int l = 0; l <= N; ++l) d.add(hz[l * T.Qx + ii], cc[l]);
-            eqg[(size_t)i * kLanes + c] = d.value();
+        } else {
+            const int jj = i - 2 * T.Qx;
+            const R *b = bb + c * (Ny + 1);
+            for (int l = 0; l <= Ny; ++l) d.add(He[l * T.Qy + jj], b[l]);
         }
-        // g_y: b_{l+1} = (u' b_l + (T'-1) b_{l-1}) / (l+1), g_y,j = sum_l He_l(y_j) b_l
-        for (int jj = lane; jj < T.Qy; jj += 32) {
-            R bm = R(1), b = uq;
-            Dot<R> d;
-            d.add(He[jj], R(1));
-            if (T.Nye >= 1) d.add(He[T.Qy + jj], b);
-            for (int l = 1; l < T.Nye; ++l) {
-                R bn = (uq * b + tm1 * bm) * Tabs<R>::inv_l(T, l + 1);
-                bm = b;
-                b = bn;
-                d.add(He[(l + 1) * T.Qy + jj], b);
-            }
-            eqg[(size_t)(2 * T.Qx + jj) * kLanes + c] = d.value();
-        }
-        __syncwarp();
+        eqg[(size_t)i * kLanes + c] = d.value();
     }
 }
 
@@ -405,7 +558,7 @@ enum { VR_PX = 0, VR_PY, VR_W, VR_FR, VR_INL0, VR_INL1, VR_INR0, VR_INR1, VR_A, 
 template <typename R>
 struct Layout {
     size_t bar, pipe, fin, f0, g, vrow, misc, total;
-    __host__ __device__ Layout(int Qx, int Qy, int N, int K, int vchunk)
+    __host__ __device__ Layout(int Qx, int Qy, int N, int Ny, int K, int vchunk)
     {
         size_t o = 0;
         bar = o;  o = al(o + kPipe * sizeof(uint64_t));
@@ -414,7 +567,7 @@ struct Layout {
         f0 = fin + (size_t)kPipe * 2 * kSubV * kRowLen * sizeof(R);
         size_t pipe_bytes = f0 + (size_t)kPipe * 2 * kSubV * kF0Len * sizeof(R) - pipe;
         size_t red_bytes = (size_t)kWarps * kNumRaw * kLanes * sizeof(R);
-        size_t eq_bytes = EqScratch<R>(K, N).total;
+        size_t eq_bytes = EqScratch<R>(K, N, Ny).total;
         size_t m = pipe_bytes > red_bytes ? pipe_bytes : red_bytes;
         m = m > eq_bytes ? m : eq_bytes;
         o = al(o + m);
@@ -434,7 +587,7 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // TMA destinations want 128-byte aligned shared memory: align the base explicitly
     unsigned char *smem = smem_dyn + ((128 - (smem_addr(smem_dyn) & 127)) & 127);
-    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.K, T.vchunk);
+    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
     R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][2][kSubV][kRowLen]
     R *s_f0 = reinterpret_cast<R *>(smem + L.f0);         // [kPipe][2][kSubV][kF0Len]
@@ -606,67 +759,135 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
             }
             __syncwarp();
         }
-        R fl[NQ][2], dd[NQ][2];
-        bool posq[NQ];
+        if constexpr (std::is_same<R, float>::value) {
+            // FP32: (phi, chi) as packed pairs
+            f2 fl[NQ], dd[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const R *x = s_vrow + kq[q] * kVRow;
-            posq[q] = (int)x[VR_A] < T.Qx;
-            const int base = posq[q] ? ck - 3 : ck + 2, st = posq[q] ? 1 : -1;   // upwind stencil order
+            for (int q = 0; q < NQ; ++q) {
+                const R *x = s_vrow + kq[q] * kVRow;
+                const bool pos = (int)x[VR_A] < T.Qx;
+                const int base = pos ? ck - 3 : ck + 2, st = pos ? 1 : -1;   // upwind stencil order
+                const R *r0 = fin + (size_t)(warp + kWarps * q) * kRowLen;
+                const R *r1 = fin + (size_t)(kSubV + warp + kWarps * q) * kRowLen;
+                f2 v[5];
 #pragma unroll
-            for (int fld = 0; fld < 2; ++fld) {
-                const R *row = fin + (size_t)(fld * kSubV + warp + kWarps * q) * kRowLen;
-                // face c0 + lane (left of node c0 + lane)
-                fl[q][fld] = weno5<R>(row[base], row[base + st], row[base + 2 * st], row[base + 3 * st],
-                                      row[base + 4 * st]);
-                dd[q][fld] = row[ck];
+                for (int i = 0; i < 5; ++i) v[i] = mk2(r0[base + i * st], r1[base + i * st]);
+                fl[q] = weno5_2(v[0], v[1], v[2], v[3], v[4]);   // face c0 + lane
+                dd[q] = mk2(r0[ck], r1[ck]);
                 if (wall) {
-                    if (posq[q] && s == 0) fl[q][fld] = x[VR_INL0 + fld];
-                    if (!posq[q] && s == T.Nx) fl[q][fld] = x[VR_INR0 + fld];
+                    if (pos && s == 0) fl[q] = mk2(x[VR_INL0], x[VR_INL1]);
+                    if (!pos && s == T.Nx) fl[q] = mk2(x[VR_INR0], x[VR_INR1]);
                 }
             }
-        }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const R *x = s_vrow + kq[q] * kVRow;
-            const int a = (int)x[VR_A], j = (int)x[VR_J], r = warp + kWarps * q, v = vbeg + kq[q];
-            const R px = x[VR_PX], py = x[VR_PY], w = x[VR_W], fr = x[VR_FR];
-            const R feq = n_c * s_g[a * kLanes + lane] * s_g[(2 * T.Qx + j) * kLanes + lane];
-            const R xx = px - ux_c, xy = py - uy_c;
-            const R qxi = qx_c * xx + qy_c * xy;
-            const R x2 = (xx * xx + xy * xy) * i5T;
-            R fo[2];
-#pragma unroll
-            for (int fld = 0; fld < 2; ++fld) {
-                const R frt = __shfl_down_sync(0xffffffffu, fl[q][fld], 1);
-                const R d = dd[q][fld];
-                const R adv = -px * (frt - fl[q][fld]) * ijd;
-                // Shakhov target minus the rest state
-                const R tgt = fld ? T_c * feq * (R(1) + cS_c * (x2 - R(0.4)) * qxi) - fr
-                                  : feq * (R(1) + cS_c * (x2 - R(0.8)) * qxi) - fr;
-                R dn = d + dt * (adv - nu_c * (d - tgt));
+            for (int q = 0; q < NQ; ++q) {
+                const R *x = s_vrow + kq[q] * kVRow;
+                const int a = (int)x[VR_A], j = (int)x[VR_J], r = warp + kWarps * q, v = vbeg + kq[q];
+                const R px = x[VR_PX], py = x[VR_PY], w = x[VR_W], fr = x[VR_FR];
+                const R feq = n_c * s_g[a * kLanes + lane] * s_g[(2 * T.Qx + j) * kLanes + lane];
+                const R xx = px - ux_c, xy = py - uy_c;
+                const R qxi = qx_c * xx + qy_c * xy;
+                const R x2 = (xx * xx + xy * xy) * i5T;
+                float fll, flh;
+                un2(fl[q], fll, flh);
+                const f2 frt = mk2(__shfl_down_sync(0xffffffffu, fll, 1), __shfl_down_sync(0xffffffffu, flh, 1));
+                const f2 adv = (fl[q] - frt) * bc2(px * ijd);
+                // Shakhov targets minus the rest state: (phi_eq (1 + S_phi), chi_eq (1 + S_chi)) - ft_rest
+                const f2 sh = fma2(bc2(cS_c * qxi), bc2(x2) - mk2(0.8f, 0.4f), bc2(1.f));
+                const f2 tgt = fma2(mk2(feq, T_c * feq), sh, bc2(-fr));
+                f2 dn = fma2(bc2(dt), fma2(bc2(-nu_c), dd[q] - tgt, adv), dd[q]);
+                float o0, o1;
                 if (stage > 0) {
-                    const R d0 = f0[(fld * kSubV + r) * kF0Len + lane + offf];
-                    dn = ca * d0 + cb * dn;
-                    if (stage == 2 && active && ok[q]) res = fmax(res, w * fabs(dn - d0));
+                    const f2 d0 = mk2(f0[r * kF0Len + lane + offf], f0[(kSubV + r) * kF0Len + lane + offf]);
+                    dn = fma2(bc2(ca), d0, bc2(cb) * dn);
+                    if (stage == 2 && active && ok[q]) {
+                        float e0, e1;
+                        un2(dn - d0, e0, e1);
+                        res = fmaxf(res, w * fmaxf(fabsf(e0), fabsf(e1)));
+                    }
                 }
-                if (active && ok[q]) Fout[fld * fstride + (size_t)v * T.Nxp + s] = dn;
-                fo[fld] = dn;
+                un2(dn, o0, o1);
+                if (active && ok[q]) {
+                    Fout[(size_t)v * T.Nxp + s] = o0;
+                    Fout[fstride + (size_t)v * T.Nxp + s] = o1;
+                    const R fw = w * o0, gw = w * o1;
+                    const R e2 = xx * xx + xy * xy;
+                    acc[R_S0] += fw;
+                    acc[R_SX] += xx * fw;
+                    acc[R_SY] += xy * fw;
+                    acc[R_SXX] += xx * xx * fw;
+                    acc[R_SXY] += xx * xy * fw;
+                    acc[R_SYY] += xy * xy * fw;
+                    acc[R_CZ] += gw;
+                    acc[R_R3X] += e2 * xx * fw;
+                    acc[R_R3Y] += e2 * xy * fw;
+                    acc[R_GX] += xx * gw;
+                    acc[R_GY] += xy * gw;
+                }
             }
-            if (active && ok[q]) {
-                const R fw = w * fo[0], gw = w * fo[1];
-                const R e2 = xx * xx + xy * xy;
-                acc[R_S0] += fw;
-                acc[R_SX] += xx * fw;
-                acc[R_SY] += xy * fw;
-                acc[R_SXX] += xx * xx * fw;
-                acc[R_SXY] += xx * xy * fw;
-                acc[R_SYY] += xy * xy * fw;
-                acc[R_CZ] += gw;
-                acc[R_R3X] += e2 * xx * fw;
-                acc[R_R3Y] += e2 * xy * fw;
-                acc[R_GX] += xx * gw;
-                acc[R_GY] += xy * gw;
+        } else {
+            R fl[NQ][2], dd[NQ][2];
+            bool posq[NQ];
+    #pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const R *x = s_vrow + kq[q] * kVRow;
+                posq[q] = (int)x[VR_A] < T.Qx;
+                const int base = posq[q] ? ck - 3 : ck + 2, st = posq[q] ? 1 : -1;   // upwind stencil order
+    #pragma unroll
+                for (int fld = 0; fld < 2; ++fld) {
+                    const R *row = fin + (size_t)(fld * kSubV + warp + kWarps * q) * kRowLen;
+                    // face c0 + lane (left of node c0 + lane)
+                    fl[q][fld] = weno5<R>(row[base], row[base + st], row[base + 2 * st], row[base + 3 * st],
+                                          row[base + 4 * st]);
+                    dd[q][fld] = row[ck];
+                    if (wall) {
+                        if (posq[q] && s == 0) fl[q][fld] = x[VR_INL0 + fld];
+                        if (!posq[q] && s == T.Nx) fl[q][fld] = x[VR_INR0 + fld];
+                    }
+                }
+            }
+    #pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const R *x = s_vrow + kq[q] * kVRow;
+                const int a = (int)x[VR_A], j = (int)x[VR_J], r = warp + kWarps * q, v = vbeg + kq[q];
+                const R px = x[VR_PX], py = x[VR_PY], w = x[VR_W], fr = x[VR_FR];
+                const R feq = n_c * s_g[a * kLanes + lane] * s_g[(2 * T.Qx + j) * kLanes + lane];
+                const R xx = px - ux_c, xy = py - uy_c;
+                const R qxi = qx_c * xx + qy_c * xy;
+                const R x2 = (xx * xx + xy * xy) * i5T;
+                R fo[2];
+    #pragma unroll
+                for (int fld = 0; fld < 2; ++fld) {
+                    const R frt = __shfl_down_sync(0xffffffffu, fl[q][fld], 1);
+                    const R d = dd[q][fld];
+                    const R adv = -px * (frt - fl[q][fld]) * ijd;
+                    // Shakhov target minus the rest state
+                    const R tgt = fld ? T_c * feq * (R(1) + cS_c * (x2 - R(0.4)) * qxi) - fr
+                                      : feq * (R(1) + cS_c * (x2 - R(0.8)) * qxi) - fr;
+                    R dn = d + dt * (adv - nu_c * (d - tgt));
+                    if (stage > 0) {
+                        const R d0 = f0[(fld * kSubV + r) * kF0Len + lane + offf];
+                        dn = ca * d0 + cb * dn;
+                        if (stage == 2 && active && ok[q]) res = fmax(res, w * fabs(dn - d0));
+                    }
+                    if (active && ok[q]) Fout[fld * fstride + (size_t)v * T.Nxp + s] = dn;
+                    fo[fld] = dn;
+                }
+                if (active && ok[q]) {
+                    const R fw = w * fo[0], gw = w * fo[1];
+                    const R e2 = xx * xx + xy * xy;
+                    acc[R_S0] += fw;
+                    acc[R_SX] += xx * fw;
+                    acc[R_SY] += xy * fw;
+                    acc[R_SXX] += xx * xx * fw;
+                    acc[R_SXY] += xx * xy * fw;
+                    acc[R_SYY] += xy * xy * fw;
+                    acc[R_CZ] += gw;
+                    acc[R_R3X] += e2 * xx * fw;
+                    acc[R_R3Y] += e2 * xy * fw;
+                    acc[R_GX] += xx * gw;
+                    acc[R_GY] += xy * gw;
+                }
             }
         }
         // order this thread's generic accesses to buffer p before the next TMA write into it
@@ -807,9 +1028,9 @@ __global__ void ctl_bump_kernel(Ctl *ctl, long long k) { ctl->base += k; }
 }  // namespace
 
 template <typename R>
-size_t stage_smem_bytes(int Qx, int Qy, int N, int K, int vchunk)
+size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk)
 {
-    return Layout<R>(Qx, Qy, N, K, vchunk).total;
+    return Layout<R>(Qx, Qy, N, Ny, K, vchunk).total;
 }
 
 template <typename R>
@@ -821,18 +1042,18 @@ cudaError_t stage_kernel_attributes(cudaFuncAttributes *fa)
 template <typename R>
 cudaError_t configure_kernels()
 {
-    const Layout<R> L(kMaxQ, kMaxQ, kMaxQ - 1, kMaxQ, kMaxVChunk);
+    const Layout<R> L(kMaxQ, kMaxQ, kMaxQ - 1, kMaxQ - 1, kMaxK, kMaxVChunk);
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(tile_equilibrium_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)EqScratch<R>(kMaxQ, kMaxQ - 1).total);
+                                (int)EqScratch<R>(kMaxK, kMaxQ - 1, kMaxQ - 1).total);
 }
 
 template <typename R>
 cudaError_t launch_stage(const DevTables &T, const DevState &S, const StateMaps &M, int stage, int rel,
                          double stop_eps, cudaStream_t st)
 {
-    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.K, T.vchunk);
+    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk);
     dim3 grid(T.ntile, T.nchunk);
     stage_kernel<R><<<grid, kThreads, L.total, st>>>(T, S, M, stage, rel, stop_eps);
     return cudaGetLastError();
@@ -841,7 +1062,7 @@ cudaError_t launch_stage(const DevTables &T, const DevState &S, const StateMaps 
 template <typename R>
 cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int buf, cudaStream_t st)
 {
-    tile_equilibrium_kernel<R><<<T.ntile, kThreads, EqScratch<R>(T.K, T.Nxe).total, st>>>(T, S, buf);
+    tile_equilibrium_kernel<R><<<T.ntile, kThreads, EqScratch<R>(T.K, T.Nxe, T.Nye).total, st>>>(T, S, buf);
     return cudaGetLastError();
 }
 
@@ -873,7 +1094,7 @@ cudaError_t launch_ctl_bump(Ctl *ctl, long long k, cudaStream_t st)
 }
 
 #define LBC_INSTANTIATE(R)                                                                                      \
-    template size_t stage_smem_bytes<R>(int, int, int, int, int);                                                    \
+    template size_t stage_smem_bytes<R>(int, int, int, int, int, int);                                                    \
     template cudaError_t stage_kernel_attributes<R>(cudaFuncAttributes *);                                      \
     template cudaError_t configure_kernels<R>();                                                                \
     template cudaError_t launch_stage<R>(const DevTables &, const DevState &, const StateMaps &, int, int, double, \
