@@ -157,6 +157,33 @@ lbc_status lbc_quadrature(int Q, int half_range, double *nodes, double *weights)
 lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, double T,
                            double *gx, double *gy);
 
+/*
+ * Allocation-free stepping (the paper has no counterpart: this serves callers
+ * that cannot allocate device memory, e.g. code embedded in an application
+ * whose own allocator owns the GPU memory, or latency-critical loops where the
+ * implicit synchronisation of an allocation is not acceptable).
+ *
+ * Advances nsteps >= 0 RK-3 steps of the problem `params` (same validation and
+ * discretisation as lbc_create) on a state the caller owns:
+ *   d_state: DEVICE pointer to the weight-divided state, float64 [2][V][Nx]
+ *            (the layout of lbc_get_state), read at entry and overwritten with
+ *            the result. It is not aligned beyond 8 bytes by requirement.
+ *   cuda_stream: a cudaStream_t or NULL (legacy default stream).
+ * All other working memory (tables, RK buffers, moment partials, control
+ * block) lives in one static device array of 8 MiB inside the library, which
+ * every GPU that loads the library holds until the process exits. Problems
+ * whose working set does not fit return LBC_EINVAL with the size needed.
+ * Calls no cudaMalloc/cudaFree or other allocating routine. The first call on
+ * each device resolves the array's device address (cudaGetSymbolAddress) and
+ * sets kernel attributes; make that first call before any stream capture on
+ * that device. Every call shares the array and clears what must start at zero;
+ * calls whose GPU work overlaps (other streams or threads) race on it and must
+ * be serialised by the caller. Returns after the work has finished
+ * (synchronises the stream).
+ * Errors: LBC_EINVAL, LBC_ECUDA, LBC_ENONFINITE, LBC_ETIMEOUT.
+ */
+lbc_status lbc_step_noalloc(const lbc_params *params, double *d_state, long nsteps, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

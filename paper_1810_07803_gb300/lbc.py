@@ -87,6 +87,7 @@ def lib():
         L.lbc_last_error.restype = C.c_char_p
         L.lbc_quadrature.argtypes = [C.c_int, C.c_int, dp, dp]
         L.lbc_equilibrium.argtypes = [C.POINTER(Params), C.c_double, C.c_double, C.c_double, dp, dp]
+        L.lbc_step_noalloc.argtypes = [C.POINTER(Params), C.c_void_p, C.c_long, vp]
         for name in declared_functions():
             if name not in ("lbc_destroy", "lbc_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -116,6 +117,14 @@ def equilibrium(params: dict, ux: float, uy: float, T: float):
     gy = np.zeros(p.Qy)
     _check(lib().lbc_equilibrium(C.byref(p), ux, uy, T, _dptr(gx), _dptr(gy)))
     return gx, gy
+
+
+def step_noalloc(params: dict, d_state: int, nsteps: int, stream=None) -> None:
+    """lbc_step_noalloc on a caller-owned device buffer (address `d_state`,
+    float64 [2][V][Nx], e.g. a torch CUDA tensor's data_ptr())."""
+    p = make_params(dict(DEFAULTS, **params))
+    st = stream if stream is not None else current_stream_handle()
+    _check(lib().lbc_step_noalloc(C.byref(p), C.c_void_p(d_state), int(nsteps), C.c_void_p(st) if st else None))
 
 
 def current_stream_handle():
