@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="state precision of the timed run (fp32: the headline path)")
     return ap.parse_args()
 
 
@@ -116,6 +118,23 @@ def measured_hbm_peak():
     except (OSError, ValueError):
         pass
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(precision: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1810_07803_gb300", "csrc", "lbc_kernels.cu")
+    prof = os.path.join(ROOT, "profiles", f"stage_kernel_{precision}_c2.md")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fields = dict(ln.split(":", 1) for ln in open(prof).read().splitlines() if ln.count(":") == 1
+                      and ln.split(":", 1)[0].strip() in ("kernel_source_sha256_16", "traffic_bytes_per_launch"))
+        if fields.get("kernel_source_sha256_16", "").strip() != digest:
+            return None
+        return float(fields["traffic_bytes_per_launch"]) if "traffic_bytes_per_launch" in fields else None
+    except (OSError, ValueError):
+        return None
 
 
 def cpu_baseline(seconds_target=12.0):
@@ -197,7 +216,7 @@ def main():
     if world > 1:
         dist.barrier()
 
-    solvers = [lbc.Solver(workloads.c2(d, precision="fp32")) for d in workloads.C2_DELTAS]
+    solvers = [lbc.Solver(workloads.c2(d, precision=args.precision)) for d in workloads.C2_DELTAS]
     V, Nx = solvers[0].V, solvers[0].Nx
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
@@ -230,7 +249,7 @@ def main():
     d2h = len(solvers) * lbc.NMOM * Nx * 8
 
     fp64 = None
-    if not args.no_fp64:
+    if not args.no_fp64 and args.precision == "fp32":
         s64 = [lbc.Solver(workloads.c2(d, precision="fp64")) for d in workloads.C2_DELTAS]
         ms64 = time_steps(s64, max(3, args.steps // 10), 2, flush)
         fp64 = {"value": len(s64) * V * Nx * world / (ms64 / 1e3), "ms_per_step": ms64,
@@ -239,19 +258,21 @@ def main():
             s.close()
 
     peak, peak_kind = measured_hbm_peak()
-    launches_per_step = 3 * len(solvers)
-    achieved = BYTES_PER_UPDATE_FP32 * units / (ms / 1e3) / 1e9
+    launches_per_step = 4 * len(solvers)   # per solve and step: three stage kernels and the step-counter bump
+    bpu = BYTES_PER_UPDATE_FP32 if args.precision == "fp32" else BYTES_PER_UPDATE_FP64
+    achieved = bpu * units / (ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config("fp32"),
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": workload_config(args.precision),
         "e2e": {"value": units * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "path": "per step and solve: lbc_set_state(host f64) + lbc_step(1) + lbc_moments(host)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "stage_kernel<float>", "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": BYTES_PER_UPDATE_FP32 * V * Nx / 3},
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.precision),
+                     "kernel": "stage_kernel<float>" if args.precision == "fp32" else "stage_kernel<double>",
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bpu * V * Nx / 3},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
