@@ -97,28 +97,195 @@ cudaError_t launch_steps(lbc_solver *s, int rel0, int nsteps, double stop_eps)
                    : launch_step_range<double>(s, rel0, nsteps, stop_eps);
 }
 
-int num_sms()
+// Captures kGraphSteps plain steps (no early stop) plus the step-counter bump
+// into one CUDA graph, launched by lbc_step for every full group of steps.
+lbc_status ensure_graph(lbc_solver *s)
 {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 152;
-    return n > 0 ? n : 152;
+    if (s->graph) return LBC_OK;
+    cudaStream_t cap;
+    LBC_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaStream_t keep = s->stream;
+        s->stream = cap;
+        e = launch_steps(s, 0, kGraphSteps, 0.0);
+        if (e == cudaSuccess) e = launch_ctl_bump(s->S.ctl, kGraphSteps, cap);
+        s->stream = keep;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&s->graph, g, 0);
+        cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return fail(LBC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    return LBC_OK;
 }
 
-// CTAs of the stage kernel resident per SM, from registers and shared memory.
-int resident_ctas(bool fp32, int Qx, int Qy, int N, int Ny, int K, int vchunk)
+}  // namespace
+
+namespace lbc {
+
+namespace {
+struct DPiece { const std::vector<double> *src; const double **dst; };
+struct FPiece { const std::vector<double> *src; const float **dst; };
+
+// The device table block: FP64 pieces (each padded to 32 doubles), then FP32
+// copies (each padded to 64 floats), then the velocity index table.
+std::vector<DPiece> dpieces(const ProblemSetup &ps, DevTables &T)
 {
-    cudaFuncAttributes fa;
-    cudaError_t e = fp32 ? stage_kernel_attributes<float>(&fa) : stage_kernel_attributes<double>(&fa);
-    int dev = 0, smem_sm = 0, regs_sm = 65536;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    size_t smem = fp32 ? stage_smem_bytes<float>(Qx, Qy, N, Ny, K, vchunk)
-                       : stage_smem_bytes<double>(Qx, Qy, N, Ny, K, vchunk);
-    int by_regs = e == cudaSuccess && fa.numRegs > 0 ? regs_sm / (fa.numRegs * kThreads) : 2;
-    int by_smem = smem_sm > 0 ? (int)(smem_sm / (smem + 1024)) : 2;
-    return std::max(1, std::min(by_regs, by_smem));
+    const HostTables &t = ps.t;
+    return {{&ps.inv_jdeta, &T.inv_jdeta}, {&t.zx, &T.zx}, {&t.wx, &T.wx}, {&t.yy, &T.yy}, {&t.wy, &T.wy},
+            {&t.alpha, &T.alpha}, {&t.sbeta, &T.sbeta}, {&t.hz, &T.hz}, {&t.Yk, &T.Yk}, {&t.Wk, &T.Wk},
+            {&t.He, &T.He}, {&ps.fwL, &T.fwL}, {&ps.fwR, &T.fwR}, {&ps.frest, &T.frest}, {&ps.vel, &T.d_vel},
+            {&ps.vrow, &T.d_vrow}, {&ps.eqtab, &T.d_eqtab}};
+}
+std::vector<FPiece> fpieces(const ProblemSetup &ps, DevTables &T)
+{
+    const HostTables &t = ps.t;
+    return {{&t.hz, &T.f_hz}, {&t.He, &T.f_He}, {&t.alpha, &T.f_alpha}, {&ps.isb, &T.f_isbeta},
+            {&t.sbeta, &T.f_sbeta}, {&t.Yk, &T.f_Yk}, {&t.Wk, &T.f_Wk}, {&ps.invl, &T.f_inv_l},
+            {&ps.vel, &T.f_vel}, {&ps.inv_jdeta, &T.f_inv_jdeta}, {&ps.vrow, &T.f_vrow}, {&ps.eqtab, &T.f_eqtab}};
+}
+size_t pad_d(size_t n) { return (n + 31) / 32 * 32; }
+size_t pad_f(size_t n) { return (n + 63) / 64 * 64; }
+}  // namespace
+
+bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std::string &err)
+{
+    if (!build_tables(p.Qx, p.Qy, Nxe, Nye, p.p0, ps.t, err)) return false;
+    const HostTables &t = ps.t;
+    ps.Nxe = Nxe;
+    ps.Nye = Nye;
+    const int V = t.V;
+    if (V > kMaxV) {
+        err = "velocity set 2 Qx Qy = " + std::to_string(V) + " exceeds " + std::to_string(kMaxV);
+        return false;
+    }
+    make_grid(p.Nx, p.stretch_A, ps.x, ps.inv_jdeta, ps.deta, ps.min_jdeta);
+
+    // time step: CFL on the smallest cell, and half the smallest relaxation time
+    double dt = p.dt > 0 ? p.dt : p.cfl * ps.min_jdeta / (t.zx.back() * p.p0);
+    if (p.dt <= 0 && p.delta > 0)
+        for (double Tw : {1.0, p.T_left, p.T_right})
+            dt = std::min(dt, 0.5 * std::pow(Tw, p.omega - 1.0) / (p.delta * std::sqrt(2.0)));
+    ps.dt = dt;
+
+    // wall Maxwellians (unit density), incoming unit fluxes, rest Maxwellian
+    std::vector<double> gx(2 * p.Qx), gy(p.Qy);
+    ps.fwL.resize(V); ps.fwR.resize(V); ps.frest.resize(V);
+    equilibrium_host(t, 0.0, p.u_left, p.T_left, gx.data(), gy.data());
+    for (int v = 0; v < V; ++v) ps.fwL[v] = gx[v / p.Qy] * gy[v % p.Qy];
+    equilibrium_host(t, 0.0, p.u_right, p.T_right, gx.data(), gy.data());
+    for (int v = 0; v < V; ++v) ps.fwR[v] = gx[v / p.Qy] * gy[v % p.Qy];
+    equilibrium_host(t, 0.0, 0.0, 1.0, gx.data(), gy.data());
+    for (int v = 0; v < V; ++v) ps.frest[v] = gx[v / p.Qy] * gy[v % p.Qy];
+    ps.vel.assign((size_t)kVelCols * V, 0.0);
+    ps.aj.assign(2 * (size_t)V, 0);
+    for (int v = 0; v < V; ++v) {
+        const int a = v / p.Qy, j = v % p.Qy, i = a < p.Qx ? a : a - p.Qx;
+        const double px = (a < p.Qx ? 1.0 : -1.0) * p.p0 * t.zx[i], py = p.p0 * t.yy[j], w = t.wx[i] * t.wy[j];
+        if (px > 0) { ps.inL += px * w * ps.fwL[v]; ps.restOutR += px * w * ps.frest[v]; }
+        else        { ps.inR += px * w * ps.fwR[v]; ps.restOutL += px * w * ps.frest[v]; }
+        const double pw[10] = {1, px, py, px * px, px * py, py * py, px * px * px, px * px * py, px * py * py,
+                               py * py * py};
+        for (int k = 0; k < 10; ++k) ps.restP[k] += pw[k] * w * ps.frest[v];
+        const double cols[kVelCols] = {px, py, w, ps.frest[v], ps.fwL[v], p.T_left * ps.fwL[v], ps.fwR[v],
+                                       p.T_right * ps.fwR[v]};
+        for (int c = 0; c < kVelCols; ++c) ps.vel[(size_t)c * V + v] = cols[c];
+        ps.aj[v] = a;
+        ps.aj[V + v] = j;
+    }
+    ps.isb.resize(t.sbeta.size());
+    for (size_t k = 0; k < ps.isb.size(); ++k) ps.isb[k] = 1.0 / t.sbeta[k];
+    ps.invl.assign(kMaxQ + 2, 0.0);
+    for (int l = 1; l < kMaxQ + 2; ++l) ps.invl[l] = 1.0 / l;
+    ps.vrow.assign((size_t)V * kVRow, 0.0);
+    for (int v = 0; v < V; ++v) {
+        const int cols[8] = {VC_PX, VC_PY, VC_W, VC_FR, VC_FWL, VC_FWLT, VC_FWR, VC_FWRT};
+        for (int c = 0; c < 8; ++c) ps.vrow[(size_t)v * kVRow + c] = ps.vel[(size_t)cols[c] * V + v];
+        ps.vrow[(size_t)v * kVRow + VR_A] = ps.aj[v];
+        ps.vrow[(size_t)v * kVRow + VR_J] = ps.aj[V + v];
+    }
+    if ((int)t.alpha.size() < Nxe + 2 || (int)t.sbeta.size() < Nxe + 2) {
+        err = "internal: recurrence table too short";
+        return false;
+    }
+    const EqTab E(Nxe, Nye, t.K, p.Qx, p.Qy);
+    ps.eqtab.assign(E.len, 0.0);
+    for (int l = 0; l < Nxe + 2; ++l) {
+        ps.eqtab[E.alpha + l] = t.alpha[l];
+        ps.eqtab[E.sbeta + l] = t.sbeta[l];
+        ps.eqtab[E.isbeta + l] = 1.0 / t.sbeta[l];
+    }
+    for (int l = 1; l < Nye + 2; ++l) ps.eqtab[E.invl + l] = 1.0 / l;
+    for (int k = 0; k < t.K; ++k) {
+        ps.eqtab[E.Yk + k] = t.Yk[k];
+        ps.eqtab[E.Wk + k] = t.Wk[k];
+    }
+    for (int k = 0; k < (Nxe + 1) * p.Qx; ++k) ps.eqtab[E.hz + k] = t.hz[k];
+    for (int k = 0; k < (Nye + 1) * p.Qy; ++k) ps.eqtab[E.He + k] = t.He[k];
+
+    DevTables dummy{};
+    size_t nd = 0, nf = 0;
+    for (auto &pc : dpieces(ps, dummy)) nd += pad_d(pc.src->size());
+    for (auto &pc : fpieces(ps, dummy)) nf += pad_f(pc.src->size());
+    const size_t dbytes = nd * sizeof(double), fbytes = nf * sizeof(float);
+    ps.blob.assign(dbytes + fbytes + ps.aj.size() * sizeof(int), 0);
+    size_t off = 0;
+    for (auto &pc : dpieces(ps, dummy)) {
+        std::memcpy(ps.blob.data() + off * sizeof(double), pc.src->data(), pc.src->size() * sizeof(double));
+        off += pad_d(pc.src->size());
+    }
+    off = 0;
+    for (auto &pc : fpieces(ps, dummy)) {
+        float *d = reinterpret_cast<float *>(ps.blob.data() + dbytes) + off;
+        for (size_t k = 0; k < pc.src->size(); ++k) d[k] = (float)(*pc.src)[k];
+        off += pad_f(pc.src->size());
+    }
+    std::memcpy(ps.blob.data() + dbytes + fbytes, ps.aj.data(), ps.aj.size() * sizeof(int));
+    return true;
+}
+
+void bind_tables(const ProblemSetup &ps, const lbc_params &p, const void *dev, DevTables &T)
+{
+    const HostTables &t = ps.t;
+    const char *base = static_cast<const char *>(dev);
+    size_t off = 0;
+    for (auto &pc : dpieces(ps, T)) {
+        *pc.dst = reinterpret_cast<const double *>(base) + off;
+        off += pad_d(pc.src->size());
+    }
+    const size_t dbytes = off * sizeof(double);
+    off = 0;
+    for (auto &pc : fpieces(ps, T)) {
+        *pc.dst = reinterpret_cast<const float *>(base + dbytes) + off;
+        off += pad_f(pc.src->size());
+    }
+    T.vel_aj = reinterpret_cast<const int *>(base + dbytes + off * sizeof(float));
+
+    T.Nx = p.Nx;
+    T.Nxp = (p.Nx + 31) / 32 * 32;
+    T.Qx = p.Qx; T.Qy = p.Qy; T.Nxe = ps.Nxe; T.Nye = ps.Nye; T.K = t.K; T.V = t.V;
+    T.ntile = (p.Nx + kTile - 1) / kTile;
+    T.p0 = p.p0; T.dt = ps.dt; T.delta = p.delta; T.Pr = p.Pr; T.omega = p.omega;
+    T.TL = p.T_left; T.TR = p.T_right; T.inL = ps.inL; T.inR = ps.inR;
+    T.restOutL = ps.restOutL; T.restOutR = ps.restOutR;
+    for (int k = 0; k < 10; ++k) {
+        T.restP[k] = ps.restP[k];
+        T.f_restP[k] = (float)ps.restP[k];
+    }
+    T.dsc[SC_NU] = p.delta * std::sqrt(2.0);
+    T.dsc[SC_EXPO] = 1.0 - p.omega;
+    T.dsc[SC_1MPR] = 1.0 - p.Pr;
+    T.dsc[SC_IP0] = 1.0 / p.p0;
+    T.dsc[SC_H0] = 1.0 / t.sbeta[0];
+    T.dsc[SC_DT] = ps.dt;
+    T.dsc[SC_IINL] = 1.0 / ps.inL;
+    T.dsc[SC_IINR] = 1.0 / ps.inR;
+    for (int k = 0; k < kNumSc; ++k) T.fsc[k] = (float)T.dsc[k];
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
@@ -149,34 +316,49 @@ lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int 
     return LBC_OK;
 }
 
-// Captures kGraphSteps plain steps (no early stop) plus the step-counter bump
-// into one CUDA graph, launched by lbc_step for every full group of steps.
-lbc_status ensure_graph(lbc_solver *s)
+// Velocity chunks per tile (multiples of the pipeline's kSubV rows, at most
+// kMaxCluster chunks: they form one cluster): the count that minimises a wave
+// model of the launch, waves x (rows per CTA + per-CTA overhead), with the
+// clusters the device can hold at once.
+lbc_status choose_launch_shape(bool fp32, DevTables &T)
 {
-    if (s->graph) return LBC_OK;
-    cudaStream_t cap;
-    LBC_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    cudaGraph_t g;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaStream_t keep = s->stream;
-        s->stream = cap;
-        e = launch_steps(s, 0, kGraphSteps, 0.0);
-        if (e == cudaSuccess) e = launch_ctl_bump(s->S.ctl, kGraphSteps, cap);
-        s->stream = keep;
-        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
-        if (e == cudaSuccess) e = e2;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(LBC_ECUDA, "no CUDA device");
+    cudaError_t e = fp32 ? configure_kernels<float>() : configure_kernels<double>();
+    if (e != cudaSuccess) return fail(LBC_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t eqs = fp32 ? equilibrium_smem_bytes<float>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K)
+                            : equilibrium_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K);
+    if (eqs > (size_t)optin)
+        return fail(LBC_EINVAL, "quadrature orders too large for the shared memory of one CTA (" +
+                                    std::to_string(eqs) + " bytes)");
+    const int subs = std::min((T.V + kSubV - 1) / kSubV, kMaxVChunk / kSubV);
+    double best = 1e300;
+    T.vchunk = T.nchunk = 0;
+    for (int nsub = 1; nsub <= subs; ++nsub) {
+        const int vch = nsub * kSubV, nch = (T.V + vch - 1) / vch;
+        if (nch > kMaxCluster) continue;
+        const size_t smem = fp32 ? stage_smem_bytes<float>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vch)
+                                 : stage_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vch);
+        if (smem > (size_t)optin) continue;
+        int ncl = 0;
+        e = fp32 ? stage_active_clusters<float>(smem, nch, &ncl) : stage_active_clusters<double>(smem, nch, &ncl);
+        if (e != cudaSuccess || ncl <= 0) {
+            cudaGetLastError();   // an unschedulable cluster shape is not an error of the solver
+            continue;
+        }
+        const double waves = std::ceil((double)T.ntile / ncl);
+        const double cost = waves * (vch + 24.0);
+        if (cost < best - 1e-9) { best = cost; T.vchunk = vch; T.nchunk = nch; }
     }
-    if (e == cudaSuccess) {
-        e = cudaGraphInstantiate(&s->graph, g, 0);
-        cudaGraphDestroy(g);
-    }
-    cudaStreamDestroy(cap);
-    if (e != cudaSuccess) return fail(LBC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    if (T.nchunk == 0)
+        return fail(LBC_EINVAL, "no schedulable cluster shape for a velocity set of " + std::to_string(T.V));
     return LBC_OK;
 }
 
-}  // namespace
+}  // namespace lbc
 
 extern "C" {
 
@@ -226,159 +408,42 @@ lbc_status lbc_create(const lbc_params *params, void *cuda_stream, lbc_solver **
     s->p = p;
     s->stream = static_cast<cudaStream_t>(cuda_stream);
     s->fp32 = p.precision == LBC_FP32_STATE;
-    std::string err;
-    if (!build_tables(p.Qx, p.Qy, Nxe, Nye, p.p0, s->tab, err)) {
-        delete s;
-        return fail(LBC_EINVAL, err);
-    }
-    const HostTables &t = s->tab;
-    const int V = t.V, Nx = p.Nx;
-    std::vector<double> inv_jdeta;
-    double deta, min_jdeta;
-    make_grid(Nx, p.stretch_A, s->x, inv_jdeta, deta, min_jdeta);
-
-    // time step: CFL on the smallest cell, and half the smallest relaxation time
-    double zmax = t.zx.back() * p.p0;
-    double dt = p.dt > 0 ? p.dt : p.cfl * min_jdeta / zmax;
-    if (p.dt <= 0 && p.delta > 0) {
-        for (double Tw : {1.0, p.T_left, p.T_right}) {
-            double tau = std::pow(Tw, p.omega - 1.0) / (p.delta * std::sqrt(2.0));
-            dt = std::min(dt, 0.5 * tau);
-        }
-    }
-
-    // wall Maxwellians (unit density) and incoming unit fluxes; rest Maxwellian
-    std::vector<double> gx(2 * p.Qx), gy(p.Qy), fwL(V), fwR(V), frest(V);
-    double inL = 0, inR = 0, restOutL = 0, restOutR = 0, restP[10] = {0};
-    equilibrium_host(t, 0.0, p.u_left, p.T_left, gx.data(), gy.data());
-    for (int v = 0; v < V; ++v) fwL[v] = gx[v / p.Qy] * gy[v % p.Qy];
-    equilibrium_host(t, 0.0, p.u_right, p.T_right, gx.data(), gy.data());
-    for (int v = 0; v < V; ++v) fwR[v] = gx[v / p.Qy] * gy[v % p.Qy];
-    equilibrium_host(t, 0.0, 0.0, 1.0, gx.data(), gy.data());
-    for (int v = 0; v < V; ++v) frest[v] = gx[v / p.Qy] * gy[v % p.Qy];
-    for (int v = 0; v < V; ++v) {
-        int a = v / p.Qy, j = v % p.Qy, i = a < p.Qx ? a : a - p.Qx;
-        double px = (a < p.Qx ? 1.0 : -1.0) * p.p0 * t.zx[i], py = p.p0 * t.yy[j], w = t.wx[i] * t.wy[j];
-        if (px > 0) { inL += px * w * fwL[v]; restOutR += px * w * frest[v]; }
-        else        { inR += px * w * fwR[v]; restOutL += px * w * frest[v]; }
-        const double f = w * frest[v];
-        const double pw[10] = {1, px, py, px * px, px * py, py * py, px * px * px, px * px * py, px * py * py,
-                               py * py * py};
-        for (int k = 0; k < 10; ++k) restP[k] += pw[k] * f;
-    }
-    s->frest = frest;
-
-    // ---- device tables: one allocation (FP64 block, then FP32 copies) ----
-    DevTables &T = s->T;
-    T.Nx = Nx;
-    T.Nxp = (Nx + 31) / 32 * 32;
-    T.Qx = p.Qx; T.Qy = p.Qy; T.Nxe = Nxe; T.Nye = Nye; T.K = t.K; T.V = V;
-    T.ntile = (Nx + kTile - 1) / kTile;
-    // velocity chunks (multiples of the pipeline's kSubV rows): pick the count
-    // that minimises a wave model of the launch, waves x (rows per CTA +
-    // per-CTA overhead), with the resident CTAs per SM of this kernel
-    {
-        const int sms = num_sms(), subs = std::min((V + kSubV - 1) / kSubV, kMaxVChunk / kSubV);
-        double best = 1e300;
-        for (int nsub = 1; nsub <= subs; ++nsub) {
-            int vch = nsub * kSubV, nch = (V + vch - 1) / vch;
-            const int slots = std::max(1, sms * resident_ctas(s->fp32, p.Qx, p.Qy, Nxe, Nye, t.K, vch));
-            double waves = std::ceil((double)T.ntile * nch / slots);
-            double cost = waves * (vch + 24.0);
-            if (cost < best - 1e-9) { best = cost; T.vchunk = vch; T.nchunk = nch; }
-        }
-    }
-    T.p0 = p.p0; T.dt = dt; T.delta = p.delta; T.Pr = p.Pr; T.omega = p.omega;
-    T.TL = p.T_left; T.TR = p.T_right; T.inL = inL; T.inR = inR;
-    T.restOutL = restOutL; T.restOutR = restOutR;
-    for (int k = 0; k < 10; ++k) T.restP[k] = restP[k];
-
-    std::vector<double> vel((size_t)kVelCols * V);
-    std::vector<double> aj(2 * (size_t)V);   // stored as doubles here, converted to int below
-    for (int v = 0; v < V; ++v) {
-        int a = v / p.Qy, j = v % p.Qy, i = a < p.Qx ? a : a - p.Qx;
-        vel[VC_PX * V + v] = (a < p.Qx ? 1.0 : -1.0) * p.p0 * t.zx[i];
-        vel[VC_PY * V + v] = p.p0 * t.yy[j];
-        vel[VC_W * V + v] = t.wx[i] * t.wy[j];
-        vel[VC_FR * V + v] = frest[v];
-        vel[VC_FWL * V + v] = fwL[v];
-        vel[VC_FWLT * V + v] = p.T_left * fwL[v];
-        vel[VC_FWR * V + v] = fwR[v];
-        vel[VC_FWRT * V + v] = p.T_right * fwR[v];
-        aj[v] = a;
-        aj[V + v] = j;
-    }
-    struct Piece { const std::vector<double> *src; const double **dst; };
-    Piece pieces[] = {
-        {&inv_jdeta, &T.inv_jdeta}, {&t.zx, &T.zx}, {&t.wx, &T.wx}, {&t.yy, &T.yy}, {&t.wy, &T.wy},
-        {&t.alpha, &T.alpha}, {&t.sbeta, &T.sbeta}, {&t.hz, &T.hz}, {&t.Yk, &T.Yk}, {&t.Wk, &T.Wk},
-        {&t.He, &T.He}, {&fwL, &T.fwL}, {&fwR, &T.fwR}, {&frest, &T.frest}, {&vel, &T.d_vel},
-    };
-    std::vector<double> isb(t.sbeta.size()), invl(kMaxQ + 2);
-    for (size_t k = 0; k < isb.size(); ++k) isb[k] = 1.0 / t.sbeta[k];
-    for (int l = 0; l < kMaxQ + 2; ++l) invl[l] = l ? 1.0 / l : 0.0;
-    struct FPiece { const std::vector<double> *src; const float **dst; };
-    FPiece fpieces[] = {
-        {&t.hz, &T.f_hz}, {&t.He, &T.f_He}, {&t.alpha, &T.f_alpha}, {&isb, &T.f_isbeta}, {&t.sbeta, &T.f_sbeta},
-        {&t.Yk, &T.f_Yk}, {&t.Wk, &T.f_Wk}, {&invl, &T.f_inv_l}, {&vel, &T.f_vel}, {&inv_jdeta, &T.f_inv_jdeta},
-        {&aj, reinterpret_cast<const float **>(&T.vel_aj)},
-    };
-    size_t total = 0;   // in doubles
-    for (auto &pc : pieces) total += (pc.src->size() + 31) / 32 * 32;
-    size_t ftotal = 0;  // in floats
-    for (auto &pc : fpieces) ftotal += (pc.src->size() + 63) / 64 * 64;
-    const size_t dbytes = total * sizeof(double), bytes = dbytes + ftotal * sizeof(float);
-    std::vector<unsigned char> host(bytes, 0);
-    std::vector<size_t> offs, foffs;
-    size_t off = 0;
-    for (auto &pc : pieces) {
-        std::memcpy(host.data() + off * sizeof(double), pc.src->data(), pc.src->size() * sizeof(double));
-        offs.push_back(off);
-        off += (pc.src->size() + 31) / 32 * 32;
-    }
-    off = 0;
-    for (auto &pc : fpieces) {
-        float *dst = reinterpret_cast<float *>(host.data() + dbytes) + off;
-        if (pc.src == &aj) {   // integer table shares the 4-byte block
-            int *di = reinterpret_cast<int *>(dst);
-            for (size_t k = 0; k < pc.src->size(); ++k) di[k] = (int)(*pc.src)[k];
-        } else {
-            for (size_t k = 0; k < pc.src->size(); ++k) dst[k] = (float)(*pc.src)[k];
-        }
-        foffs.push_back(off);
-        off += (pc.src->size() + 63) / 64 * 64;
-    }
     auto cleanup = [&](lbc_status code) {
         lbc_destroy(s);
         return code;
     };
-    cudaError_t e = cudaMallocAsync(&s->table_block, bytes, s->stream);
+    ProblemSetup ps;
+    std::string err;
+    if (!setup_problem(p, Nxe, Nye, ps, err)) return cleanup(fail(LBC_EINVAL, err));
+    s->x = ps.x;
+    s->frest = ps.frest;
+
+    // ---- device tables (one allocation) and the launch shape ----
+    cudaError_t e = cudaMallocAsync(&s->table_block, ps.blob.size(), s->stream);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMallocAsync(tables): ") + cudaGetErrorString(e));
         return cleanup(e == cudaErrorMemoryAllocation ? LBC_ENOMEM : LBC_ECUDA);
     }
-    e = cudaMemcpyAsync(s->table_block, host.data(), bytes, cudaMemcpyHostToDevice, s->stream);
-    if (e != cudaSuccess) { set_error(std::string("cudaMemcpyAsync(tables): ") + cudaGetErrorString(e)); return cleanup(LBC_ECUDA); }
-    e = cudaStreamSynchronize(s->stream);   // the pageable host copy must finish before `host` goes away
+    e = cudaMemcpyAsync(s->table_block, ps.blob.data(), ps.blob.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);   // the pageable source must outlive the copy
     if (e != cudaSuccess) { set_error(std::string("table upload: ") + cudaGetErrorString(e)); return cleanup(LBC_ECUDA); }
-    for (size_t k = 0; k < sizeof(pieces) / sizeof(pieces[0]); ++k)
-        *pieces[k].dst = static_cast<const double *>(s->table_block) + offs[k];
-    for (size_t k = 0; k < sizeof(fpieces) / sizeof(fpieces[0]); ++k)
-        *fpieces[k].dst = reinterpret_cast<const float *>(static_cast<const char *>(s->table_block) + dbytes) + foffs[k];
+    DevTables &T = s->T;
+    bind_tables(ps, p, s->table_block, T);
+    st = choose_launch_shape(s->fp32, T);
+    if (st != LBC_OK) return cleanup(st);
 
     // ---- device state ----
+    const int V = T.V;
     const size_t esz = s->fp32 ? sizeof(float) : sizeof(double);
     auto r256 = [](size_t x) { return (x + 255) / 256 * 256; };
     const size_t fbytes = r256(2 * (size_t)V * T.Nxp * esz);
     const size_t pbytes = r256((size_t)T.nchunk * kNumRaw * T.Nxp * esz);
-    const size_t shbytes = r256(2 * (size_t)T.Nxp * esz);
     const size_t embytes = r256((size_t)T.Nxp * kEqM * esz);
     const size_t egbytes = r256((size_t)T.ntile * (2 * p.Qx + p.Qy) * kLanes * esz);
-    const size_t cnbytes = r256((size_t)T.ntile * sizeof(int));
     const size_t rbytes = kResidRing * sizeof(unsigned long long);
     const size_t cbytes = 256;
     const size_t mbytes = r256((size_t)LBC_NMOM * T.Nxp * sizeof(double));
-    const size_t sbytes = 3 * (fbytes + pbytes + shbytes + embytes + egbytes + cnbytes) + rbytes + cbytes + mbytes;
+    const size_t sbytes = 3 * (fbytes + embytes + egbytes) + pbytes + rbytes + cbytes + mbytes;
     e = cudaMallocAsync(&s->state_block, sbytes, s->stream);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMallocAsync(state): ") + cudaGetErrorString(e));
@@ -388,11 +453,9 @@ lbc_status lbc_create(const lbc_params *params, void *cuda_stream, lbc_solver **
     if (e != cudaSuccess) { set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)); return cleanup(LBC_ECUDA); }
     char *b = static_cast<char *>(s->state_block);
     for (int k = 0; k < 3; ++k) { s->S.F[k] = b; b += fbytes; }
-    for (int k = 0; k < 3; ++k) { s->S.part[k] = b; b += pbytes; }
-    for (int k = 0; k < 3; ++k) { s->S.shift[k] = b; b += shbytes; }
     for (int k = 0; k < 3; ++k) { s->S.eqm[k] = b; b += embytes; }
     for (int k = 0; k < 3; ++k) { s->S.eqg[k] = b; b += egbytes; }
-    for (int k = 0; k < 3; ++k) { s->S.count[k] = reinterpret_cast<int *>(b); b += cnbytes; }
+    s->S.part = b; b += pbytes;
     s->S.resid = reinterpret_cast<unsigned long long *>(b); b += rbytes;
     s->S.ctl = reinterpret_cast<Ctl *>(b); b += cbytes;
     s->S.mom_out = reinterpret_cast<double *>(b);
@@ -403,9 +466,6 @@ lbc_status lbc_create(const lbc_params *params, void *cuda_stream, lbc_solver **
         set_error(std::string("cudaMallocHost: ") + cudaGetErrorString(e));
         return cleanup(e == cudaErrorMemoryAllocation ? LBC_ENOMEM : LBC_ECUDA);
     }
-
-    e = s->fp32 ? configure_kernels<float>() : configure_kernels<double>();
-    if (e != cudaSuccess) { set_error(std::string("kernel attributes: ") + cudaGetErrorString(e)); return cleanup(LBC_ECUDA); }
     for (int k = 0; k < 3; ++k) {
         st = encode_state_map(&s->M.in[k], s->S.F[k], s->fp32, V, T.Nxp, kRowLen);
         if (st != LBC_OK) return cleanup(st);
@@ -487,8 +547,10 @@ lbc_status lbc_run_to_steady(lbc_solver *s, double residual, long max_steps, lon
 lbc_status lbc_moments(lbc_solver *s, double *out, double *x)
 {
     if (!s || !out) return fail(LBC_EINVAL, "NULL argument");
-    LBC_CUDA_TRY(s->fp32 ? launch_finalize_moments<float>(s->T, s->S, 0, s->stream)
-                         : launch_finalize_moments<double>(s->T, s->S, 0, s->stream));
+    LBC_CUDA_TRY(s->fp32 ? launch_moments_partial<float>(s->T, s->S, 0, s->stream)
+                         : launch_moments_partial<double>(s->T, s->S, 0, s->stream));
+    LBC_CUDA_TRY(s->fp32 ? launch_finalize_moments<float>(s->T, s->S, s->stream)
+                         : launch_finalize_moments<double>(s->T, s->S, s->stream));
     LBC_CUDA_TRY(cudaMemcpy2DAsync(out, s->p.Nx * sizeof(double), s->S.mom_out, s->T.Nxp * sizeof(double),
                                    s->p.Nx * sizeof(double), LBC_NMOM, cudaMemcpyDeviceToHost, s->stream));
     LBC_CUDA_TRY(cudaMemcpyAsync(s->h_ctl, s->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));

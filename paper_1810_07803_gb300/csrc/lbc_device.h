@@ -3,6 +3,9 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <string>
+#include <vector>
+
 #include "lbc_internal.h"
 
 namespace lbc {
@@ -15,8 +18,22 @@ constexpr int kWarps = 8;          // warps per CTA
 constexpr int kThreads = kWarps * 32;
 constexpr int kSubV = 16;          // velocities per pipeline stage (two per warp)
 constexpr int kPipe = 4;           // pipeline depth (stages in flight)
-constexpr int kEqM = 9;            // per-node stage data: n ux uy T qx qy 1/tau cS 1/(5T)
+constexpr int kEqM = 12;           // per-node stage data: n ux uy T qx qy 1/tau cS 1/(5T) 1/(J deta), 2 pad
+                                   // (48 B per FP32 node: a tile's block is one 16-byte-aligned bulk copy)
 constexpr int kMaxVChunk = 256;    // velocities per CTA at most (per-velocity data is staged in smem)
+constexpr int kMaxCluster = 16;    // chunk CTAs of a tile form one thread-block cluster (non-portable size 16)
+constexpr int kMaxV = kMaxCluster * kMaxVChunk;   // largest velocity set 2 Qx Qy
+
+// Scalars derived from the parameters, in both precisions (no FP64 arithmetic in the FP32 kernels).
+enum { SC_NU = 0,      // delta sqrt(2): 1/tau = SC_NU n T^(1 - omega)   (Eq. tau)
+       SC_EXPO,        // 1 - omega
+       SC_1MPR,        // 1 - Pr
+       SC_IP0,         // 1 / p0
+       SC_H0,          // h_0 = 1 / sbeta_0 (orthonormal h_0)
+       SC_DT,          // time step
+       SC_IINL,        // 1 / inL
+       SC_IINR,        // 1 / inR
+       kNumSc };
 
 // Read-only problem data, passed by value to every kernel. The state is stored
 // as the deviation d = ft - ft_rest from the weight-divided rest Maxwellian.
@@ -27,6 +44,9 @@ struct DevTables {
     double inL, inR;               // sum_{incoming} p_x w_v fw_v (signed) for a unit wall density
     double restOutL, restOutR;     // sum_{outgoing} p_x w_v ft_rest_v at each wall
     double restP[10];              // rest power sums sum_v w p_x^a p_y^b ft_rest: 00 10 01 20 11 02 30 21 12 03
+    float f_restP[10];
+    double dsc[kNumSc];
+    float fsc[kNumSc];
     const double *inv_jdeta;       // [Nx] 1/(J_s deta)
     const double *zx, *wx, *yy, *wy;
     const double *alpha, *sbeta;   // orthonormal recurrence of h_l
@@ -42,8 +62,36 @@ struct DevTables {
     const double *d_vel;
     const float *f_vel;
     const int *vel_aj;     // [2][V]
+    const double *d_vrow;  // [V][kVRow]
+    const float *f_vrow;
+    const double *d_eqtab; // EqTab layout
+    const float *f_eqtab;
 };
 enum { VC_PX = 0, VC_PY, VC_W, VC_FR, VC_FWL, VC_FWLT, VC_FWR, VC_FWRT, kVelCols };
+// Per-velocity rows [V][kVRow] (both precisions), copied per velocity chunk into
+// shared memory: p_x, p_y, w, ft_rest, unit-density wall Maxwellians (phi, chi;
+// left, right), and the indices a, j (small integers, exact in either precision).
+enum { VR_PX = 0, VR_PY, VR_W, VR_FR, VR_FWL, VR_FWLT, VR_FWR, VR_FWRT, VR_A, VR_J, kVRow };
+
+// Tables of the equilibrium construction, one contiguous block per precision,
+// each piece padded to 4 elements (16-byte pieces in FP32): recurrence of h_l,
+// 1/l, projection rule, h_l(z_i) [N+1][Qx] and He_l(y_j) [Ny+1][Qy].
+struct EqTab {
+    int alpha, sbeta, isbeta, invl, Yk, Wk, hz, He, len;
+    __host__ __device__ EqTab(int N, int Ny, int K, int Qx, int Qy)
+    {
+        alpha = 0;
+        sbeta = alpha + r4(N + 2);
+        isbeta = sbeta + r4(N + 2);
+        invl = isbeta + r4(N + 2);
+        Yk = invl + r4(Ny + 2);
+        Wk = Yk + r4(K);
+        hz = Wk + r4(K);
+        He = hz + r4((N + 1) * Qx);
+        len = He + r4((Ny + 1) * Qy);
+    }
+    __host__ __device__ static int r4(int x) { return (x + 3) / 4 * 4; }
+};
 
 // Control block in device memory.
 struct Ctl {
@@ -58,11 +106,11 @@ struct Ctl {
 // Mutable device state; arrays marked (R) hold the state precision.
 struct DevState {
     void *F[3];            // (R) [2][V][Nxp] deviation from the rest state
-    void *part[3];         // (R) [nchunk][kNumRaw][Nxp] raw moment sums of the deviation per velocity chunk
-    void *shift[3];        // (R) [2][Nxp] velocity shift of those sums
+    void *part;            // (R) [nchunk][kNumRaw][Nxp] raw moment sums (about p = 0) of the deviation per
+                           //     velocity chunk (set-up and lbc_moments only; the stage kernel exchanges its
+                           //     partials inside the tile's cluster)
     void *eqm[3];          // (R) [Nxp][kEqM] moments and relaxation data of buffer b
     void *eqg[3];          // (R) [ntile][2Qx + Qy][kLanes] equilibrium factors of buffer b
-    int *count[3];         // [ntile] chunk CTAs done with buffer b (the last one builds eqm/eqg)
     unsigned long long *resid;   // [kResidRing] per-step residual (bits of a double >= 0)
     Ctl *ctl;
     double *mom_out;       // [LBC_NMOM][Nxp] scratch for lbc_moments
@@ -74,10 +122,38 @@ struct StateMaps {
     CUtensorMap f0;        // box kF0Len x kSubV (RK base state, buffer 0)
 };
 
+// Host-side image of one problem: tables, grid, time step, wall and rest data,
+// and the device table block (FP64 pieces, FP32 copies, the index table).
+struct ProblemSetup {
+    HostTables t;
+    int Nxe = 0, Nye = 0;
+    std::vector<double> x, inv_jdeta;
+    double deta = 0, min_jdeta = 0, dt = 0;
+    std::vector<double> fwL, fwR, frest, vel, isb, invl, vrow, eqtab;
+    std::vector<int> aj;
+    double inL = 0, inR = 0, restOutL = 0, restOutR = 0, restP[10] = {0};
+    std::vector<unsigned char> blob;   // device table block contents
+};
+// Validated parameters -> ProblemSetup (time step: see lbc_create in include/lbc.h).
+bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std::string &err);
+// Fills T from ps, with the table pointers into the device copy `dev` of ps.blob.
+// Leaves the launch shape (vchunk, nchunk) to choose_launch_shape.
+void bind_tables(const ProblemSetup &ps, const lbc_params &p, const void *dev, DevTables &T);
+// Sets the stage kernel's attributes on the current device and picks T.vchunk,
+// T.nchunk. LBC_ECUDA without a device; LBC_EINVAL if no cluster shape fits.
+lbc_status choose_launch_shape(bool fp32, DevTables &T);
+// TMA descriptor of a state buffer viewed as [2V rows][Nxp columns], box box_cols x kSubV.
+lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_cols);
+
 template <typename R>
 size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk);
 template <typename R>
 cudaError_t stage_kernel_attributes(cudaFuncAttributes *fa);
+template <typename R>
+size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K);
+// Clusters of `nchunk` stage CTAs that can be resident at once (0: not launchable).
+template <typename R>
+cudaError_t stage_active_clusters(size_t smem, int nchunk, int *nclusters);
 template <typename R>
 cudaError_t configure_kernels();   // per-device kernel attributes; call before capture
 template <typename R>
@@ -88,7 +164,7 @@ cudaError_t launch_moments_partial(const DevTables &T, const DevState &S, int bu
 template <typename R>
 cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int buf, cudaStream_t st);
 template <typename R>
-cudaError_t launch_finalize_moments(const DevTables &T, const DevState &S, int buf, cudaStream_t st);
+cudaError_t launch_finalize_moments(const DevTables &T, const DevState &S, cudaStream_t st);
 cudaError_t launch_ctl_set(Ctl *ctl, long long base, long long check_from, int stopped, cudaStream_t st);
 cudaError_t launch_ctl_bump(Ctl *ctl, long long k, cudaStream_t st);
 

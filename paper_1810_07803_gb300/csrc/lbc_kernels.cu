@@ -2,7 +2,8 @@
 //
 // One CTA owns a tile of 31 nodes (lane l: node c0 + l and the face on its
 // left, so each lane computes one WENO-5 face per row) x one chunk of the
-// velocity set, both fields. Per stage it:
+// velocity set, both fields; the chunk CTAs of a tile form one thread-block
+// cluster. Per stage a CTA:
 //  (1) reads its nodes' stage data (moments, 1/tau, Shakhov prefactor) and
 //      discrete equilibrium factors g_x, g_y (Eqs. gx, gy), built by the
 //      previous stage (or at set-up);
@@ -12,10 +13,12 @@
 //      of kSubV rows, mbarrier completion): WENO-5 faces upwind by sign p_x,
 //      Shakhov target (Sec. II) with 1/tau of Eq. tau, TVD RK-3 combination,
 //      store, and the new stage's raw moments over the chunk's velocities;
-//  (4) publishes the per-chunk moment partials; the last chunk CTA of the tile
-//      to finish turns them into the next stage's tile data (moments in FP64,
-//      equilibrium factors by the stable Gauss-sum projection). On the last
-//      stage it also folds the residual max w |f^{n+1} - f^n|.
+//  (4) publishes its per-chunk moment partials in shared memory; after a
+//      cluster barrier, CTA r of the cluster sums the partials of nodes
+//      r, r + nchunk, ... over all chunks (distributed shared memory) and
+//      builds their next-stage data (moments, equilibrium factors by the
+//      stable Gauss-sum projection). On the last stage it also folds the
+//      residual max w |f^{n+1} - f^n|.
 // The state is the deviation d = ft - ft_rest from the weight-divided rest
 // Maxwellian (n = 1, u = 0, T = 1): WENO-5, the ghost extrapolation and the RK
 // combination are affine-invariant, so they act on d unchanged, and the FP32
@@ -43,6 +46,10 @@ template <> struct Tabs<double> {
     __device__ static double sbeta(const DevTables &T, int l) { return T.sbeta[l]; }
     __device__ static double isbeta(const DevTables &T, int l) { return 1.0 / T.sbeta[l]; }
     __device__ static double inv_l(const DevTables &, int l) { return 1.0 / l; }
+    __device__ static double sc(const DevTables &T, int k) { return T.dsc[k]; }
+    __device__ static const double *vrow(const DevTables &T) { return T.d_vrow; }
+    __device__ static const double *eqtab(const DevTables &T) { return T.d_eqtab; }
+    __device__ static double restP(const DevTables &T, int k) { return T.restP[k]; }
 };
 template <> struct Tabs<float> {
     __device__ static const float *vel(const DevTables &T) { return T.f_vel; }
@@ -55,6 +62,10 @@ template <> struct Tabs<float> {
     __device__ static float sbeta(const DevTables &T, int l) { return T.f_sbeta[l]; }
     __device__ static float isbeta(const DevTables &T, int l) { return T.f_isbeta[l]; }
     __device__ static float inv_l(const DevTables &T, int l) { return T.f_inv_l[l]; }
+    __device__ static float sc(const DevTables &T, int k) { return T.fsc[k]; }
+    __device__ static const float *vrow(const DevTables &T) { return T.f_vrow; }
+    __device__ static const float *eqtab(const DevTables &T) { return T.f_eqtab; }
+    __device__ static float restP(const DevTables &T, int k) { return T.f_restP[k]; }
 };
 
 // ---- compensated arithmetic (error-free transformations of Knuth and Dekker) ----
@@ -226,7 +237,7 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
 }
 
 // Raw sums of the rest Maxwellian about shift (sx, sy), from its power sums P_ab.
-__device__ void rest_raw(const double *P, double sx, double sy, double *r)
+__device__ __forceinline__ void rest_raw(const double *P, double sx, double sy, double *r)
 {
     const double P00 = P[0], P10 = P[1], P01 = P[2], P20 = P[3], P11 = P[4], P02 = P[5];
     const double P30 = P[6], P21 = P[7], P12 = P[8], P03 = P[9];
@@ -248,7 +259,7 @@ __device__ void rest_raw(const double *P, double sx, double sy, double *r)
 }
 
 // n, u_x, u_y, T, P_xx, P_yy, P_zz, P_xy, q_x, q_y from raw sums about (sx, sy).
-__device__ void raw_to_moments(const double *r, double sx, double sy, double *m)
+__device__ __forceinline__ void raw_to_moments(const double *r, double sx, double sy, double *m)
 {
     double n = r[R_S0], in = 1.0 / n;
     double bx = r[R_SX] * in, by = r[R_SY] * in;
@@ -308,38 +319,106 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// ---- tile stage data ----
+// ---- thread-block cluster (the chunk CTAs of one tile) ----
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// Store into the shared memory of cluster CTA `rank`, at the address that `local` has in this CTA.
+template <typename R> __device__ __forceinline__ void st_cluster(R *local, uint32_t rank, R v);
+template <> __device__ __forceinline__ void st_cluster<float>(float *local, uint32_t rank, float v)
+{
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(local)), "r"(rank));
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
+}
+template <> __device__ __forceinline__ void st_cluster<double>(double *local, uint32_t rank, double v)
+{
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(local)), "r"(rank));
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+}
+
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
+// completing on the mbarrier `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---- stage data of a set of nodes ----
 // orders per block of the tabulated recurrence (bounded by shared memory at Q = 64)
 template <typename R> struct OrderBlock { static constexpr int value = sizeof(R) == 4 ? 8 : 4; };
 
+// Shared scratch of node_equilibrium for up to `ncap` nodes. The first `red`
+// bytes are left to the stage kernel's warp partials, so that the equilibrium
+// tables can be copied into `tab` while those are being reduced.
 template <typename R>
 struct EqScratch {
-    size_t raw, mo, sc, rpm, bb, cb, H, total;
+    size_t red, tab, raw, shf, sc, rpm, bb, cb, H, total;
     int cstride;
-    __host__ __device__ EqScratch(int K, int N, int Ny)
+    __host__ __device__ EqScratch(int K, int N, int Ny, int Qx, int Qy, int ncap = kTile)
     {
         cstride = 2 * (N + 1) + 1;   // odd stride: conflict-free rows per node
-        raw = 0;
-        mo = raw + (size_t)kLanes * kNumRaw * sizeof(R);
-        sc = mo + (size_t)kLanes * 12 * sizeof(R);
-        rpm = sc + (size_t)kLanes * 8 * sizeof(R);
-        bb = rpm + (size_t)kLanes * 2 * K * sizeof(R);
-        cb = bb + (size_t)kLanes * (Ny + 1) * sizeof(R);
-        H = cb + (size_t)kLanes * cstride * sizeof(R);
-        total = H + (size_t)OrderBlock<R>::value * kTile * K * sizeof(R);
+        red = (size_t)kWarps * kNumRaw * kLanes * sizeof(R);
+        tab = al16(red);
+        raw = al16(tab + (size_t)EqTab(N, Ny, K, Qx, Qy).len * sizeof(R));
+        shf = al16(raw + (size_t)ncap * kNumRaw * sizeof(R));
+        sc = al16(shf + (size_t)2 * kLanes * sizeof(R));
+        rpm = al16(sc + (size_t)ncap * 8 * sizeof(R));
+        bb = al16(rpm + (size_t)ncap * 2 * K * sizeof(R));
+        cb = al16(bb + (size_t)ncap * (Ny + 1) * sizeof(R));
+        H = al16(cb + (size_t)ncap * cstride * sizeof(R));
+        total = H + (size_t)OrderBlock<R>::value * ncap * K * sizeof(R);
     }
+    __host__ __device__ static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
 };
 
-// Moments from raw sums about (sx, sy), in the state precision (FP32 path: the
-// partials are FP32 and the equilibrium is built in FP32, so FP64 here would not
-// change the result; FP64 path: FP64 throughout).
+// Raw sums of the rest Maxwellian about the shift (sx, sy), from its power sums P_ab.
 template <typename R>
-__device__ void raw_to_moments_r(const R *r, R sx, R sy, R *m)
+__device__ __forceinline__ void rest_raw_r(const DevTables &T, R sx, R sy, R *r)
+{
+    // constant indices only: the parameter block stays in the constant bank (no local copy)
+    const R P00 = Tabs<R>::restP(T, 0), P10 = Tabs<R>::restP(T, 1), P01 = Tabs<R>::restP(T, 2);
+    const R P20 = Tabs<R>::restP(T, 3), P11 = Tabs<R>::restP(T, 4), P02 = Tabs<R>::restP(T, 5);
+    const R P30 = Tabs<R>::restP(T, 6), P21 = Tabs<R>::restP(T, 7), P12 = Tabs<R>::restP(T, 8);
+    const R P03 = Tabs<R>::restP(T, 9);
+    r[R_S0] = P00;
+    r[R_SX] = P10 - sx * P00;
+    r[R_SY] = P01 - sy * P00;
+    r[R_SXX] = P20 - R(2) * sx * P10 + sx * sx * P00;
+    r[R_SXY] = P11 - sx * P01 - sy * P10 + sx * sy * P00;
+    r[R_SYY] = P02 - R(2) * sy * P01 + sy * sy * P00;
+    r[R_CZ] = P00;                       // chi_rest = T_rest phi_rest, T_rest = 1
+    const R a3 = P30 - R(3) * sx * P20 + R(3) * sx * sx * P10 - sx * sx * sx * P00;
+    const R ab2 = P12 - R(2) * sy * P11 + sy * sy * P10 - sx * P02 + R(2) * sx * sy * P01 - sx * sy * sy * P00;
+    const R b3 = P03 - R(3) * sy * P02 + R(3) * sy * sy * P01 - sy * sy * sy * P00;
+    const R ba2 = P21 - R(2) * sx * P11 + sx * sx * P01 - sy * P20 + R(2) * sx * sy * P10 - sy * sx * sx * P00;
+    r[R_R3X] = a3 + ab2;
+    r[R_R3Y] = b3 + ba2;
+    r[R_GX] = P10 - sx * P00;
+    r[R_GY] = P01 - sy * P00;
+}
+
+// Moments from raw sums about (sx, sy), in the state precision.
+template <typename R>
+__device__ __forceinline__ void raw_to_moments_r(const R *r, R sx, R sy, R *m)
 {
     R n = r[R_S0], in = R(1) / n;
     R bx = r[R_SX] * in, by = r[R_SY] * in;
     R pxx = r[R_SXX] - n * bx * bx;
-    R pxy = r[R_SXY] - n * bx * by;
     R pyy = r[R_SYY] - n * by * by;
     R pzz = r[R_CZ];
     R r2 = r[R_SXX] + r[R_SYY], b2 = bx * bx + by * by;
@@ -353,63 +432,65 @@ __device__ void raw_to_moments_r(const R *r, R sx, R sy, R *m)
     m[9] = R(0.5) * hy + R(0.5) * (r[R_GY] - by * pzz);
 }
 
-// Stage data of one tile of buffer `buf` (block-wide, all threads): sums the
-// per-chunk raw moment partials, turns them into moments (adding the rest
-// state's share), and builds the discrete equilibrium factors of Eqs. gx, gy
-// at every node of the tile (algorithm: see equilibrium_host). Writes eqm[buf]
-// for the tile's nodes and the tile's block of eqg[buf].
-// The last CTA of a tile runs this at the end of a stage, so it is organised
-// for latency: every phase spreads over all threads of the block (recurrences
-// per (node, projection node), dot products per (node, order), factors per
-// (node, velocity)).
+// Combines the Dot2 states of lane groups (xor distance o) into each lane.
 template <typename R>
-__device__ void tile_equilibrium(const DevTables &T, const DevState &S, int buf, int tile, unsigned char *scratch)
+__device__ __forceinline__ void dot_combine(Dot<R> &d, int o)
+{
+    const R so = __shfl_xor_sync(0xffffffffu, d.s, o), co = __shfl_xor_sync(0xffffffffu, d.c, o);
+    if constexpr (std::is_same<R, float>::value) {
+        R t, e;
+        two_sum(d.s, so, t, e);
+        d.s = t;
+        d.c = d.c + co + e;
+    } else {
+        d.s += so;
+    }
+}
+
+// Stage data of the nodes c = cfirst + i cstep (i < nn <= ncap) of tile `tile`
+// for buffer `buf` (block-wide, all threads). Input in `scratch` (EqScratch
+// for ncap nodes): the
+// equilibrium tables (EqTab), the raw moment sums of the deviation per node,
+// raw[i][m], and the shift of those sums per tile node, shf[0][c] = s_x,
+// shf[1][c] = s_y. Adds the rest state's share, turns the sums into moments,
+// and builds the discrete equilibrium factors of Eqs. gx, gy (algorithm: see
+// equilibrium_host). Writes eqm[buf] of the nodes and their columns of the
+// tile's eqg[buf] block.
+// Organised for latency: tables are read from shared memory, and every phase
+// spreads over all threads of the block (recurrences per (node, projection
+// node), dot products over 4 lanes per (node, order), factors per (node,
+// velocity)).
+template <typename R>
+__device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf, int tile, int cfirst, int cstep,
+                                 int nn, int ncap, unsigned char *scratch)
 {
     const int tid = threadIdx.x, c0 = tile * kTile;
     const int N = T.Nxe, K = T.K, G = 2 * T.Qx + T.Qy, Ny = T.Nye;
-    const EqScratch<R> L(K, N, Ny);
-    R *raw = reinterpret_cast<R *>(scratch + L.raw);    // [32][kNumRaw]
-    R *mo = reinterpret_cast<R *>(scratch + L.mo);      // [32][12]
-    R *sc = reinterpret_cast<R *>(scratch + L.sc);      // [32][8]: sT a a^2/2
-    R *rpm = reinterpret_cast<R *>(scratch + L.rpm);    // [31][2][K]
-    R *bb = reinterpret_cast<R *>(scratch + L.bb);      // [31][Ny+1]   Hermite coefficients of g_y
-    R *cb = reinterpret_cast<R *>(scratch + L.cb);      // [31][cstride] c^+_l, c^-_l
-    R *H = reinterpret_cast<R *>(scratch + L.H);        // [kLB][31 K]  h_l(sqrt(T') Y_k)
+    const EqScratch<R> L(K, N, Ny, T.Qx, T.Qy, ncap);
+    const EqTab E(N, Ny, K, T.Qx, T.Qy);
+    const R *tab = reinterpret_cast<const R *>(scratch + L.tab);
+    const R *raw = reinterpret_cast<const R *>(scratch + L.raw);   // [nn][kNumRaw]
+    const R *shf = reinterpret_cast<const R *>(scratch + L.shf);   // [2][kLanes]
+    R *sc = reinterpret_cast<R *>(scratch + L.sc);      // [nn][8]: sT a a^2/2
+    R *rpm = reinterpret_cast<R *>(scratch + L.rpm);    // [nn][2][K]
+    R *bb = reinterpret_cast<R *>(scratch + L.bb);      // [nn][Ny+1]   Hermite coefficients of g_y
+    R *cb = reinterpret_cast<R *>(scratch + L.cb);      // [nn][cstride] c^+_l, c^-_l
+    R *H = reinterpret_cast<R *>(scratch + L.H);        // [kLB][nn K]  h_l(sqrt(T') Y_k)
     constexpr int kLB = OrderBlock<R>::value;
-    const R *part = static_cast<const R *>(S.part[buf]);
-    const R *shift = static_cast<const R *>(S.shift[buf]);
     R *eqm = static_cast<R *>(S.eqm[buf]);
     R *eqg = static_cast<R *>(S.eqg[buf]) + (size_t)tile * G * kLanes;
 
-    // raw sums of the deviation, all chunks
-    for (int idx = tid; idx < kLanes * kNumRaw; idx += kThreads) {
-        const int c = idx & 31, m = idx >> 5, s = c0 + c;
-        CSum<R> acc;
-        if (c < kTile && s < T.Nx) {
-            const R *pp = part + (size_t)m * T.Nxp + s;
-            const size_t cs = (size_t)kNumRaw * T.Nxp;
-            int ch = 0;
-            for (; ch + 4 <= T.nchunk; ch += 4) {   // four loads in flight
-                R v0 = __ldcg(pp + ch * cs), v1 = __ldcg(pp + (ch + 1) * cs);
-                R v2 = __ldcg(pp + (ch + 2) * cs), v3 = __ldcg(pp + (ch + 3) * cs);
-                acc.add(v0); acc.add(v1); acc.add(v2); acc.add(v3);
-            }
-            for (; ch < T.nchunk; ++ch) acc.add(__ldcg(pp + ch * cs));
-        }
-        raw[c * kNumRaw + m] = acc.value();
-    }
-    __syncthreads();
     // moments, relaxation data and per-node scalars (thread per node)
-    if (tid < kLanes) {
-        const int c = tid, s = c0 + c;
-        const bool live = c < kTile && s < T.Nx;
+    if (tid < nn) {
+        const int c = cfirst + tid * cstep, s = c0 + c;
+        const bool live = s < T.Nx;
         R m[10];
         if (live) {
-            const R sx = __ldcg(&shift[s]), sy = __ldcg(&shift[T.Nxp + s]);
-            double rd[kNumRaw];
-            rest_raw(T.restP, (double)sx, (double)sy, rd);
+            const R sx = shf[c], sy = shf[kLanes + c];
             R rr[kNumRaw];
-            for (int k = 0; k < kNumRaw; ++k) rr[k] = R(rd[k]) + raw[c * kNumRaw + k];
+            rest_raw_r<R>(T, sx, sy, rr);
+#pragma unroll
+            for (int k = 0; k < kNumRaw; ++k) rr[k] += raw[tid * kNumRaw + k];
             raw_to_moments_r<R>(rr, sx, sy, m);
             // a NaN/Inf anywhere in the node's populations reaches its moments
             if (!isfinite(m[0]) || !isfinite(m[3]) || !isfinite(m[8]) || !isfinite(m[9]) || !(m[0] > R(0)) ||
@@ -419,95 +500,105 @@ __device__ void tile_equilibrium(const DevTables &T, const DevState &S, int buf,
             m[0] = R(1); m[1] = m[2] = R(0); m[3] = R(1); m[8] = m[9] = R(0);
         }
         const R n = m[0], ux = m[1], uy = m[2], Tc = m[3];
-        const R nu = n * R(T.delta * 1.4142135623730951) * pow(Tc, R(1.0 - T.omega));   // 1/tau, Eq. tau
-        const R cS = R(1.0 - T.Pr) / (n * Tc * Tc);                                     // Shakhov prefactor
+        const R nu = n * Tabs<R>::sc(T, SC_NU) * pow(Tc, Tabs<R>::sc(T, SC_EXPO));   // 1/tau, Eq. tau
+        const R cS = Tabs<R>::sc(T, SC_1MPR) / (n * Tc * Tc);                        // Shakhov prefactor
         if (live) {
             R *e = eqm + (size_t)s * kEqM;
             e[0] = n; e[1] = ux; e[2] = uy; e[3] = Tc; e[4] = m[8]; e[5] = m[9];
-            e[6] = nu; e[7] = cS; e[8] = R(1) / (R(5) * Tc);
+            e[6] = nu; e[7] = cS; e[8] = R(1) / (R(5) * Tc); e[9] = Tabs<R>::ijd(T)[s];
         }
-        const R ip0 = R(1.0 / T.p0), Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
-        R *x = sc + c * 8;
+        const R ip0 = Tabs<R>::sc(T, SC_IP0), Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
+        R *x = sc + tid * 8;
         x[0] = sT; x[1] = a; x[2] = R(0.5) * a * a;
         // g_y coefficients b_l = E[He_l(u' + sqrt(T') Y)] / l!: b_{l+1} = (u' b_l + (T'-1) b_{l-1}) / (l+1)
-        if (c < kTile) {
-            const R uq = uy * ip0, tm1 = Tp - R(1);
-            R *b = bb + c * (Ny + 1);
-            R bm = R(1), bl = uq;
-            b[0] = R(1);
-            if (Ny >= 1) b[1] = uq;
-            for (int l = 1; l < Ny; ++l) {
-                const R bn = (uq * bl + tm1 * bm) * Tabs<R>::inv_l(T, l + 1);
-                bm = bl;
-                bl = bn;
-                b[l + 1] = bn;
-            }
+        const R uq = uy * ip0, tm1 = Tp - R(1);
+        const R *invl = tab + E.invl;
+        R *b = bb + tid * (Ny + 1);
+        R bm = R(1), bl = uq;
+        b[0] = R(1);
+        b[1] = uq;
+        for (int l = 1; l < Ny; ++l) {
+            const R bn = (uq * bl + tm1 * bm) * invl[l + 1];
+            bm = bl;
+            bl = bn;
+            b[l + 1] = bn;
         }
     }
     __syncthreads();
     // weights r_k^{+-} = W_k exp(+-a Y_k - a^2/2) of every (node, projection node)
-    const R *Yk = Tabs<R>::Yk(T), *Wk = Tabs<R>::Wk(T);
-    for (int idx = tid; idx < kTile * K; idx += kThreads) {
-        const int c = idx / K, k = idx - c * K;
-        const R *x = sc + c * 8;
+    const R *Yk = tab + E.Yk, *Wk = tab + E.Wk;
+    const int nk = nn * K;
+    for (int idx = tid; idx < nk; idx += kThreads) {
+        const int i = idx / K, k = idx - i * K;
+        const R *x = sc + i * 8;
         const R Y = Yk[k], W = Wk[k];
-        rpm[(c * 2) * K + k] = W * exp(x[1] * Y - x[2]);
-        rpm[(c * 2 + 1) * K + k] = W * exp(-x[1] * Y - x[2]);
+        rpm[(i * 2) * K + k] = W * exp(x[1] * Y - x[2]);
+        rpm[(i * 2 + 1) * K + k] = W * exp(-x[1] * Y - x[2]);
     }
     // projection coefficients c^{+-}_l = sum_k r_k^{+-} h_l(sqrt(T') Y_k), in blocks of kLB orders:
     // recurrence state per (node, projection node) kept in registers across blocks
     constexpr int kItems = (kTile * kMaxK + kThreads - 1) / kThreads;
     R zt[kItems], h[kItems], hp[kItems];
-    const R *alpha = Tabs<R>::alpha(T);
-    const R h0 = R(1.0 / T.sbeta[0]);
+    const R *alpha = tab + E.alpha, *sbeta = tab + E.sbeta, *isbeta = tab + E.isbeta;
+    const R h0 = Tabs<R>::sc(T, SC_H0);
 #pragma unroll
     for (int it = 0; it < kItems; ++it) {
         const int idx = tid + it * kThreads;
-        const int c = idx / K, k = idx - c * K;
+        const int i = idx / K, k = idx - i * K;
         zt[it] = R(0);
-        if (idx < kTile * K) zt[it] = sc[c * 8] * Yk[k];
+        if (idx < nk) zt[it] = sc[i * 8] * Yk[k];
         h[it] = h0;
         hp[it] = R(0);
     }
     for (int lb = 0; lb <= N; lb += kLB) {
         const int le = min(N, lb + kLB - 1);
         for (int l = lb; l <= le; ++l) {
-            const R al = alpha[l], sb = Tabs<R>::sbeta(T, l), isb1 = Tabs<R>::isbeta(T, l + 1);
+            const R al = alpha[l], sb = sbeta[l], isb1 = isbeta[l + 1];
 #pragma unroll
             for (int it = 0; it < kItems; ++it) {
                 const int idx = tid + it * kThreads;
-                if (idx < kTile * K) H[(l - lb) * kTile * K + idx] = h[it];
+                if (idx < nk) H[(l - lb) * nk + idx] = h[it];
                 const R hn = ((zt[it] - al) * h[it] - sb * hp[it]) * isb1;
                 hp[it] = h[it];
                 h[it] = hn;
             }
         }
         __syncthreads();
-        const int nl = le - lb + 1;
-        for (int idx = tid; idx < kTile * 2 * nl; idx += kThreads) {
-            const int c = idx / (2 * nl), rem = idx - c * 2 * nl, sgn = rem / nl, jl = rem - sgn * nl;
-            const R *r = rpm + (c * 2 + sgn) * K, *hh = H + jl * kTile * K + c * K;
+        // 4 lanes per dot product (k strided by 4), partial states combined by shuffles
+        const int nl = le - lb + 1, items = nn * 2 * nl;
+        for (int base = 0; base < 4 * items; base += kThreads) {   // same trip count in every thread
+            const int i4 = base + tid, item = i4 >> 2, q = i4 & 3;
             Dot<R> d;
-            for (int k = 0; k < K; ++k) d.add(r[k], hh[k]);
-            cb[c * L.cstride + sgn * (N + 1) + lb + jl] = d.value();
+            int i = 0, sgn = 0, jl = 0;
+            if (item < items) {
+                i = item / (2 * nl);
+                const int rem = item - i * 2 * nl;
+                sgn = rem / nl;
+                jl = rem - sgn * nl;
+                const R *r = rpm + (i * 2 + sgn) * K, *hh = H + jl * nk + i * K;
+                for (int k = q; k < K; k += 4) d.add(r[k], hh[k]);
+            }
+            dot_combine(d, 1);
+            dot_combine(d, 2);
+            if (item < items && q == 0) cb[i * L.cstride + sgn * (N + 1) + lb + jl] = d.value();
         }
         __syncthreads();
     }
-    // factors: g_x/w at (node, a), g_y/w at (node, j); node fastest for coalesced stores
-    const R *hz = Tabs<R>::hz(T), *He = Tabs<R>::He(T);
-    for (int idx = tid; idx < G * kTile; idx += kThreads) {
-        const int i = idx / kTile, c = idx - i * kTile;
+    // factors: g_x/w at (node, a), g_y/w at (node, j)
+    const R *hz = tab + E.hz, *He = tab + E.He;
+    for (int idx = tid; idx < G * nn; idx += kThreads) {
+        const int ig = idx / nn, i = idx - ig * nn;
         Dot<R> d;
-        if (i < 2 * T.Qx) {
-            const int ii = i < T.Qx ? i : i - T.Qx;
-            const R *cc = cb + c * L.cstride + (i < T.Qx ? 0 : N + 1);
+        if (ig < 2 * T.Qx) {
+            const int ii = ig < T.Qx ? ig : ig - T.Qx;
+            const R *cc = cb + i * L.cstride + (ig < T.Qx ? 0 : N + 1);
             for (int l = 0; l <= N; ++l) d.add(hz[l * T.Qx + ii], cc[l]);
         } else {
-            const int jj = i - 2 * T.Qx;
-            const R *b = bb + c * (Ny + 1);
+            const int jj = ig - 2 * T.Qx;
+            const R *b = bb + i * (Ny + 1);
             for (int l = 0; l <= Ny; ++l) d.add(He[l * T.Qy + jj], b[l]);
         }
-        eqg[(size_t)i * kLanes + c] = d.value();
+        eqg[(size_t)ig * kLanes + cfirst + i * cstep] = d.value();
     }
 }
 
@@ -543,56 +634,63 @@ __device__ void block_wall_density(const DevTables &T, const R *phi, bool right,
     if (threadIdx.x == 0) {
         double s = right ? T.restOutR : T.restOutL;
         for (int k = 0; k < kWarps; ++k) s += wsum[k];
-        *out = -s / (right ? T.inR : T.inL);
+        *out = -s * (right ? T.dsc[SC_IINR] : T.dsc[SC_IINL]);
     }
     __syncthreads();
 }
 
-// Per-velocity data staged in shared memory for the chunk: p_x, p_y, w, ft_rest,
-// incoming wall values (phi, chi; left, right) minus ft_rest at the current n_w,
-// and the indices a, j.
-enum { VR_PX = 0, VR_PY, VR_W, VR_FR, VR_INL0, VR_INL1, VR_INR0, VR_INR1, VR_A, VR_J, kVRow };
-
 // Dynamic shared memory layout of the stage kernel. The pipeline region is
-// reused after the main loop for the moment reduction and the tile stage data.
+// reused after the main loop for the moment reduction and the node stage data
+// (EqScratch); `xch` receives the moment partials that the cluster's CTAs send
+// to this CTA for the nodes it owns.
 template <typename R>
 struct Layout {
-    size_t bar, pipe, fin, f0, g, vrow, misc, total;
+    size_t bar, pipe, fin, f0, g, eqm, vrow, xch, misc, total;
     __host__ __device__ Layout(int Qx, int Qy, int N, int Ny, int K, int vchunk)
     {
         size_t o = 0;
-        bar = o;  o = al(o + kPipe * sizeof(uint64_t));
+        bar = o;  o = al(o + (kPipe + 2) * sizeof(uint64_t));
         pipe = o;
         fin = o;
         f0 = fin + (size_t)kPipe * 2 * kSubV * kRowLen * sizeof(R);
-        size_t pipe_bytes = f0 + (size_t)kPipe * 2 * kSubV * kF0Len * sizeof(R) - pipe;
-        size_t red_bytes = (size_t)kWarps * kNumRaw * kLanes * sizeof(R);
-        size_t eq_bytes = EqScratch<R>(K, N, Ny).total;
-        size_t m = pipe_bytes > red_bytes ? pipe_bytes : red_bytes;
+        size_t m = f0 + (size_t)kPipe * 2 * kSubV * kF0Len * sizeof(R) - pipe;
+        const size_t eq_bytes = EqScratch<R>(K, N, Ny, Qx, Qy, node_cap(Qx, Qy, vchunk)).total;
         m = m > eq_bytes ? m : eq_bytes;
         o = al(o + m);
         g = o;    o = al(o + (size_t)(2 * Qx + Qy) * kLanes * sizeof(R));
+        eqm = o;  o = al(o + (size_t)kLanes * kEqM * sizeof(R));
         vrow = o; o = al(o + (size_t)vchunk * kVRow * sizeof(R));
+        xch = o;  o = al(o + (size_t)(kTile + kMaxCluster) * kNumRaw * sizeof(R));
         misc = o; o = al(o + 16 * sizeof(double));
         total = o + 128;   // slack for aligning the dynamic base
     }
     __host__ __device__ static size_t al(size_t x) { return (x + 127) / 128 * 128; }
+    // nodes per CTA in the cluster's equilibrium step: ceil(kTile / nchunk)
+    __host__ __device__ static int node_cap(int Qx, int Qy, int vchunk)
+    {
+        const int nch = (2 * Qx * Qy + vchunk - 1) / vchunk;
+        return (kTile + nch - 1) / nch;
+    }
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
-stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateMaps M, int stage, int rel,
-             double stop_eps)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
+stage_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevState S,
+             const __grid_constant__ StateMaps M, int stage, int rel, double stop_eps)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // TMA destinations want 128-byte aligned shared memory: align the base explicitly
     unsigned char *smem = smem_dyn + ((128 - (smem_addr(smem_dyn) & 127)) & 127);
     const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);   // [kPipe] rows, data, tables
+    uint64_t *bar_data = bar + kPipe, *bar_tab = bar + kPipe + 1;
     R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][2][kSubV][kRowLen]
     R *s_f0 = reinterpret_cast<R *>(smem + L.f0);         // [kPipe][2][kSubV][kF0Len]
     R *s_g = reinterpret_cast<R *>(smem + L.g);           // [2Qx + Qy][kLanes]
-    double *s_misc = reinterpret_cast<double *>(smem + L.misc);   // wsum[8], nwL, nwR, flag
+    R *s_eqm = reinterpret_cast<R *>(smem + L.eqm);       // [kTile][kEqM]
+    R *s_vrow = reinterpret_cast<R *>(smem + L.vrow);     // [vchunk][kVRow]
+    R *s_xch = reinterpret_cast<R *>(smem + L.xch);       // [nchunk][nn_max][kNumRaw]
+    double *s_misc = reinterpret_cast<double *>(smem + L.misc);   // wsum[8], nwL, nwR
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x, c0 = tile * kTile, chunk = blockIdx.y;
@@ -616,12 +714,16 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
     const int vbeg = chunk * T.vchunk;
     const int vend = min(V, vbeg + T.vchunk);
     const int nsub = (vend - vbeg + kSubV - 1) / kSubV;
+    const int nloc = min(kTile, T.Nx - c0);   // nodes of this tile inside the channel
     const uint32_t tx_bytes =
         (uint32_t)((2 * kSubV * kRowLen + (stage > 0 ? 2 * kSubV * kF0Len : 0)) * sizeof(R));
     const CUtensorMap *in_map = &M.in[in];
     // TMA x coordinates must be 16-byte aligned: start the boxes at multiples of 4 nodes
     const int x0 = ((c0 - 3) >> 2) << 2, off = c0 - 3 - x0;     // node s <-> column s - x0
     const int xf = (c0 >> 2) << 2, offf = c0 - xf;
+    const int ncap = Layout<R>::node_cap(T.Qx, T.Qy, T.vchunk);
+    const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, ncap);
+    const uint32_t tab_bytes = (uint32_t)(EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy).len * sizeof(R));
 
     auto issue = [&](int sub) {
         int p = sub % kPipe, v0 = vbeg + sub * kSubV;
@@ -637,66 +739,49 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
     };
 
     if (tid == 0) {
-        for (int p = 0; p < kPipe; ++p) mbar_init(&bar[p], 1);
+        for (int p = 0; p < kPipe + 2; ++p) mbar_init(&bar[p], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0)
+    cluster_arrive_relaxed();   // this CTA runs: the others may write into its shared memory after their wait
+    if (tid == 0) {
         for (int sub = 0; sub < min(kPipe, nsub); ++sub) issue(sub);
+        // ---- (1) the tile's stage data and the chunk's per-velocity rows, by bulk copies ----
+        const uint32_t gb = (uint32_t)(G * kLanes * sizeof(R)), eb = (uint32_t)(nloc * kEqM * sizeof(R));
+        const uint32_t vb = (uint32_t)((vend - vbeg) * kVRow * sizeof(R));
+        mbar_expect_tx(bar_data, gb + eb + vb);
+        bulk_load(s_g, static_cast<const R *>(S.eqg[in]) + (size_t)tile * G * kLanes, gb, bar_data);
+        bulk_load(s_eqm, static_cast<const R *>(S.eqm[in]) + (size_t)c0 * kEqM, eb, bar_data);
+        bulk_load(s_vrow, Tabs<R>::vrow(T) + (size_t)vbeg * kVRow, vb, bar_data);
+    }
 
     const R *Fin = static_cast<const R *>(S.F[in]);
     R *Fout = static_cast<R *>(S.F[out]);
     const size_t fstride = (size_t)V * T.Nxp;
 
-    // ---- (1) the tile's stage data (overlaps the first loads) ----
-    {
-        const R *src = static_cast<const R *>(S.eqg[in]) + (size_t)tile * G * kLanes;
-        for (int idx = tid; idx < G * kLanes; idx += kThreads) s_g[idx] = src[idx];
-    }
-    const int s = c0 + lane;
-    const bool active = lane < kTile && s < T.Nx;
-    R n_c = R(1), ux_c = R(0), uy_c = R(0), T_c = R(1), qx_c = R(0), qy_c = R(0), nu_c = R(0), cS_c = R(0),
-      i5T = R(0.2), ijd = R(0);
-    if (active) {
-        const R *e = static_cast<const R *>(S.eqm[in]) + (size_t)s * kEqM;
-        n_c = e[0]; ux_c = e[1]; uy_c = e[2]; T_c = e[3]; qx_c = e[4]; qy_c = e[5];
-        nu_c = e[6]; cS_c = e[7]; i5T = e[8];
-        ijd = Tabs<R>::ijd(T)[s];
-    }
-
-    // ---- (2) wall densities (tiles whose stencil reaches a wall) ----
+    // ---- (2) wall densities (tiles whose stencil reaches a wall), while the copies land ----
     const bool needL = c0 == 0;
     const bool needR = c0 + 33 >= T.Nx;
     if (needL) block_wall_density<R>(T, Fin, false, s_misc, &s_misc[8]);
     if (needR) block_wall_density<R>(T, Fin, true, s_misc, &s_misc[9]);
-    __syncthreads();
+    bool timed_out = __syncthreads_or(!mbar_wait(bar_data, 0));
+
+    const int s = c0 + lane;
+    const bool active = lane < nloc;
+    R n_c = R(1), ux_c = R(0), uy_c = R(0), T_c = R(1), qx_c = R(0), qy_c = R(0), nu_c = R(0), cS_c = R(0),
+      i5T = R(0.2), ijd = R(0);
+    if (active && !timed_out) {
+        const R *e = s_eqm + lane * kEqM;
+        n_c = e[0]; ux_c = e[1]; uy_c = e[2]; T_c = e[3]; qx_c = e[4]; qy_c = e[5];
+        nu_c = e[6]; cS_c = e[7]; i5T = e[8]; ijd = e[9];
+    }
+    const R nwL = R(needL ? s_misc[8] : 0.0), nwR = R(needR ? s_misc[9] : 0.0);
 
     // ---- (3) stream the chunk's velocity rows ----
     const R ca = R(stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0));
     const R cb = R(stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0));
-    const R dt = R(T.dt);
-    R *s_vrow = reinterpret_cast<R *>(smem + L.vrow);   // [vchunk][kVRow]
-    {
-        const R nwL = R(needL ? s_misc[8] : 0.0), nwR = R(needR ? s_misc[9] : 0.0);
-        const R *vel = Tabs<R>::vel(T);
-        for (int k = tid; k < vend - vbeg; k += kThreads) {
-            const int v = vbeg + k;
-            R *x = s_vrow + k * kVRow;
-            const R fr = vel[VC_FR * V + v];
-            x[VR_PX] = vel[VC_PX * V + v];
-            x[VR_PY] = vel[VC_PY * V + v];
-            x[VR_W] = vel[VC_W * V + v];
-            x[VR_FR] = fr;
-            x[VR_INL0] = nwL * vel[VC_FWL * V + v] - fr;
-            x[VR_INL1] = nwL * vel[VC_FWLT * V + v] - fr;
-            x[VR_INR0] = nwR * vel[VC_FWR * V + v] - fr;
-            x[VR_INR1] = nwR * vel[VC_FWRT * V + v] - fr;
-            x[VR_A] = R(T.vel_aj[v]);       // small integers, exact in either precision
-            x[VR_J] = R(T.vel_aj[V + v]);
-        }
-    }
-    __syncthreads();
+    const R dt = Tabs<R>::sc(T, SC_DT);
     const bool wall = needL || needR;
     const int ck = lane + 3 + off;          // column of node c0 + lane
 
@@ -704,12 +789,10 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
 #pragma unroll
     for (int m = 0; m < kNumRaw; ++m) acc[m] = R(0);
     R res = R(0);
-    bool timed_out = false;
 
-    for (int sub = 0; sub < nsub; ++sub) {
+    for (int sub = 0; sub < nsub && !timed_out; ++sub) {
         const int p = sub % kPipe;
-        if (!mbar_wait(&bar[p], (uint32_t)((sub / kPipe) & 1))) timed_out = true;
-        if (__syncthreads_or(timed_out)) {
+        if (__syncthreads_or(!mbar_wait(&bar[p], (uint32_t)((sub / kPipe) & 1)))) {
             timed_out = true;
             break;
         }
@@ -724,19 +807,24 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
         for (int q = 0; q < NQ; ++q) {
             kq[q] = sub * kSubV + warp + kWarps * q;
             ok[q] = vbeg + kq[q] < vend;
-            if (!ok[q]) kq[q] = sub * kSubV + warp;   // duplicate a valid row; results are discarded
+            if (!ok[q]) kq[q] = vend - vbeg - 1;   // the chunk's last velocity row; results are discarded
         }
         if (wall) {
             // ghost nodes: lanes 0-15 -> (velocity, field, side, node)
             if (lane < 8 * NQ) {
                 const int q = lane >> 3, fld = (lane >> 2) & 1, side = (lane >> 1) & 1, gi = lane & 1;
                 const int r = warp + kWarps * q;
-                const R *x = s_vrow + kq[q] * kVRow;
+                int kqq = kq[0];
+                bool okq = ok[0];
+#pragma unroll
+                for (int qq = 1; qq < NQ; ++qq)   // select, not a dynamic index (keeps kq, ok in registers)
+                    if (q == qq) { kqq = kq[qq]; okq = ok[qq]; }
+                const R *x = s_vrow + kqq * kVRow;
                 const bool pos = (int)x[VR_A] < T.Qx;
                 R *row = fin + (size_t)(fld * kSubV + r) * kRowLen;
-                if (ok[q] && side == 0 && needL) {        // nodes -1 (gi 0), -2 (gi 1)
+                if (okq && side == 0 && needL) {          // nodes -1 (gi 0), -2 (gi 1)
                     R g;
-                    if (pos) g = x[VR_INL0 + fld];
+                    if (pos) g = nwL * x[VR_FWL + fld] - x[VR_FR];
                     else {
                         const int cz = -x0;      // column of node 0
                         R f1 = row[cz], f2 = row[cz + 1], f3 = row[cz + 2], f4 = row[cz + 3];
@@ -744,9 +832,9 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
                                     : R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
                     }
                     row[-1 - gi - x0] = g;
-                } else if (ok[q] && side == 1 && needR) { // nodes Nx (gi 0), Nx+1 (gi 1)
+                } else if (okq && side == 1 && needR) {   // nodes Nx (gi 0), Nx+1 (gi 1)
                     R g;
-                    if (!pos) g = x[VR_INR0 + fld];
+                    if (!pos) g = nwR * x[VR_FWR + fld] - x[VR_FR];
                     else {
                         const int cl = T.Nx - 1 - x0;
                         R f1 = row[cl], f2 = row[cl - 1], f3 = row[cl - 2], f4 = row[cl - 3];
@@ -775,8 +863,9 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
                 fl[q] = weno5_2(v[0], v[1], v[2], v[3], v[4]);   // face c0 + lane
                 dd[q] = mk2(r0[ck], r1[ck]);
                 if (wall) {
-                    if (pos && s == 0) fl[q] = mk2(x[VR_INL0], x[VR_INL1]);
-                    if (!pos && s == T.Nx) fl[q] = mk2(x[VR_INR0], x[VR_INR1]);
+                    const R fr = x[VR_FR];
+                    if (pos && s == 0) fl[q] = mk2(nwL * x[VR_FWL] - fr, nwL * x[VR_FWLT] - fr);
+                    if (!pos && s == T.Nx) fl[q] = mk2(nwR * x[VR_FWR] - fr, nwR * x[VR_FWRT] - fr);
                 }
             }
 #pragma unroll
@@ -841,8 +930,8 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
                                           row[base + 4 * st]);
                     dd[q][fld] = row[ck];
                     if (wall) {
-                        if (posq[q] && s == 0) fl[q][fld] = x[VR_INL0 + fld];
-                        if (!posq[q] && s == T.Nx) fl[q][fld] = x[VR_INR0 + fld];
+                        if (posq[q] && s == 0) fl[q][fld] = nwL * x[VR_FWL + fld] - x[VR_FR];
+                        if (!posq[q] && s == T.Nx) fl[q][fld] = nwR * x[VR_FWR + fld] - x[VR_FR];
                     }
                 }
             }
@@ -896,66 +985,108 @@ stage_kernel(const DevTables T, const DevState S, const __grid_constant__ StateM
         if (tid == 0 && sub + kPipe < nsub) issue(sub + kPipe);
     }
 
+    const int rank = (int)cluster_ctarank(), nch = T.nchunk;
+    const int nn = (kTile - rank + nch - 1) / nch;          // nodes rank, rank + nch, ... of the tile
+    const int nnmax = (kTile + nch - 1) / nch;
+    unsigned char *scr = smem + L.pipe;                     // EqScratch
     if (timed_out) {
-        // give up: record it, let in-flight copies land (bounded), then leave
+        // give up: record it and let in-flight copies land (bounded); the CTA
+        // still takes part in the cluster barriers below, without touching data
         if (tid == 0) {
             atomicExch(&S.ctl->timeout, 1);
             for (int p = 0; p < kPipe; ++p) {
                 mbar_wait(&bar[p], 0);
                 mbar_wait(&bar[p], 1);
             }
+            mbar_wait(bar_data, 0);
         }
+        __syncthreads();
+        cluster_wait();
+        cluster_arrive();
+        cluster_wait();
         return;
     }
 
-    // ---- (4) publish the chunk's raw moment partials and the residual ----
-    R *s_red = reinterpret_cast<R *>(smem + L.pipe);   // [kWarps][kNumRaw][kLanes]
+    // ---- (4) the chunk's raw moment partials, sent to the CTAs that own the nodes ----
+    if (tid == 0) {   // the equilibrium tables, into the pipeline region that the loop no longer reads
+        mbar_expect_tx(bar_tab, tab_bytes);
+        bulk_load(scr + E.tab, Tabs<R>::eqtab(T), tab_bytes, bar_tab);
+    }
+    R *s_red = reinterpret_cast<R *>(scr);   // [kWarps][kNumRaw][kLanes], below E.tab
 #pragma unroll
     for (int m = 0; m < kNumRaw; ++m) s_red[(warp * kNumRaw + m) * kLanes + lane] = acc[m];
-    __syncthreads();
-    R *part = static_cast<R *>(S.part[out]);
-    for (int idx = tid; idx < kLanes * kNumRaw; idx += kThreads) {
-        const int c = idx & 31, m = idx >> 5, sn = c0 + c;
-        CSum<R> t;
-        for (int w2 = 0; w2 < kWarps; ++w2) t.add(s_red[(w2 * kNumRaw + m) * kLanes + c]);
-        if (c < kTile && sn < T.Nx) part[((size_t)chunk * kNumRaw + m) * T.Nxp + sn] = t.value();
-    }
-    if (chunk == 0 && active) {
-        R *sh = static_cast<R *>(S.shift[out]);
-        sh[s] = ux_c;
-        sh[T.Nxp + s] = uy_c;
-    }
     if (stage == 2) {
         R rr = res;
         for (int o = 16; o > 0; o >>= 1) rr = fmax(rr, __shfl_xor_sync(0xffffffffu, rr, o));
         if (lane == 0 && rr > R(0))
             atomicMax(&S.resid[step % kResidRing], (unsigned long long)__double_as_longlong((double)rr));
     }
-
-    // ---- the last chunk CTA of this tile builds the next stage's tile data ----
-    __threadfence();
     __syncthreads();
-    int *flag = reinterpret_cast<int *>(&s_misc[10]);
-    if (tid == 0) *flag = atomicAdd(&S.count[out][tile], 1) == T.nchunk - 1;
-    __syncthreads();
-    if (*flag) {
-        __threadfence();
-        tile_equilibrium<R>(T, S, out, tile, smem + L.pipe);
-        if (tid == 0) S.count[out][tile] = 0;
+    cluster_wait();   // every CTA of the cluster has started (pairs with the arrive at the top)
+    for (int idx = tid; idx < kTile * kNumRaw; idx += kThreads) {
+        const int c = idx / kNumRaw, m = idx - c * kNumRaw;
+        CSum<R> t;
+        for (int w2 = 0; w2 < kWarps; ++w2) t.add(s_red[(w2 * kNumRaw + m) * kLanes + c]);
+        const int owner = c % nch, i = c / nch;
+        st_cluster(&s_xch[((size_t)rank * nnmax + i) * kNumRaw + m], (uint32_t)owner, t.value());
     }
+    cluster_arrive();
+    cluster_wait();   // every chunk's partials of this CTA's nodes are in s_xch
+
+    // ---- (5) the next stage's data of this CTA's nodes ----
+    {
+        R *raw = reinterpret_cast<R *>(scr + E.raw);
+        R *shf = reinterpret_cast<R *>(scr + E.shf);
+        for (int idx = tid; idx < nn * kNumRaw; idx += kThreads) {
+            const int i = idx / kNumRaw, m = idx - i * kNumRaw;
+            CSum<R> t;
+            for (int ch = 0; ch < nch; ++ch) t.add(s_xch[((size_t)ch * nnmax + i) * kNumRaw + m]);
+            raw[idx] = t.value();
+        }
+        if (tid < kLanes) {   // warp 0, lane = node: the sums are about the input stage's mean velocity
+            shf[tid] = ux_c;
+            shf[kLanes + tid] = uy_c;
+        }
+    }
+    const bool tab_late = __syncthreads_or(!mbar_wait(bar_tab, 0));
+    if (tab_late) {
+        if (tid == 0) atomicExch(&S.ctl->timeout, 1);
+        return;
+    }
+    node_equilibrium<R>(T, S, out, tile, rank, nch, nn, ncap, scr);
 }
 
-// Stage data of every tile of buffer `buf` (after set-up or lbc_set_state).
+// Stage data of every tile of buffer `buf` from the chunk partials of
+// moments_partial_kernel (after set-up or lbc_set_state).
 template <typename R>
-__global__ void __launch_bounds__(kThreads) tile_equilibrium_kernel(DevTables T, DevState S, int buf)
+__global__ void __launch_bounds__(kThreads)
+tile_equilibrium_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevState S, int buf)
 {
     extern __shared__ __align__(16) unsigned char smem_eq[];
-    tile_equilibrium<R>(T, S, buf, blockIdx.x, smem_eq);
+    const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy);
+    R *tab = reinterpret_cast<R *>(smem_eq + E.tab);
+    R *raw = reinterpret_cast<R *>(smem_eq + E.raw);
+    R *shf = reinterpret_cast<R *>(smem_eq + E.shf);
+    const R *part = static_cast<const R *>(S.part);
+    const int c0 = blockIdx.x * kTile;
+    const int tlen = EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy).len;
+    for (int k = threadIdx.x; k < tlen; k += kThreads) tab[k] = Tabs<R>::eqtab(T)[k];
+    for (int idx = threadIdx.x; idx < kTile * kNumRaw; idx += kThreads) {
+        const int c = idx / kNumRaw, m = idx - c * kNumRaw, s = c0 + c;
+        CSum<R> acc;
+        if (s < T.Nx)
+            for (int ch = 0; ch < T.nchunk; ++ch) acc.add(part[((size_t)ch * kNumRaw + m) * T.Nxp + s]);
+        raw[idx] = acc.value();
+    }
+    if (threadIdx.x < 2 * kLanes) shf[threadIdx.x] = R(0);   // the partials are sums about p = 0
+    __syncthreads();
+    node_equilibrium<R>(T, S, buf, blockIdx.x, 0, 1, kTile, kTile, smem_eq);
 }
 
-// Raw moment sums (shift 0) of the deviation in buffer `buf`, per velocity chunk.
+// Raw moment sums (about p = 0) of the deviation in buffer `buf`, per velocity chunk.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) moments_partial_kernel(DevTables T, DevState S, int buf)
+__global__ void __launch_bounds__(kThreads)
+moments_partial_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevState S, int buf)
 {
     __shared__ double red[kWarps][kNumRaw][kLanes];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -980,28 +1111,23 @@ __global__ void __launch_bounds__(kThreads) moments_partial_kernel(DevTables T, 
 #pragma unroll
     for (int m = 0; m < kNumRaw; ++m) red[warp][m][lane] = acc[m];
     __syncthreads();
-    R *part = static_cast<R *>(S.part[buf]);
+    R *part = static_cast<R *>(S.part);
     for (int idx = tid; idx < kLanes * kNumRaw; idx += kThreads) {
         const int c = idx & 31, m = idx >> 5, sn = c0 + c;
         double t = 0.0;
         for (int w2 = 0; w2 < kWarps; ++w2) t += red[w2][m][c];
         if (c < kTile && sn < T.Nx) part[((size_t)chunk * kNumRaw + m) * T.Nxp + sn] = R(t);
     }
-    if (chunk == 0 && active) {
-        R *sh = static_cast<R *>(S.shift[buf]);
-        sh[s] = R(0);
-        sh[T.Nxp + s] = R(0);
-    }
 }
 
+// FP64 moments per node from the chunk partials of moments_partial_kernel.
 template <typename R>
-__global__ void finalize_moments_kernel(DevTables T, DevState S, int buf)
+__global__ void finalize_moments_kernel(DevTables T, DevState S)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= T.Nx) return;
-    const R *part = static_cast<const R *>(S.part[buf]);
-    const R *shift = static_cast<const R *>(S.shift[buf]);
-    const double sx = (double)shift[s], sy = (double)shift[T.Nxp + s];
+    const R *part = static_cast<const R *>(S.part);
+    const double sx = 0.0, sy = 0.0;
     double r[kNumRaw];
     rest_raw(T.restP, sx, sy, r);
     for (int m = 0; m < kNumRaw; ++m) {
@@ -1042,27 +1168,65 @@ cudaError_t stage_kernel_attributes(cudaFuncAttributes *fa)
 template <typename R>
 cudaError_t configure_kernels()
 {
-    const Layout<R> L(kMaxQ, kMaxQ, kMaxQ - 1, kMaxQ - 1, kMaxK, kMaxVChunk);
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(tile_equilibrium_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)EqScratch<R>(kMaxK, kMaxQ - 1, kMaxQ - 1).total);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tile_equilibrium_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    return e;
 }
 
+template <typename R>
+size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K)
+{
+    return EqScratch<R>(K, N, Ny, Qx, Qy).total;
+}
+
+// One cluster per tile: the tile's nchunk chunk CTAs (cluster dimension y).
 template <typename R>
 cudaError_t launch_stage(const DevTables &T, const DevState &S, const StateMaps &M, int stage, int rel,
                          double stop_eps, cudaStream_t st)
 {
     const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk);
-    dim3 grid(T.ntile, T.nchunk);
-    stage_kernel<R><<<grid, kThreads, L.total, st>>>(T, S, M, stage, rel, stop_eps);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(T.ntile, T.nchunk, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = L.total;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = (unsigned)T.nchunk;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, stage_kernel<R>, T, S, M, stage, rel, stop_eps);
+}
+
+template <typename R>
+cudaError_t stage_active_clusters(size_t smem, int nchunk, int *nclusters)
+{
+    *nclusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, nchunk, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = (unsigned)nchunk;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(nclusters, stage_kernel<R>, &cfg);
 }
 
 template <typename R>
 cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int buf, cudaStream_t st)
 {
-    tile_equilibrium_kernel<R><<<T.ntile, kThreads, EqScratch<R>(T.K, T.Nxe, T.Nye).total, st>>>(T, S, buf);
+    tile_equilibrium_kernel<R><<<T.ntile, kThreads, EqScratch<R>(T.K, T.Nxe, T.Nye, T.Qx, T.Qy).total, st>>>(T, S, buf);
     return cudaGetLastError();
 }
 
@@ -1075,9 +1239,9 @@ cudaError_t launch_moments_partial(const DevTables &T, const DevState &S, int bu
 }
 
 template <typename R>
-cudaError_t launch_finalize_moments(const DevTables &T, const DevState &S, int buf, cudaStream_t st)
+cudaError_t launch_finalize_moments(const DevTables &T, const DevState &S, cudaStream_t st)
 {
-    finalize_moments_kernel<R><<<(T.Nx + 127) / 128, 128, 0, st>>>(T, S, buf);
+    finalize_moments_kernel<R><<<(T.Nx + 127) / 128, 128, 0, st>>>(T, S);
     return cudaGetLastError();
 }
 
@@ -1101,7 +1265,9 @@ cudaError_t launch_ctl_bump(Ctl *ctl, long long k, cudaStream_t st)
                                          cudaStream_t);                                                         \
     template cudaError_t launch_tile_equilibrium<R>(const DevTables &, const DevState &, int, cudaStream_t);     \
     template cudaError_t launch_moments_partial<R>(const DevTables &, const DevState &, int, cudaStream_t);      \
-    template cudaError_t launch_finalize_moments<R>(const DevTables &, const DevState &, int, cudaStream_t);
+    template cudaError_t launch_finalize_moments<R>(const DevTables &, const DevState &, cudaStream_t);            \
+    template cudaError_t stage_active_clusters<R>(size_t, int, int *);                                             \
+    template size_t equilibrium_smem_bytes<R>(int, int, int, int, int);
 LBC_INSTANTIATE(float)
 LBC_INSTANTIATE(double)
 
