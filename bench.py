@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="chunk CTAs per tile of the batched launch (0: autotune; fix it to profile a shape)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="state precision of the timed run (fp32: the headline path)")
     return ap.parse_args()
@@ -125,7 +127,7 @@ def profiled_traffic(precision: str):
     or None when the kernel source changed since the counters were taken."""
     import hashlib
     src = os.path.join(ROOT, "paper_1810_07803_gb300", "csrc", "lbc_kernels.cu")
-    prof = os.path.join(ROOT, "profiles", f"stage_kernel_{precision}_c2.md")
+    prof = os.path.join(ROOT, "profiles", f"stage_batch_kernel_{precision}_c2.md")
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         fields = dict(ln.split(":", 1) for ln in open(prof).read().splitlines() if ln.count(":") == 1
@@ -181,6 +183,7 @@ def run_reference(args, rank):
 
 
 def time_steps(solvers, steps, warmup, flush):
+    """ms per step of single solvers stepped one after the other (L2 flushed between steps)."""
     import torch
     for _ in range(warmup):
         for s in solvers:
@@ -194,7 +197,25 @@ def time_steps(solvers, steps, warmup, flush):
             s.step(1)
         evs[k][1].record()
     torch.cuda.synchronize()
-    return sum(a.elapsed_time(b) for a, b in evs) / steps   # ms per step
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def time_batch(batch, steps, warmup, flush):
+    """(ms per step, ms per stage launch) of a batch, L2 flushed between steps.
+    The step is timed with events around it on the current stream (the batch's
+    stream); the stage launches with events the library records around each."""
+    import torch
+    batch.step(warmup)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stage_ms = 0.0
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record()
+        stage_ms += batch.step_timed(1)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps, stage_ms / (3 * steps)
 
 
 def main():
@@ -216,63 +237,70 @@ def main():
     if world > 1:
         dist.barrier()
 
-    solvers = [lbc.Solver(workloads.c2(d, precision=args.precision)) for d in workloads.C2_DELTAS]
-    V, Nx = solvers[0].V, solvers[0].Nx
+    params = [workloads.c2(d, precision=args.precision) for d in workloads.C2_DELTAS]
+    batch = lbc.Batch(params, cluster=args.cluster)
+    # cells per CTA: chosen by timing every feasible cluster size, unless fixed
+    cluster = batch.autotune(3) if args.cluster == 0 else batch.shape()[0]
+    nsol = batch.n
+    V, Nx = batch.V[0], batch.Nx[0]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms = time_steps(solvers, args.steps, args.warmup, flush)
+        ms, launch_ms = time_batch(batch, args.steps, args.warmup, flush)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
+        t = torch.tensor([ms, launch_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    units = len(solvers) * V * Nx
+        ms, launch_ms = (float(v) for v in t.tolist())
+    units = nsol * V * Nx
     value = units * world / (ms / 1e3)
 
-    # end to end through the public API: host state in, host moments out, every step
-    import numpy as np
-    host_states = [s.get_state() for s in solvers]
+    # end to end through the public API: host states in, host moments out, every step
+    host_states = [batch.get_state(i) for i in range(nsol)]
     e2e_steps = min(args.steps, 10)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for s, hs in zip(solvers, host_states):
-            s.set_state(hs)
-            s.step(1)
-            s.moments()
+        for i, hs in enumerate(host_states):
+            batch.set_state(i, hs)
+        batch.step(1)
+        for i in range(nsol):
+            batch.moments(i)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     h2d = sum(hs.nbytes for hs in host_states)
-    d2h = len(solvers) * lbc.NMOM * Nx * 8
+    d2h = nsol * lbc.NMOM * Nx * 8
 
     fp64 = None
     if not args.no_fp64 and args.precision == "fp32":
         s64 = [lbc.Solver(workloads.c2(d, precision="fp64")) for d in workloads.C2_DELTAS]
         ms64 = time_steps(s64, max(3, args.steps // 10), 2, flush)
         fp64 = {"value": len(s64) * V * Nx * world / (ms64 / 1e3), "ms_per_step": ms64,
-                "note": "same workload, FP64 state and arithmetic, one solve per launch"}
+                "note": "same workload, FP64 state and arithmetic, one solve per launch, solves in sequence"}
         for s in s64:
             s.close()
 
     peak, peak_kind = measured_hbm_peak()
-    launches_per_step = 4 * len(solvers)   # per solve and step: three stage kernels and the step-counter bump
+    launches_per_step = 4   # one batched launch per RK stage (all solves) and the step-counter bump
     bpu = BYTES_PER_UPDATE_FP32 if args.precision == "fp32" else BYTES_PER_UPDATE_FP64
-    achieved = bpu * units / (ms / 1e3) / 1e9
+    bytes_per_launch = bpu * units / 3   # one RK stage of every solve
+    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": workload_config(args.precision),
+        "config": dict(workload_config(args.precision), cluster=cluster,
+                       launch="one batched stage launch per RK stage for the four solves"),
         "e2e": {"value": units * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "path": "per step and solve: lbc_set_state(host f64) + lbc_step(1) + lbc_moments(host)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.precision),
-                     "kernel": "stage_kernel<float>" if args.precision == "fp32" else "stage_kernel<double>",
-                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bpu * V * Nx / 3},
+                     "kernel": "stage_batch_kernel<float>" if args.precision == "fp32" else "stage_batch_kernel<double>",
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "launch_ms": launch_ms},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
@@ -280,8 +308,7 @@ def main():
         line["fp64_plain"] = fp64
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
-    for s in solvers:
-        s.close()
+    batch.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -41,6 +41,8 @@
 #ifndef LBC_H
 #define LBC_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -88,9 +90,10 @@ typedef struct {
 /*
  * Creates a solver for one Couette problem and sets the rest Maxwellian
  * n = 1, u = 0, T = 1 at every node.
- *   params: copied. Requires 1 <= Qx <= 64, 1 <= Qy <= 64, 0 <= N < Q (and
- *           N >= 2 on both axes, so the equilibrium has a temperature),
- *           Nx >= 8, delta >= 0, T_w > 0, 0 <= stretch_A < 1, p0 > 0.
+ *   params: copied. Requires 1 <= Qx <= 64, 1 <= Qy <= 64, 2 Qx Qy <= 4096,
+ *           0 <= N < Q (and N >= 2 on both axes, so the equilibrium has a
+ *           temperature), Nx >= 8, delta >= 0, T_w > 0, 0 <= stretch_A < 1,
+ *           p0 > 0; the largest orders must also fit one CTA's shared memory.
  *   Automatic time step: dt = min(cfl * min_s(J_s deta) / max|p_x|, tau_min / 2),
  *   with tau_min the smallest relaxation time (Eq. tau) of the initial state
  *   and of the two walls at n = 1.
@@ -156,6 +159,54 @@ const char *lbc_last_error(void);
 lbc_status lbc_quadrature(int Q, int half_range, double *nodes, double *weights);
 lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, double T,
                            double *gx, double *gy);
+
+/*
+ * Batches: many independent Couette problems ("instances") stepped together,
+ * one stage kernel launch per RK stage for the whole batch (no counterpart in
+ * the paper, which solves one problem at a time; the discretisation of every
+ * instance is exactly that of lbc_create).
+ *
+ * Each tile of 31 nodes of each instance is one work item; its velocity set is
+ * split over `cluster` chunk CTAs that form one thread-block cluster. Work
+ * items are scheduled longest first; instances of any size, order and
+ * parameters mix freely. All instances of a batch share one precision.
+ *
+ * lbc_batch_create: params[n] (copied), n >= 1; cluster = chunk CTAs per tile
+ *   in [1, 16], or 0 to choose by a wave model of the whole batch.
+ *   Errors: LBC_EINVAL (message names the instance), LBC_ENOMEM, LBC_ECUDA.
+ * lbc_batch_step: nsteps RK-3 steps of every instance (enqueued only).
+ *   LBC_ENONFINITE if an instance is poisoned (lbc_batch_set_state clears it).
+ * lbc_batch_run_to_steady: every instance steps until its own residual (as in
+ *   lbc_run_to_steady) falls below `residual`, or max_steps more steps; an
+ *   instance that converged stops while the others go on. steps_done[n] and
+ *   final_residual[n] (caller-owned, either may be NULL) receive each
+ *   instance's steps taken by this call and its last step's residual.
+ *   LBC_ENOTCONV if any instance reached max_steps (the others' results hold).
+ * lbc_batch_moments / get_state / set_state / info: as the single-solver calls,
+ *   for instance i in [0, n).
+ * lbc_batch_shape: the launch shape (cluster size, work items, dynamic shared
+ *   memory bytes of one stage CTA).
+ * lbc_batch_autotune: for a batch whose instances have taken no step, times
+ *   trial_steps steps for every feasible cluster size and keeps the fastest;
+ *   the instances are at their initial (rest) state afterwards. *cluster
+ *   (may be NULL) receives the choice. Synchronises the stream.
+ */
+typedef struct lbc_batch lbc_batch;
+lbc_status lbc_batch_create(const lbc_params *params, int n, int cluster, void *cuda_stream, lbc_batch **out);
+lbc_status lbc_batch_step(lbc_batch *b, long nsteps);
+lbc_status lbc_batch_run_to_steady(lbc_batch *b, double residual, long max_steps, long *steps_done,
+                                   double *final_residual);
+lbc_status lbc_batch_moments(lbc_batch *b, int i, double *out, double *x);
+lbc_status lbc_batch_get_state(lbc_batch *b, int i, double *state);
+lbc_status lbc_batch_set_state(lbc_batch *b, int i, const double *state);
+lbc_status lbc_batch_info(const lbc_batch *b, int i, int *Nx, int *V, double *dt, long *steps_taken);
+lbc_status lbc_batch_shape(const lbc_batch *b, int *cluster, int *nwork, size_t *smem_bytes);
+lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster);
+/* As lbc_batch_step with eager launches, timing each stage launch with CUDA
+ * events on the batch's stream; *stage_ms receives the sum of the 3 nsteps
+ * stage-kernel durations (for roofline reports). Synchronises the stream. */
+lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms);
+void lbc_batch_destroy(lbc_batch *b);
 
 /*
  * Allocation-free stepping (the paper has no counterpart: this serves callers

@@ -1,48 +1,21 @@
-// C ABI of the solver (include/lbc.h): validation, set-up, device memory,
-// stepping (eager launches and CUDA graphs), run-to-steady, moments, state I/O.
+// C ABI of the solver (include/lbc.h): batches of Couette instances and the
+// single-instance solver built on them -- device memory, stepping through
+// CUDA graphs, run-to-steady, moments and state I/O.
 #include <algorithm>
 #include <cmath>
-#include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
 #include "lbc_device.h"
 
-namespace lbc {
-
-namespace {
-thread_local std::string g_err;
-constexpr int kGraphSteps = 64;   // RK-3 steps captured per CUDA graph
-}  // namespace
-
-void set_error(const std::string &msg) { g_err = msg; }
-
-}  // namespace lbc
-
 using namespace lbc;
 
-struct lbc_solver {
-    lbc_params p{};
-    HostTables tab;
-    DevTables T{};
-    DevState S{};
-    StateMaps M{};
-    cudaStream_t stream = nullptr;
-    bool fp32 = false;
-    bool poisoned = false;
-    long long steps = 0;             // completed steps
-    std::vector<double> x;
-    std::vector<double> frest;       // weight-divided rest Maxwellian per velocity (state origin)
-    void *table_block = nullptr;     // all constant tables, one allocation
-    void *state_block = nullptr;     // state, moment partials, control
-    cudaGraphExec_t graph = nullptr;
-    unsigned long long *h_resid = nullptr;   // pinned copy of the residual ring
-    Ctl *h_ctl = nullptr;                     // pinned copy of the control block
-};
-
 namespace {
+
+constexpr int kGraphSteps = 64;   // RK-3 steps captured per CUDA graph
 
 #define LBC_CUDA_TRY(call)                                                                   \
     do {                                                                                     \
@@ -53,70 +26,82 @@ namespace {
         }                                                                                    \
     } while (0)
 
-lbc_status fail(lbc_status st, const std::string &msg)
-{
-    set_error(msg);
-    return st;
-}
+struct InstHost {
+    lbc_params p{};
+    std::vector<double> x;       // node positions
+    std::vector<double> frest;   // weight-divided rest Maxwellian per velocity (state origin)
+    long long steps = 0;         // completed steps
+};
 
-lbc_status validate(const lbc_params &p, int &Nxe, int &Nye)
-{
-    if (p.Qx < 1 || p.Qx > kMaxQ || p.Qy < 1 || p.Qy > kMaxQ) return fail(LBC_EINVAL, "Qx and Qy must be in [1, 64]");
-    Nxe = p.Nexp_x ? p.Nexp_x : p.Qx - 1;
-    Nye = p.Nexp_y ? p.Nexp_y : p.Qy - 1;
-    if (Nxe < 2 || Nxe >= p.Qx) return fail(LBC_EINVAL, "expansion order Nexp_x must satisfy 2 <= N < Qx");
-    if (Nye < 2 || Nye >= p.Qy) return fail(LBC_EINVAL, "expansion order Nexp_y must satisfy 2 <= N < Qy");
-    if (p.Nx < 8 || p.Nx > (1 << 24)) return fail(LBC_EINVAL, "Nx must be in [8, 2^24]");
-    if (!(p.delta >= 0.0) || !std::isfinite(p.delta)) return fail(LBC_EINVAL, "delta must be finite and >= 0");
-    if (!(p.T_left > 0.0) || !(p.T_right > 0.0)) return fail(LBC_EINVAL, "wall temperatures must be > 0");
-    if (!std::isfinite(p.u_left) || !std::isfinite(p.u_right)) return fail(LBC_EINVAL, "wall velocities must be finite");
-    if (!(p.stretch_A >= 0.0 && p.stretch_A < 1.0)) return fail(LBC_EINVAL, "stretch_A must be in [0, 1)");
-    if (p.p0 < 0.0 || !std::isfinite(p.p0)) return fail(LBC_EINVAL, "p0 must be > 0 (0 selects 1)");
-    if (p.cfl < 0.0 || p.dt < 0.0) return fail(LBC_EINVAL, "cfl and dt must be >= 0");
-    if (!std::isfinite(p.Pr) || p.Pr <= 0.0) return fail(LBC_EINVAL, "Pr must be > 0");
-    if (p.mu_law != LBC_MU_POWER) return fail(LBC_EINVAL, "only the power-law viscosity (LBC_MU_POWER) is built");
-    if (!std::isfinite(p.omega)) return fail(LBC_EINVAL, "omega must be finite");
-    if (p.precision != LBC_FP64 && p.precision != LBC_FP32_STATE) return fail(LBC_EINVAL, "unknown precision");
-    return LBC_OK;
-}
+size_t r256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+struct lbc_batch {
+    int n = 0;
+    bool fp32 = false;
+    bool single = false;          // one instance: the stage kernel with the descriptor as a parameter
+    int cluster = 0;              // chunk CTAs per tile
+    size_t smem = 0;              // dynamic shared memory of a stage launch
+    cudaStream_t stream = nullptr;
+    std::vector<InstHost> ih;
+    std::vector<Inst> inst;       // host images of the device descriptors
+    Inst *d_inst = nullptr;       // [n] in table_block
+    int2 *d_work = nullptr;       // [nwork] (instance, tile), longest CTAs first
+    int nwork = 0;
+    void *table_block = nullptr;  // tables of every instance, descriptors, work list
+    void *state_block = nullptr;  // states, stage data, partials, residual rings, control
+    Ctl *d_ctl = nullptr;         // [n]
+    double *d_last = nullptr;     // [n] last residual of each instance
+    Ctl *h_ctl = nullptr;         // pinned [n]
+    double *h_last = nullptr;     // pinned [n]
+    bool steady_mode = false;     // the device control blocks hold run-to-steady settings
+    bool poisoned = false;        // some instance holds a NaN/Inf
+    cudaGraphExec_t graph = nullptr;
+};
+
+struct lbc_solver {
+    lbc_batch *b = nullptr;
+};
+
+namespace {
 
 template <typename R>
-cudaError_t launch_step_range(lbc_solver *s, int rel0, int nsteps, double stop_eps)
+cudaError_t launch_steps_t(lbc_batch *b, int nsteps, cudaStream_t st)
 {
     for (int k = 0; k < nsteps; ++k)
-        for (int st = 0; st < 3; ++st) {
-            cudaError_t e = launch_stage<R>(s->T, s->S, s->M, st, rel0 + k, stop_eps, s->stream);
+        for (int stage = 0; stage < 3; ++stage) {
+            cudaError_t e = b->single ? launch_stage<R>(b->inst[0], b->smem, stage, k, st)
+                                      : launch_stage_batch<R>(b->d_inst, b->d_work, b->nwork, b->cluster, b->smem,
+                                                              stage, k, st);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
 }
 
-cudaError_t launch_steps(lbc_solver *s, int rel0, int nsteps, double stop_eps)
+// nsteps RK-3 steps of every instance, then the step counters.
+cudaError_t launch_steps(lbc_batch *b, int nsteps, cudaStream_t st)
 {
-    return s->fp32 ? launch_step_range<float>(s, rel0, nsteps, stop_eps)
-                   : launch_step_range<double>(s, rel0, nsteps, stop_eps);
+    cudaError_t e = b->fp32 ? launch_steps_t<float>(b, nsteps, st) : launch_steps_t<double>(b, nsteps, st);
+    if (e == cudaSuccess) e = launch_ctl_bump(b->d_ctl, b->n, nsteps, st);
+    return e;
 }
 
-// Captures kGraphSteps plain steps (no early stop) plus the step-counter bump
-// into one CUDA graph, launched by lbc_step for every full group of steps.
-lbc_status ensure_graph(lbc_solver *s)
+// kGraphSteps steps and the counter bump captured once; replayed by step and run-to-steady.
+lbc_status ensure_graph(lbc_batch *b)
 {
-    if (s->graph) return LBC_OK;
+    if (b->graph) return LBC_OK;
     cudaStream_t cap;
     LBC_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaStream_t keep = s->stream;
-        s->stream = cap;
-        e = launch_steps(s, 0, kGraphSteps, 0.0);
-        if (e == cudaSuccess) e = launch_ctl_bump(s->S.ctl, kGraphSteps, cap);
-        s->stream = keep;
+        e = launch_steps(b, kGraphSteps, cap);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
     }
     if (e == cudaSuccess) {
-        e = cudaGraphInstantiate(&s->graph, g, 0);
+        e = cudaGraphInstantiate(&b->graph, g, 0);
         cudaGraphDestroy(g);
     }
     cudaStreamDestroy(cap);
@@ -124,512 +109,618 @@ lbc_status ensure_graph(lbc_solver *s)
     return LBC_OK;
 }
 
-}  // namespace
-
-namespace lbc {
-
-namespace {
-struct DPiece { const std::vector<double> *src; const double **dst; };
-struct FPiece { const std::vector<double> *src; const float **dst; };
-
-// The device table block: FP64 pieces (each padded to 32 doubles), then FP32
-// copies (each padded to 64 floats), then the velocity index table.
-std::vector<DPiece> dpieces(const ProblemSetup &ps, DevTables &T)
+lbc_status run_steps(lbc_batch *b, long nsteps)
 {
-    const HostTables &t = ps.t;
-    return {{&ps.inv_jdeta, &T.inv_jdeta}, {&t.zx, &T.zx}, {&t.wx, &T.wx}, {&t.yy, &T.yy}, {&t.wy, &T.wy},
-            {&t.alpha, &T.alpha}, {&t.sbeta, &T.sbeta}, {&t.hz, &T.hz}, {&t.Yk, &T.Yk}, {&t.Wk, &T.Wk},
-            {&t.He, &T.He}, {&ps.fwL, &T.fwL}, {&ps.fwR, &T.fwR}, {&ps.frest, &T.frest}, {&ps.vel, &T.d_vel},
-            {&ps.vrow, &T.d_vrow}, {&ps.eqtab, &T.d_eqtab}};
-}
-std::vector<FPiece> fpieces(const ProblemSetup &ps, DevTables &T)
-{
-    const HostTables &t = ps.t;
-    return {{&t.hz, &T.f_hz}, {&t.He, &T.f_He}, {&t.alpha, &T.f_alpha}, {&ps.isb, &T.f_isbeta},
-            {&t.sbeta, &T.f_sbeta}, {&t.Yk, &T.f_Yk}, {&t.Wk, &T.f_Wk}, {&ps.invl, &T.f_inv_l},
-            {&ps.vel, &T.f_vel}, {&ps.inv_jdeta, &T.f_inv_jdeta}, {&ps.vrow, &T.f_vrow}, {&ps.eqtab, &T.f_eqtab}};
-}
-size_t pad_d(size_t n) { return (n + 31) / 32 * 32; }
-size_t pad_f(size_t n) { return (n + 63) / 64 * 64; }
-}  // namespace
-
-bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std::string &err)
-{
-    if (!build_tables(p.Qx, p.Qy, Nxe, Nye, p.p0, ps.t, err)) return false;
-    const HostTables &t = ps.t;
-    ps.Nxe = Nxe;
-    ps.Nye = Nye;
-    const int V = t.V;
-    if (V > kMaxV) {
-        err = "velocity set 2 Qx Qy = " + std::to_string(V) + " exceeds " + std::to_string(kMaxV);
-        return false;
+    while (nsteps >= kGraphSteps) {
+        lbc_status st = ensure_graph(b);
+        if (st != LBC_OK) return st;
+        LBC_CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+        nsteps -= kGraphSteps;
     }
-    make_grid(p.Nx, p.stretch_A, ps.x, ps.inv_jdeta, ps.deta, ps.min_jdeta);
-
-    // time step: CFL on the smallest cell, and half the smallest relaxation time
-    double dt = p.dt > 0 ? p.dt : p.cfl * ps.min_jdeta / (t.zx.back() * p.p0);
-    if (p.dt <= 0 && p.delta > 0)
-        for (double Tw : {1.0, p.T_left, p.T_right})
-            dt = std::min(dt, 0.5 * std::pow(Tw, p.omega - 1.0) / (p.delta * std::sqrt(2.0)));
-    ps.dt = dt;
-
-    // wall Maxwellians (unit density), incoming unit fluxes, rest Maxwellian
-    std::vector<double> gx(2 * p.Qx), gy(p.Qy);
-    ps.fwL.resize(V); ps.fwR.resize(V); ps.frest.resize(V);
-    equilibrium_host(t, 0.0, p.u_left, p.T_left, gx.data(), gy.data());
-    for (int v = 0; v < V; ++v) ps.fwL[v] = gx[v / p.Qy] * gy[v % p.Qy];
-    equilibrium_host(t, 0.0, p.u_right, p.T_right, gx.data(), gy.data());
-    for (int v = 0; v < V; ++v) ps.fwR[v] = gx[v / p.Qy] * gy[v % p.Qy];
-    equilibrium_host(t, 0.0, 0.0, 1.0, gx.data(), gy.data());
-    for (int v = 0; v < V; ++v) ps.frest[v] = gx[v / p.Qy] * gy[v % p.Qy];
-    ps.vel.assign((size_t)kVelCols * V, 0.0);
-    ps.aj.assign(2 * (size_t)V, 0);
-    for (int v = 0; v < V; ++v) {
-        const int a = v / p.Qy, j = v % p.Qy, i = a < p.Qx ? a : a - p.Qx;
-        const double px = (a < p.Qx ? 1.0 : -1.0) * p.p0 * t.zx[i], py = p.p0 * t.yy[j], w = t.wx[i] * t.wy[j];
-        if (px > 0) { ps.inL += px * w * ps.fwL[v]; ps.restOutR += px * w * ps.frest[v]; }
-        else        { ps.inR += px * w * ps.fwR[v]; ps.restOutL += px * w * ps.frest[v]; }
-        const double pw[10] = {1, px, py, px * px, px * py, py * py, px * px * px, px * px * py, px * py * py,
-                               py * py * py};
-        for (int k = 0; k < 10; ++k) ps.restP[k] += pw[k] * w * ps.frest[v];
-        const double cols[kVelCols] = {px, py, w, ps.frest[v], ps.fwL[v], p.T_left * ps.fwL[v], ps.fwR[v],
-                                       p.T_right * ps.fwR[v]};
-        for (int c = 0; c < kVelCols; ++c) ps.vel[(size_t)c * V + v] = cols[c];
-        ps.aj[v] = a;
-        ps.aj[V + v] = j;
-    }
-    ps.isb.resize(t.sbeta.size());
-    for (size_t k = 0; k < ps.isb.size(); ++k) ps.isb[k] = 1.0 / t.sbeta[k];
-    ps.invl.assign(kMaxQ + 2, 0.0);
-    for (int l = 1; l < kMaxQ + 2; ++l) ps.invl[l] = 1.0 / l;
-    ps.vrow.assign((size_t)V * kVRow, 0.0);
-    for (int v = 0; v < V; ++v) {
-        const int cols[8] = {VC_PX, VC_PY, VC_W, VC_FR, VC_FWL, VC_FWLT, VC_FWR, VC_FWRT};
-        for (int c = 0; c < 8; ++c) ps.vrow[(size_t)v * kVRow + c] = ps.vel[(size_t)cols[c] * V + v];
-        ps.vrow[(size_t)v * kVRow + VR_A] = ps.aj[v];
-        ps.vrow[(size_t)v * kVRow + VR_J] = ps.aj[V + v];
-    }
-    if ((int)t.alpha.size() < Nxe + 2 || (int)t.sbeta.size() < Nxe + 2) {
-        err = "internal: recurrence table too short";
-        return false;
-    }
-    const EqTab E(Nxe, Nye, t.K, p.Qx, p.Qy);
-    ps.eqtab.assign(E.len, 0.0);
-    for (int l = 0; l < Nxe + 2; ++l) {
-        ps.eqtab[E.alpha + l] = t.alpha[l];
-        ps.eqtab[E.sbeta + l] = t.sbeta[l];
-        ps.eqtab[E.isbeta + l] = 1.0 / t.sbeta[l];
-    }
-    for (int l = 1; l < Nye + 2; ++l) ps.eqtab[E.invl + l] = 1.0 / l;
-    for (int k = 0; k < t.K; ++k) {
-        ps.eqtab[E.Yk + k] = t.Yk[k];
-        ps.eqtab[E.Wk + k] = t.Wk[k];
-    }
-    for (int k = 0; k < (Nxe + 1) * p.Qx; ++k) ps.eqtab[E.hz + k] = t.hz[k];
-    for (int k = 0; k < (Nye + 1) * p.Qy; ++k) ps.eqtab[E.He + k] = t.He[k];
-
-    DevTables dummy{};
-    size_t nd = 0, nf = 0;
-    for (auto &pc : dpieces(ps, dummy)) nd += pad_d(pc.src->size());
-    for (auto &pc : fpieces(ps, dummy)) nf += pad_f(pc.src->size());
-    const size_t dbytes = nd * sizeof(double), fbytes = nf * sizeof(float);
-    ps.blob.assign(dbytes + fbytes + ps.aj.size() * sizeof(int), 0);
-    size_t off = 0;
-    for (auto &pc : dpieces(ps, dummy)) {
-        std::memcpy(ps.blob.data() + off * sizeof(double), pc.src->data(), pc.src->size() * sizeof(double));
-        off += pad_d(pc.src->size());
-    }
-    off = 0;
-    for (auto &pc : fpieces(ps, dummy)) {
-        float *d = reinterpret_cast<float *>(ps.blob.data() + dbytes) + off;
-        for (size_t k = 0; k < pc.src->size(); ++k) d[k] = (float)(*pc.src)[k];
-        off += pad_f(pc.src->size());
-    }
-    std::memcpy(ps.blob.data() + dbytes + fbytes, ps.aj.data(), ps.aj.size() * sizeof(int));
-    return true;
-}
-
-void bind_tables(const ProblemSetup &ps, const lbc_params &p, const void *dev, DevTables &T)
-{
-    const HostTables &t = ps.t;
-    const char *base = static_cast<const char *>(dev);
-    size_t off = 0;
-    for (auto &pc : dpieces(ps, T)) {
-        *pc.dst = reinterpret_cast<const double *>(base) + off;
-        off += pad_d(pc.src->size());
-    }
-    const size_t dbytes = off * sizeof(double);
-    off = 0;
-    for (auto &pc : fpieces(ps, T)) {
-        *pc.dst = reinterpret_cast<const float *>(base + dbytes) + off;
-        off += pad_f(pc.src->size());
-    }
-    T.vel_aj = reinterpret_cast<const int *>(base + dbytes + off * sizeof(float));
-
-    T.Nx = p.Nx;
-    T.Nxp = (p.Nx + 31) / 32 * 32;
-    T.Qx = p.Qx; T.Qy = p.Qy; T.Nxe = ps.Nxe; T.Nye = ps.Nye; T.K = t.K; T.V = t.V;
-    T.ntile = (p.Nx + kTile - 1) / kTile;
-    T.p0 = p.p0; T.dt = ps.dt; T.delta = p.delta; T.Pr = p.Pr; T.omega = p.omega;
-    T.TL = p.T_left; T.TR = p.T_right; T.inL = ps.inL; T.inR = ps.inR;
-    T.restOutL = ps.restOutL; T.restOutR = ps.restOutR;
-    for (int k = 0; k < 10; ++k) {
-        T.restP[k] = ps.restP[k];
-        T.f_restP[k] = (float)ps.restP[k];
-    }
-    T.dsc[SC_NU] = p.delta * std::sqrt(2.0);
-    T.dsc[SC_EXPO] = 1.0 - p.omega;
-    T.dsc[SC_1MPR] = 1.0 - p.Pr;
-    T.dsc[SC_IP0] = 1.0 / p.p0;
-    T.dsc[SC_H0] = 1.0 / t.sbeta[0];
-    T.dsc[SC_DT] = ps.dt;
-    T.dsc[SC_IINL] = 1.0 / ps.inL;
-    T.dsc[SC_IINR] = 1.0 / ps.inR;
-    for (int k = 0; k < kNumSc; ++k) T.fsc[k] = (float)T.dsc[k];
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_cols)
-{
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !ptr)
-            return fail(LBC_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-        fn = reinterpret_cast<EncodeTiledFn>(ptr);
-    }
-    const size_t esz = fp32 ? 4 : 8;
-    cuuint64_t dims[2] = {(cuuint64_t)Nxp, (cuuint64_t)(2 * V)};
-    cuuint64_t strides[1] = {(cuuint64_t)Nxp * esz};
-    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)kSubV};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(LBC_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+    if (nsteps > 0) LBC_CUDA_TRY(launch_steps(b, (int)nsteps, b->stream));
     return LBC_OK;
 }
 
-// Velocity chunks per tile (multiples of the pipeline's kSubV rows, at most
-// kMaxCluster chunks: they form one cluster): the count that minimises a wave
-// model of the launch, waves x (rows per CTA + per-CTA overhead), with the
-// clusters the device can hold at once.
-lbc_status choose_launch_shape(bool fp32, DevTables &T)
+lbc_status upload_ctl(lbc_batch *b, int first, int count)
 {
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(LBC_ECUDA, "no CUDA device");
-    cudaError_t e = fp32 ? configure_kernels<float>() : configure_kernels<double>();
-    if (e != cudaSuccess) return fail(LBC_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t eqs = fp32 ? equilibrium_smem_bytes<float>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K)
-                            : equilibrium_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K);
-    if (eqs > (size_t)optin)
-        return fail(LBC_EINVAL, "quadrature orders too large for the shared memory of one CTA (" +
-                                    std::to_string(eqs) + " bytes)");
-    const int subs = std::min((T.V + kSubV - 1) / kSubV, kMaxVChunk / kSubV);
-    double best = 1e300;
-    T.vchunk = T.nchunk = 0;
-    for (int nsub = 1; nsub <= subs; ++nsub) {
-        const int vch = nsub * kSubV, nch = (T.V + vch - 1) / vch;
-        if (nch > kMaxCluster) continue;
-        const size_t smem = fp32 ? stage_smem_bytes<float>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vch)
-                                 : stage_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vch);
-        if (smem > (size_t)optin) continue;
-        int ncl = 0;
-        e = fp32 ? stage_active_clusters<float>(smem, nch, &ncl) : stage_active_clusters<double>(smem, nch, &ncl);
-        if (e != cudaSuccess || ncl <= 0) {
-            cudaGetLastError();   // an unschedulable cluster shape is not an error of the solver
-            continue;
-        }
-        const double waves = std::ceil((double)T.ntile / ncl);
-        const double cost = waves * (vch + 24.0);
-        if (cost < best - 1e-9) { best = cost; T.vchunk = vch; T.nchunk = nch; }
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->d_ctl + first, b->h_ctl + first, count * sizeof(Ctl), cudaMemcpyHostToDevice,
+                                 b->stream));
+    return LBC_OK;
+}
+
+// Device control blocks -> h_ctl (synchronises); reports a timeout, records non-finite instances.
+lbc_status read_ctl(lbc_batch *b)
+{
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    bool any = false;
+    for (int i = 0; i < b->n; ++i) {
+        if (b->h_ctl[i].timeout) return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
+        any = any || b->h_ctl[i].nonfinite;
     }
-    if (T.nchunk == 0)
-        return fail(LBC_EINVAL, "no schedulable cluster shape for a velocity set of " + std::to_string(T.V));
+    if (any) {
+        b->poisoned = true;
+        return fail(LBC_ENONFINITE, "non-finite value in the state");
+    }
     return LBC_OK;
 }
 
-}  // namespace lbc
-
-extern "C" {
-
-const char *lbc_last_error(void) { return g_err.c_str(); }
-
-lbc_status lbc_quadrature(int Q, int half_range, double *nodes, double *weights)
+// Device control blocks for plain stepping: counters = completed steps, no early stop.
+lbc_status plain_mode(lbc_batch *b)
 {
-    if (!nodes || !weights) return fail(LBC_EINVAL, "nodes and weights must not be NULL");
-    std::vector<double> z, w;
-    bool ok = half_range ? half_range_rule(Q, z, w) : full_range_rule(Q, z, w);
-    if (!ok) return fail(LBC_EINVAL, "Q must be in [1, 64]");
-    std::copy(z.begin(), z.end(), nodes);
-    std::copy(w.begin(), w.end(), weights);
+    if (!b->steady_mode) return LBC_OK;
+    for (int i = 0; i < b->n; ++i) {
+        Ctl &c = b->h_ctl[i];
+        c.base = b->ih[i].steps;
+        c.check_from = b->ih[i].steps;
+        c.stop_eps = 0.0;
+        c.stop_step = 0;
+        c.stopped = 0;
+    }
+    b->steady_mode = false;
+    return upload_ctl(b, 0, b->n);
+}
+
+// Stage data of buffer 0 of instance i from its state (after create or set_state).
+lbc_status rebuild_stage_data(lbc_batch *b, int i)
+{
+    const Inst &I = b->inst[i];
+    LBC_CUDA_TRY(b->fp32 ? launch_moments_partial<float>(I.T, I.S, 0, b->stream)
+                         : launch_moments_partial<double>(I.T, I.S, 0, b->stream));
+    LBC_CUDA_TRY(b->fp32 ? launch_tile_equilibrium<float>(I.T, I.S, 0, b->stream)
+                         : launch_tile_equilibrium<double>(I.T, I.S, 0, b->stream));
     return LBC_OK;
 }
 
-lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, double T, double *gx, double *gy)
+// Per-instance device bytes (partials sized for the largest cluster, so a
+// batch can change its launch shape without reallocating).
+struct StateSizes {
+    size_t f, eqm, eqg, part, resid, mom, total;
+    StateSizes(const DevTables &T, bool fp32)
+    {
+        const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+        f = r256(2 * (size_t)T.V * T.Nxp * esz);
+        eqm = r256((size_t)T.Nxp * kEqM * esz);
+        eqg = r256((size_t)T.ntile * (2 * T.Qx + T.Qy) * kLanes * esz);
+        part = r256((size_t)kMaxCluster * kNumRaw * T.Nxp * esz);
+        resid = kResidRing * sizeof(unsigned long long);
+        mom = r256((size_t)LBC_NMOM * T.Nxp * sizeof(double));
+        total = 3 * (f + eqm + eqg) + part + resid + mom;
+    }
+};
+
+// Work list: every (instance, tile), instances with the longest CTAs first.
+void build_work(lbc_batch *b, std::vector<int2> &work)
 {
-    if (!params || !gx || !gy) return fail(LBC_EINVAL, "NULL argument");
-    if (!(T > 0.0)) return fail(LBC_EINVAL, "T must be > 0");
-    lbc_params p = *params;
-    if (p.p0 == 0.0) p.p0 = 1.0;
-    int Nxe, Nye;
-    lbc_params q = p;
-    if (q.Nx < 8) q.Nx = 8;   // grid-independent call: only the velocity-space fields matter
-    lbc_status st = validate(q, Nxe, Nye);
-    if (st != LBC_OK) return st;
-    HostTables t;
-    std::string err;
-    if (!build_tables(p.Qx, p.Qy, Nxe, Nye, p.p0, t, err)) return fail(LBC_EINVAL, err);
-    equilibrium_host(t, ux, uy, T, gx, gy);
+    std::vector<int> order(b->n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b->inst[x].T.vchunk > b->inst[y].T.vchunk; });
+    work.clear();
+    for (int i : order)
+        for (int t = 0; t < b->inst[i].T.ntile; ++t) work.push_back(make_int2(i, t));
+}
+
+// Uploads the descriptors and the work list (at creation and after a launch-shape change).
+lbc_status upload_descriptors(lbc_batch *b)
+{
+    std::vector<int2> work;
+    build_work(b, work);
+    if ((int)work.size() != b->nwork) return fail(LBC_ECUDA, "internal: work list size changed");
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->d_inst, b->inst.data(), b->n * sizeof(Inst), cudaMemcpyHostToDevice, b->stream));
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                 b->stream));
+    LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));   // pageable sources
     return LBC_OK;
 }
 
-lbc_status lbc_create(const lbc_params *params, void *cuda_stream, lbc_solver **out)
+lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *cuda_stream, lbc_batch **out)
 {
-    if (!params || !out) return fail(LBC_EINVAL, "params and out must not be NULL");
-    lbc_params p = *params;
-    if (p.p0 == 0.0) p.p0 = 1.0;
-    if (p.cfl == 0.0) p.cfl = 0.5;
-    int Nxe, Nye;
-    lbc_status st = validate(p, Nxe, Nye);
-    if (st != LBC_OK) return st;
-
-    lbc_solver *s = new (std::nothrow) lbc_solver();
-    if (!s) return fail(LBC_ENOMEM, "host allocation failed");
-    s->p = p;
-    s->stream = static_cast<cudaStream_t>(cuda_stream);
-    s->fp32 = p.precision == LBC_FP32_STATE;
+    if (!params || !out || n < 1) return fail(LBC_EINVAL, "params, out and n >= 1 are required");
+    if (cluster_in < 0 || cluster_in > kMaxCluster) return fail(LBC_EINVAL, "cluster must be in [0, 16]");
+    std::vector<lbc_params> ps(params, params + n);
+    std::vector<int> Nxe(n), Nye(n);
+    for (int i = 0; i < n; ++i) {
+        lbc_params &p = ps[i];
+        if (p.p0 == 0.0) p.p0 = 1.0;
+        if (p.cfl == 0.0) p.cfl = 0.5;
+        lbc_status st = validate(p, Nxe[i], Nye[i]);
+        if (st != LBC_OK) return n > 1 ? fail(st, "instance " + std::to_string(i) + ": " + last_error()) : st;
+        if (p.precision != ps[0].precision) return fail(LBC_EINVAL, "every instance of a batch has one precision");
+    }
+    lbc_batch *b = new (std::nothrow) lbc_batch();
+    if (!b) return fail(LBC_ENOMEM, "host allocation failed");
     auto cleanup = [&](lbc_status code) {
-        lbc_destroy(s);
+        std::string msg = last_error();
+        lbc_batch_destroy(b);
+        set_error(msg);
         return code;
     };
-    ProblemSetup ps;
-    std::string err;
-    if (!setup_problem(p, Nxe, Nye, ps, err)) return cleanup(fail(LBC_EINVAL, err));
-    s->x = ps.x;
-    s->frest = ps.frest;
+    b->n = n;
+    b->fp32 = ps[0].precision == LBC_FP32_STATE;
+    b->single = n == 1;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->ih.resize(n);
+    b->inst.resize(n);
 
-    // ---- device tables (one allocation) and the launch shape ----
-    cudaError_t e = cudaMallocAsync(&s->table_block, ps.blob.size(), s->stream);
+    // ---- host set-up of every instance; table block offsets ----
+    std::vector<ProblemSetup> setup(n);
+    std::vector<size_t> toff(n);
+    size_t tbytes = 0;
+    for (int i = 0; i < n; ++i) {
+        std::string err;
+        if (!setup_problem(ps[i], Nxe[i], Nye[i], setup[i], err))
+            return cleanup(fail(LBC_EINVAL, (n > 1 ? "instance " + std::to_string(i) + ": " : std::string()) + err));
+        b->ih[i].p = ps[i];
+        b->ih[i].x = setup[i].x;
+        b->ih[i].frest = setup[i].frest;
+        toff[i] = tbytes;
+        tbytes += r256(setup[i].blob.size());
+    }
+    int ntile_total = 0;
+    for (int i = 0; i < n; ++i) ntile_total += (ps[i].Nx + kTile - 1) / kTile;
+    b->nwork = ntile_total;
+    const size_t inst_off = tbytes, work_off = inst_off + r256(n * sizeof(Inst));
+    tbytes = work_off + r256(b->nwork * sizeof(int2));
+    cudaError_t e = cudaMallocAsync(&b->table_block, tbytes, b->stream);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMallocAsync(tables): ") + cudaGetErrorString(e));
         return cleanup(e == cudaErrorMemoryAllocation ? LBC_ENOMEM : LBC_ECUDA);
     }
-    e = cudaMemcpyAsync(s->table_block, ps.blob.data(), ps.blob.size(), cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);   // the pageable source must outlive the copy
-    if (e != cudaSuccess) { set_error(std::string("table upload: ") + cudaGetErrorString(e)); return cleanup(LBC_ECUDA); }
-    DevTables &T = s->T;
-    bind_tables(ps, p, s->table_block, T);
-    st = choose_launch_shape(s->fp32, T);
+    char *tb = static_cast<char *>(b->table_block);
+    b->d_inst = reinterpret_cast<Inst *>(tb + inst_off);
+    b->d_work = reinterpret_cast<int2 *>(tb + work_off);
+    for (int i = 0; i < n; ++i) bind_tables(setup[i], ps[i], tb + toff[i], b->inst[i].T);
+
+    // ---- launch shape ----
+    lbc_status st;
+    if (b->single) {
+        st = choose_launch_shape(b->fp32, b->inst[0].T);
+        if (st == LBC_OK && cluster_in > 0 && cluster_in != b->inst[0].T.nchunk) {
+            b->inst[0].T.nchunk = cluster_in;
+            b->inst[0].T.vchunk = chunk_rows(b->inst[0].T.V, cluster_in);
+            if (b->inst[0].T.vchunk > kMaxVChunk) st = fail(LBC_EINVAL, "cluster too small for the velocity set");
+        }
+        if (st == LBC_OK) {
+            b->cluster = b->inst[0].T.nchunk;
+            b->smem = stage_launch_smem(b->fp32, b->inst[0].T);
+        }
+    } else {
+        std::vector<DevTables> Ts(n);
+        for (int i = 0; i < n; ++i) Ts[i] = b->inst[i].T;
+        st = choose_batch_shape(b->fp32, Ts, cluster_in, b->cluster, b->smem);
+        for (int i = 0; i < n && st == LBC_OK; ++i) b->inst[i].T = Ts[i];
+    }
     if (st != LBC_OK) return cleanup(st);
 
     // ---- device state ----
-    const int V = T.V;
-    const size_t esz = s->fp32 ? sizeof(float) : sizeof(double);
-    auto r256 = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t fbytes = r256(2 * (size_t)V * T.Nxp * esz);
-    const size_t pbytes = r256((size_t)T.nchunk * kNumRaw * T.Nxp * esz);
-    const size_t embytes = r256((size_t)T.Nxp * kEqM * esz);
-    const size_t egbytes = r256((size_t)T.ntile * (2 * p.Qx + p.Qy) * kLanes * esz);
-    const size_t rbytes = kResidRing * sizeof(unsigned long long);
-    const size_t cbytes = 256;
-    const size_t mbytes = r256((size_t)LBC_NMOM * T.Nxp * sizeof(double));
-    const size_t sbytes = 3 * (fbytes + embytes + egbytes) + pbytes + rbytes + cbytes + mbytes;
-    e = cudaMallocAsync(&s->state_block, sbytes, s->stream);
+    std::vector<size_t> soff(n);
+    size_t sbytes = 0;
+    for (int i = 0; i < n; ++i) {
+        soff[i] = sbytes;
+        sbytes += StateSizes(b->inst[i].T, b->fp32).total;
+    }
+    const size_t ctl_off = sbytes, last_off = ctl_off + r256(n * sizeof(Ctl));
+    sbytes = last_off + r256(n * sizeof(double));
+    e = cudaMallocAsync(&b->state_block, sbytes, b->stream);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMallocAsync(state): ") + cudaGetErrorString(e));
         return cleanup(e == cudaErrorMemoryAllocation ? LBC_ENOMEM : LBC_ECUDA);
     }
-    e = cudaMemsetAsync(s->state_block, 0, sbytes, s->stream);
+    e = cudaMemsetAsync(b->state_block, 0, sbytes, b->stream);   // deviation 0 = the rest state; control zeroed
     if (e != cudaSuccess) { set_error(std::string("cudaMemsetAsync: ") + cudaGetErrorString(e)); return cleanup(LBC_ECUDA); }
-    char *b = static_cast<char *>(s->state_block);
-    for (int k = 0; k < 3; ++k) { s->S.F[k] = b; b += fbytes; }
-    for (int k = 0; k < 3; ++k) { s->S.eqm[k] = b; b += embytes; }
-    for (int k = 0; k < 3; ++k) { s->S.eqg[k] = b; b += egbytes; }
-    s->S.part = b; b += pbytes;
-    s->S.resid = reinterpret_cast<unsigned long long *>(b); b += rbytes;
-    s->S.ctl = reinterpret_cast<Ctl *>(b); b += cbytes;
-    s->S.mom_out = reinterpret_cast<double *>(b);
-
-    e = cudaMallocHost(&s->h_resid, rbytes);
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_ctl, sizeof(Ctl));
+    char *sb = static_cast<char *>(b->state_block);
+    b->d_ctl = reinterpret_cast<Ctl *>(sb + ctl_off);
+    b->d_last = reinterpret_cast<double *>(sb + last_off);
+    for (int i = 0; i < n; ++i) {
+        DevTables &T = b->inst[i].T;
+        DevState &S = b->inst[i].S;
+        const StateSizes z(T, b->fp32);
+        char *p = sb + soff[i];
+        for (int k = 0; k < 3; ++k) { S.F[k] = p; p += z.f; }
+        for (int k = 0; k < 3; ++k) { S.eqm[k] = p; p += z.eqm; }
+        for (int k = 0; k < 3; ++k) { S.eqg[k] = p; p += z.eqg; }
+        S.part = p; p += z.part;
+        S.resid = reinterpret_cast<unsigned long long *>(p); p += z.resid;
+        S.mom_out = reinterpret_cast<double *>(p);
+        S.ctl = b->d_ctl + i;
+        StateMaps &M = b->inst[i].M;
+        for (int k = 0; k < 3 && st == LBC_OK; ++k) st = encode_state_map(&M.in[k], S.F[k], b->fp32, T.V, T.Nxp, kRowLen);
+        if (st == LBC_OK) st = encode_state_map(&M.f0, S.F[0], b->fp32, T.V, T.Nxp, kF0Len);
+        if (st != LBC_OK) return cleanup(st);
+    }
+    e = cudaMallocHost(&b->h_ctl, n * sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_last, n * sizeof(double));
     if (e != cudaSuccess) {
         set_error(std::string("cudaMallocHost: ") + cudaGetErrorString(e));
         return cleanup(e == cudaErrorMemoryAllocation ? LBC_ENOMEM : LBC_ECUDA);
     }
-    for (int k = 0; k < 3; ++k) {
-        st = encode_state_map(&s->M.in[k], s->S.F[k], s->fp32, V, T.Nxp, kRowLen);
-        if (st != LBC_OK) return cleanup(st);
-    }
-    st = encode_state_map(&s->M.f0, s->S.F[0], s->fp32, V, T.Nxp, kF0Len);
+    std::memset(b->h_ctl, 0, n * sizeof(Ctl));
+
+    // ---- tables, descriptors, work list; stage data of the rest state ----
+    std::vector<unsigned char> image(inst_off, 0);
+    for (int i = 0; i < n; ++i) std::memcpy(image.data() + toff[i], setup[i].blob.data(), setup[i].blob.size());
+    e = cudaMemcpyAsync(b->table_block, image.data(), image.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) { set_error(std::string("table upload: ") + cudaGetErrorString(e)); return cleanup(LBC_ECUDA); }
+    st = upload_descriptors(b);   // synchronises: `image` may go away afterwards
+    for (int i = 0; i < n && st == LBC_OK; ++i) st = rebuild_stage_data(b, i);
     if (st != LBC_OK) return cleanup(st);
-    // The zeroed state is the rest Maxwellian (deviation 0) with zero moment partials;
-    // build its stage data (moments and equilibrium factors) for the first stage.
-    e = s->fp32 ? launch_tile_equilibrium<float>(T, s->S, 0, s->stream)
-                : launch_tile_equilibrium<double>(T, s->S, 0, s->stream);
-    if (e == cudaSuccess) e = launch_ctl_set(s->S.ctl, 0, 0, 0, s->stream);
-    if (e != cudaSuccess) { set_error(std::string("init launch: ") + cudaGetErrorString(e)); return cleanup(LBC_ECUDA); }
+    *out = b;
+    return LBC_OK;
+}
+
+lbc_status batch_run_to_steady(lbc_batch *b, double residual, long max_steps, long *steps_done,
+                               double *final_residual)
+{
+    if (!b || !(residual > 0.0) || max_steps < 0) return fail(LBC_EINVAL, "bad batch, residual or max_steps");
+    if (b->poisoned) return fail(LBC_ENONFINITE, "a state is non-finite");
+    const int n = b->n;
+    std::vector<long long> start(n);
+    for (int i = 0; i < n; ++i) {
+        start[i] = b->ih[i].steps;
+        Ctl &c = b->h_ctl[i];
+        c.base = start[i];
+        c.check_from = start[i];
+        c.stop_eps = residual;
+        c.stop_step = 0;
+        c.stopped = 0;
+    }
+    b->steady_mode = true;
+    lbc_status st = upload_ctl(b, 0, n);
+    if (st != LBC_OK) return st;
+    long done = 0;
+    bool all = false;
+    while (done < max_steps && !all) {
+        const long k = std::min<long>(kGraphSteps, max_steps - done);
+        st = run_steps(b, k);
+        if (st != LBC_OK) return st;
+        LBC_CUDA_TRY(launch_last_residuals(b->d_inst, n, b->d_last, b->stream));
+        LBC_CUDA_TRY(cudaMemcpyAsync(b->h_last, b->d_last, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        st = read_ctl(b);
+        if (st != LBC_OK) return st;
+        done += k;
+        all = true;
+        for (int i = 0; i < n; ++i) all = all && b->h_ctl[i].stopped;
+    }
+    bool converged = true;
+    for (int i = 0; i < n; ++i) {
+        const Ctl &c = b->h_ctl[i];
+        long taken = done;
+        bool conv = false;
+        if (c.stopped) {
+            taken = (long)(c.stop_step - start[i]);
+            conv = true;
+        } else if (done > 0 && b->h_last[i] < residual) {
+            conv = true;   // the last step launched fell below the threshold
+        }
+        converged = converged && conv;
+        b->ih[i].steps = start[i] + taken;
+        if (steps_done) steps_done[i] = taken;
+        if (final_residual) final_residual[i] = done > 0 ? b->h_last[i] : INFINITY;
+    }
+    if (!converged) return fail(LBC_ENOTCONV, "max_steps reached before the residual threshold");
+    return LBC_OK;
+}
+
+lbc_status check_index(const lbc_batch *b, int i)
+{
+    if (!b) return fail(LBC_EINVAL, "NULL batch");
+    if (i < 0 || i >= b->n) return fail(LBC_EINVAL, "instance index out of range");
+    return LBC_OK;
+}
+
+lbc_status batch_moments(lbc_batch *b, int i, double *out, double *x)
+{
+    lbc_status st = check_index(b, i);
+    if (st != LBC_OK) return st;
+    if (!out) return fail(LBC_EINVAL, "NULL argument");
+    const Inst &I = b->inst[i];
+    LBC_CUDA_TRY(b->fp32 ? launch_moments_partial<float>(I.T, I.S, 0, b->stream)
+                         : launch_moments_partial<double>(I.T, I.S, 0, b->stream));
+    LBC_CUDA_TRY(b->fp32 ? launch_finalize_moments<float>(I.T, I.S, b->stream)
+                         : launch_finalize_moments<double>(I.T, I.S, b->stream));
+    LBC_CUDA_TRY(cudaMemcpy2DAsync(out, I.T.Nx * sizeof(double), I.S.mom_out, I.T.Nxp * sizeof(double),
+                                   I.T.Nx * sizeof(double), LBC_NMOM, cudaMemcpyDeviceToHost, b->stream));
+    st = read_ctl(b);
+    if (st != LBC_OK) return st;
+    if (x) std::copy(b->ih[i].x.begin(), b->ih[i].x.end(), x);
+    return LBC_OK;
+}
+
+lbc_status batch_get_state(lbc_batch *b, int i, double *state)
+{
+    lbc_status st = check_index(b, i);
+    if (st != LBC_OK) return st;
+    if (!state) return fail(LBC_EINVAL, "NULL argument");
+    const DevTables &T = b->inst[i].T;
+    const int V = T.V, Nx = T.Nx, Nxp = T.Nxp;
+    const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
+    std::vector<unsigned char> tmp(2 * (size_t)V * Nxp * esz);
+    LBC_CUDA_TRY(cudaMemcpyAsync(tmp.data(), b->inst[i].S.F[0], tmp.size(), cudaMemcpyDeviceToHost, b->stream));
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    const std::vector<double> &frest = b->ih[i].frest;
+    for (size_t r = 0; r < 2 * (size_t)V; ++r) {
+        const double fr = frest[r % V];
+        for (int c = 0; c < Nx; ++c)
+            state[r * Nx + c] = fr + (b->fp32 ? (double)reinterpret_cast<float *>(tmp.data())[r * Nxp + c]
+                                              : reinterpret_cast<double *>(tmp.data())[r * Nxp + c]);
+    }
+    for (int k = 0; k < b->n; ++k)
+        if (b->h_ctl[k].timeout) return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
+    return LBC_OK;
+}
+
+lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
+{
+    lbc_status st = check_index(b, i);
+    if (st != LBC_OK) return st;
+    if (!state) return fail(LBC_EINVAL, "NULL argument");
+    const DevTables &T = b->inst[i].T;
+    const int V = T.V, Nx = T.Nx, Nxp = T.Nxp;
+    for (size_t k = 0; k < 2 * (size_t)V * Nx; ++k)
+        if (!std::isfinite(state[k])) return fail(LBC_EINVAL, "state holds a NaN or Inf");
+    const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
+    std::vector<unsigned char> tmp(2 * (size_t)V * Nxp * esz, 0);
+    const std::vector<double> &frest = b->ih[i].frest;
+    for (size_t r = 0; r < 2 * (size_t)V; ++r) {
+        const double fr = frest[r % V];
+        for (int c = 0; c < Nx; ++c) {
+            if (b->fp32) reinterpret_cast<float *>(tmp.data())[r * Nxp + c] = (float)(state[r * Nx + c] - fr);
+            else reinterpret_cast<double *>(tmp.data())[r * Nxp + c] = state[r * Nx + c] - fr;
+        }
+    }
+    // control blocks: keep the others' flags, clear this instance's
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    b->h_ctl[i].nonfinite = 0;
+    bool any = false;
+    for (int k = 0; k < b->n; ++k) any = any || b->h_ctl[k].nonfinite;
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->inst[i].S.F[0], tmp.data(), tmp.size(), cudaMemcpyHostToDevice, b->stream));
+    st = upload_ctl(b, i, 1);
+    if (st == LBC_OK) st = rebuild_stage_data(b, i);
+    if (st != LBC_OK) return st;
+    LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    b->poisoned = any;
+    return LBC_OK;
+}
+
+// Times trial_steps steps per feasible cluster size (after one warm-up step) and
+// keeps the fastest; every instance starts and ends at the rest state.
+lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
+{
+    if (!b || trial_steps < 1) return fail(LBC_EINVAL, "bad batch or trial_steps");
+    for (int i = 0; i < b->n; ++i)
+        if (b->ih[i].steps != 0) return fail(LBC_EINVAL, "autotune needs every instance at its initial state");
+    if (b->single) {
+        if (cluster_out) *cluster_out = b->cluster;
+        return LBC_OK;   // the single-instance shape comes from the wave model of its own launch
+    }
+    cudaEvent_t t0, t1;
+    LBC_CUDA_TRY(cudaEventCreate(&t0));
+    LBC_CUDA_TRY(cudaEventCreate(&t1));
+    const std::vector<Inst> keep = b->inst;
+    float best = 1e30f;
+    int best_c = b->cluster;
+    size_t best_smem = b->smem;
+    std::vector<DevTables> best_T;
+    lbc_status st = LBC_OK;
+    for (int C = 1; C <= kMaxCluster && st == LBC_OK; ++C) {
+        std::vector<DevTables> Ts(b->n);
+        for (int i = 0; i < b->n; ++i) Ts[i] = keep[i].T;
+        int c = 0;
+        size_t smem = 0;
+        if (choose_batch_shape(b->fp32, Ts, C, c, smem) != LBC_OK) continue;
+        for (int i = 0; i < b->n; ++i) b->inst[i].T = Ts[i];
+        b->cluster = c;
+        b->smem = smem;
+        st = upload_descriptors(b);
+        if (st != LBC_OK) break;
+        cudaError_t e = launch_steps(b, 1, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+        if (e == cudaSuccess) e = launch_steps(b, trial_steps, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e != cudaSuccess) { st = fail(LBC_ECUDA, std::string("autotune: ") + cudaGetErrorString(e)); break; }
+        if (ms < best) { best = ms; best_c = c; best_smem = smem; best_T = Ts; }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (best_T.empty()) {   // nothing measured: keep the model's choice
+        b->inst = keep;
+        st = st == LBC_OK ? fail(LBC_EINVAL, "no cluster size could be timed") : st;
+    } else {
+        for (int i = 0; i < b->n; ++i) b->inst[i].T = best_T[i];
+        b->cluster = best_c;
+        b->smem = best_smem;
+    }
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    lbc_status st2 = upload_descriptors(b);
+    // back to the rest state: zero states and control, rebuild the stage data
+    for (int i = 0; i < b->n && st2 == LBC_OK; ++i) {
+        const DevTables &T = b->inst[i].T;
+        const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
+        cudaError_t e = cudaMemsetAsync(b->inst[i].S.F[0], 0, 2 * (size_t)T.V * T.Nxp * esz, b->stream);
+        if (e != cudaSuccess) st2 = fail(LBC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+        if (st2 == LBC_OK) st2 = rebuild_stage_data(b, i);
+    }
+    if (st2 == LBC_OK) {
+        std::memset(b->h_ctl, 0, b->n * sizeof(Ctl));
+        b->steady_mode = false;
+        st2 = upload_ctl(b, 0, b->n);
+    }
+    if (st2 == LBC_OK) LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (st == LBC_OK) st = st2;
+    if (st == LBC_OK && cluster_out) *cluster_out = b->cluster;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbc_status lbc_batch_create(const lbc_params *params, int n, int cluster, void *cuda_stream, lbc_batch **out)
+{
+    return batch_create(params, n, cluster, cuda_stream, out);
+}
+
+lbc_status lbc_batch_step(lbc_batch *b, long nsteps)
+{
+    if (!b || nsteps < 0) return fail(LBC_EINVAL, "bad batch or nsteps");
+    if (b->poisoned) return fail(LBC_ENONFINITE, "a state is non-finite");
+    lbc_status st = plain_mode(b);
+    if (st == LBC_OK) st = run_steps(b, nsteps);
+    if (st != LBC_OK) return st;
+    for (int i = 0; i < b->n; ++i) b->ih[i].steps += nsteps;
+    return LBC_OK;
+}
+
+lbc_status lbc_batch_run_to_steady(lbc_batch *b, double residual, long max_steps, long *steps_done,
+                                   double *final_residual)
+{
+    return batch_run_to_steady(b, residual, max_steps, steps_done, final_residual);
+}
+
+lbc_status lbc_batch_moments(lbc_batch *b, int i, double *out, double *x) { return batch_moments(b, i, out, x); }
+lbc_status lbc_batch_get_state(lbc_batch *b, int i, double *state) { return batch_get_state(b, i, state); }
+lbc_status lbc_batch_set_state(lbc_batch *b, int i, const double *state) { return batch_set_state(b, i, state); }
+
+lbc_status lbc_batch_info(const lbc_batch *b, int i, int *Nx, int *V, double *dt, long *steps_taken)
+{
+    lbc_status st = check_index(b, i);
+    if (st != LBC_OK) return st;
+    const DevTables &T = b->inst[i].T;
+    if (Nx) *Nx = T.Nx;
+    if (V) *V = T.V;
+    if (dt) *dt = T.dt;
+    if (steps_taken) *steps_taken = (long)b->ih[i].steps;
+    return LBC_OK;
+}
+
+lbc_status lbc_batch_shape(const lbc_batch *b, int *cluster, int *nwork, size_t *smem_bytes)
+{
+    if (!b) return fail(LBC_EINVAL, "NULL batch");
+    if (cluster) *cluster = b->cluster;
+    if (nwork) *nwork = b->nwork;
+    if (smem_bytes) *smem_bytes = b->smem;
+    return LBC_OK;
+}
+
+lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster) { return batch_autotune(b, trial_steps, cluster); }
+
+lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms)
+{
+    if (!b || nsteps < 0 || !stage_ms) return fail(LBC_EINVAL, "bad batch, nsteps or stage_ms");
+    if (b->poisoned) return fail(LBC_ENONFINITE, "a state is non-finite");
+    lbc_status st = plain_mode(b);
+    if (st != LBC_OK) return st;
+    const int nl = (int)(3 * nsteps);
+    std::vector<cudaEvent_t> ev(2 * (size_t)nl, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < ev.size() && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+    for (long k = 0; k < nsteps && e == cudaSuccess; ++k)
+        for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+            const size_t j = 2 * (size_t)(3 * k + stage);
+            e = cudaEventRecord(ev[j], b->stream);
+            if (e == cudaSuccess)
+                e = b->fp32 ? (b->single ? launch_stage<float>(b->inst[0], b->smem, stage, (int)k, b->stream)
+                                         : launch_stage_batch<float>(b->d_inst, b->d_work, b->nwork, b->cluster,
+                                                                     b->smem, stage, (int)k, b->stream))
+                            : (b->single ? launch_stage<double>(b->inst[0], b->smem, stage, (int)k, b->stream)
+                                         : launch_stage_batch<double>(b->d_inst, b->d_work, b->nwork, b->cluster,
+                                                                      b->smem, stage, (int)k, b->stream));
+            if (e == cudaSuccess) e = cudaEventRecord(ev[j + 1], b->stream);
+        }
+    if (e == cudaSuccess) e = launch_ctl_bump(b->d_ctl, b->n, nsteps, b->stream);
+    double total = 0.0;
+    for (int k = 0; k < nl && e == cudaSuccess; ++k) {
+        e = cudaEventSynchronize(ev[2 * k + 1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+        total += ms;
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail(LBC_ECUDA, std::string("timed step: ") + cudaGetErrorString(e));
+    for (int i = 0; i < b->n; ++i) b->ih[i].steps += nsteps;
+    *stage_ms = total;
+    return LBC_OK;
+}
+
+void lbc_batch_destroy(lbc_batch *b)
+{
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->state_block) cudaFreeAsync(b->state_block, b->stream);
+    if (b->table_block) cudaFreeAsync(b->table_block, b->stream);
+    if (b->h_ctl || b->h_last) cudaStreamSynchronize(b->stream);
+    if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    if (b->h_last) cudaFreeHost(b->h_last);
+    delete b;
+}
+
+// ---- the single-instance solver: a batch of one ----
+
+lbc_status lbc_create(const lbc_params *params, void *cuda_stream, lbc_solver **out)
+{
+    if (!params || !out) return fail(LBC_EINVAL, "params and out must not be NULL");
+    lbc_solver *s = new (std::nothrow) lbc_solver();
+    if (!s) return fail(LBC_ENOMEM, "host allocation failed");
+    lbc_status st = batch_create(params, 1, 0, cuda_stream, &s->b);
+    if (st != LBC_OK) {
+        delete s;
+        return st;
+    }
     *out = s;
     return LBC_OK;
 }
 
 lbc_status lbc_step(lbc_solver *s, long nsteps)
 {
-    if (!s || nsteps < 0) return fail(LBC_EINVAL, "bad solver or nsteps");
-    if (s->poisoned) return fail(LBC_ENONFINITE, "solver state is non-finite");
-    long left = nsteps;
-    while (left >= kGraphSteps) {
-        lbc_status st = ensure_graph(s);
-        if (st != LBC_OK) return st;
-        LBC_CUDA_TRY(cudaGraphLaunch(s->graph, s->stream));
-        left -= kGraphSteps;
-    }
-    if (left > 0) {
-        LBC_CUDA_TRY(launch_steps(s, 0, (int)left, 0.0));
-        LBC_CUDA_TRY(launch_ctl_bump(s->S.ctl, left, s->stream));
-    }
-    s->steps += nsteps;
-    return LBC_OK;
+    if (!s) return fail(LBC_EINVAL, "bad solver or nsteps");
+    return lbc_batch_step(s->b, nsteps);
 }
 
 lbc_status lbc_run_to_steady(lbc_solver *s, double residual, long max_steps, long *steps_done,
                              double *final_residual)
 {
-    if (!s || !(residual > 0.0) || max_steps < 0) return fail(LBC_EINVAL, "bad solver, residual or max_steps");
-    if (s->poisoned) return fail(LBC_ENONFINITE, "solver state is non-finite");
-    const long long start = s->steps;
-    LBC_CUDA_TRY(launch_ctl_set(s->S.ctl, start, start, 0, s->stream));
-    long done = 0;
-    double last = INFINITY;
-    bool converged = false;
-    // chunks of up to kGraphSteps steps, each followed by a read-back of the residuals
-    while (done < max_steps && !converged) {
-        int k = (int)std::min<long>(kGraphSteps, max_steps - done);
-        long long base = start + done;
-        LBC_CUDA_TRY(launch_steps(s, 0, k, residual));
-        LBC_CUDA_TRY(launch_ctl_bump(s->S.ctl, k, s->stream));
-        LBC_CUDA_TRY(cudaMemcpyAsync(s->h_resid, s->S.resid, kResidRing * sizeof(unsigned long long),
-                                     cudaMemcpyDeviceToHost, s->stream));
-        LBC_CUDA_TRY(cudaMemcpyAsync(s->h_ctl, s->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
-        LBC_CUDA_TRY(cudaStreamSynchronize(s->stream));
-        if (s->h_ctl->timeout) return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
-        if (s->h_ctl->nonfinite) {
-            s->poisoned = true;
-            return fail(LBC_ENONFINITE, "non-finite value in the state");
-        }
-        int taken = k;
-        for (int i = 0; i < k; ++i) {
-            unsigned long long bits = s->h_resid[(base + i) % kResidRing];
-            double r;
-            std::memcpy(&r, &bits, sizeof r);
-            last = r;
-            if (r < residual) { taken = i + 1; converged = true; break; }
-        }
-        done += taken;
-    }
-    s->steps = start + done;
-    LBC_CUDA_TRY(launch_ctl_set(s->S.ctl, s->steps, s->steps, 0, s->stream));
-    if (steps_done) *steps_done = done;
-    if (final_residual) *final_residual = last;
-    if (!converged) return fail(LBC_ENOTCONV, "max_steps reached before the residual threshold");
-    return LBC_OK;
+    if (!s) return fail(LBC_EINVAL, "bad solver, residual or max_steps");
+    return batch_run_to_steady(s->b, residual, max_steps, steps_done, final_residual);
 }
 
 lbc_status lbc_moments(lbc_solver *s, double *out, double *x)
 {
-    if (!s || !out) return fail(LBC_EINVAL, "NULL argument");
-    LBC_CUDA_TRY(s->fp32 ? launch_moments_partial<float>(s->T, s->S, 0, s->stream)
-                         : launch_moments_partial<double>(s->T, s->S, 0, s->stream));
-    LBC_CUDA_TRY(s->fp32 ? launch_finalize_moments<float>(s->T, s->S, s->stream)
-                         : launch_finalize_moments<double>(s->T, s->S, s->stream));
-    LBC_CUDA_TRY(cudaMemcpy2DAsync(out, s->p.Nx * sizeof(double), s->S.mom_out, s->T.Nxp * sizeof(double),
-                                   s->p.Nx * sizeof(double), LBC_NMOM, cudaMemcpyDeviceToHost, s->stream));
-    LBC_CUDA_TRY(cudaMemcpyAsync(s->h_ctl, s->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
-    LBC_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    if (x) std::copy(s->x.begin(), s->x.end(), x);
-    if (s->h_ctl->timeout) return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
-    if (s->h_ctl->nonfinite) {
-        s->poisoned = true;
-        return fail(LBC_ENONFINITE, "non-finite value in the state");
-    }
-    return LBC_OK;
+    if (!s) return fail(LBC_EINVAL, "NULL argument");
+    return batch_moments(s->b, 0, out, x);
 }
 
 lbc_status lbc_get_state(lbc_solver *s, double *state)
 {
-    if (!s || !state) return fail(LBC_EINVAL, "NULL argument");
-    const int V = s->T.V, Nx = s->T.Nx, Nxp = s->T.Nxp;
-    const size_t esz = s->fp32 ? sizeof(float) : sizeof(double);
-    std::vector<unsigned char> tmp(2 * (size_t)V * Nxp * esz);
-    LBC_CUDA_TRY(cudaMemcpyAsync(tmp.data(), s->S.F[0], tmp.size(), cudaMemcpyDeviceToHost, s->stream));
-    LBC_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    for (size_t r = 0; r < 2 * (size_t)V; ++r) {
-        const double fr = s->frest[r % V];
-        for (int c = 0; c < Nx; ++c)
-            state[r * Nx + c] = fr + (s->fp32 ? (double)reinterpret_cast<float *>(tmp.data())[r * Nxp + c]
-                                              : reinterpret_cast<double *>(tmp.data())[r * Nxp + c]);
-    }
-    if (s->h_ctl) {
-        LBC_CUDA_TRY(cudaMemcpyAsync(s->h_ctl, s->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
-        LBC_CUDA_TRY(cudaStreamSynchronize(s->stream));
-        if (s->h_ctl->timeout) return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
-    }
-    return LBC_OK;
+    if (!s) return fail(LBC_EINVAL, "NULL argument");
+    return batch_get_state(s->b, 0, state);
 }
 
 lbc_status lbc_set_state(lbc_solver *s, const double *state)
 {
-    if (!s || !state) return fail(LBC_EINVAL, "NULL argument");
-    const int V = s->T.V, Nx = s->T.Nx, Nxp = s->T.Nxp;
-    for (size_t i = 0; i < 2 * (size_t)V * Nx; ++i)
-        if (!std::isfinite(state[i])) return fail(LBC_EINVAL, "state holds a NaN or Inf");
-    const size_t esz = s->fp32 ? sizeof(float) : sizeof(double);
-    std::vector<unsigned char> tmp(2 * (size_t)V * Nxp * esz, 0);
-    for (size_t r = 0; r < 2 * (size_t)V; ++r) {
-        const double fr = s->frest[r % V];
-        for (int c = 0; c < Nx; ++c) {
-            if (s->fp32) reinterpret_cast<float *>(tmp.data())[r * Nxp + c] = (float)(state[r * Nx + c] - fr);
-            else reinterpret_cast<double *>(tmp.data())[r * Nxp + c] = state[r * Nx + c] - fr;
-        }
-    }
-    LBC_CUDA_TRY(cudaMemcpyAsync(s->S.F[0], tmp.data(), tmp.size(), cudaMemcpyHostToDevice, s->stream));
-    LBC_CUDA_TRY(s->fp32 ? launch_moments_partial<float>(s->T, s->S, 0, s->stream)
-                         : launch_moments_partial<double>(s->T, s->S, 0, s->stream));
-    LBC_CUDA_TRY(s->fp32 ? launch_tile_equilibrium<float>(s->T, s->S, 0, s->stream)
-                         : launch_tile_equilibrium<double>(s->T, s->S, 0, s->stream));
-    LBC_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    s->poisoned = false;
-    return LBC_OK;
+    if (!s) return fail(LBC_EINVAL, "NULL argument");
+    return batch_set_state(s->b, 0, state);
 }
 
 lbc_status lbc_info(const lbc_solver *s, int *Nx, int *V, double *dt, long *steps_taken)
 {
     if (!s) return fail(LBC_EINVAL, "NULL solver");
-    if (Nx) *Nx = s->T.Nx;
-    if (V) *V = s->T.V;
-    if (dt) *dt = s->T.dt;
-    if (steps_taken) *steps_taken = (long)s->steps;
-    return LBC_OK;
+    return lbc_batch_info(s->b, 0, Nx, V, dt, steps_taken);
 }
 
 void lbc_destroy(lbc_solver *s)
 {
     if (!s) return;
-    if (s->graph) cudaGraphExecDestroy(s->graph);
-    if (s->state_block) cudaFreeAsync(s->state_block, s->stream);
-    if (s->table_block) cudaFreeAsync(s->table_block, s->stream);
-    if (s->h_resid || s->h_ctl) cudaStreamSynchronize(s->stream);
-    if (s->h_resid) cudaFreeHost(s->h_resid);
-    if (s->h_ctl) cudaFreeHost(s->h_ctl);
+    lbc_batch_destroy(s->b);
     delete s;
 }
 

@@ -93,11 +93,14 @@ struct EqTab {
     __host__ __device__ static int r4(int x) { return (x + 3) / 4 * 4; }
 };
 
-// Control block in device memory.
+// Control block in device memory, one per instance. The host keeps the
+// authoritative copy and uploads it to (re)start a run.
 struct Ctl {
     long long base;        // steps launched so far (stage kernels add their relative index)
     long long check_from;  // early stop considers residuals of steps >= check_from only
-    int stopped;           // set once a residual fell below the stop threshold
+    double stop_eps;       // early-stop threshold on the previous step's residual (0: never stop)
+    long long stop_step;   // the step at which the instance stopped (valid once stopped)
+    int stopped;           // set once a residual fell below stop_eps
     int nonfinite;         // set if a NaN/Inf was produced
     int timeout;           // set if a bounded wait on an mbarrier gave up
     int pad;
@@ -122,6 +125,14 @@ struct StateMaps {
     CUtensorMap f0;        // box kF0Len x kSubV (RK base state, buffer 0)
 };
 
+// Everything the stage kernel needs about one instance (one Couette problem),
+// in device memory. The tensor maps come first: they need 64-byte alignment.
+struct alignas(128) Inst {
+    StateMaps M;
+    DevTables T;
+    DevState S;
+};
+
 // Host-side image of one problem: tables, grid, time step, wall and rest data,
 // and the device table block (FP64 pieces, FP32 copies, the index table).
 struct ProblemSetup {
@@ -139,33 +150,51 @@ bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std:
 // Fills T from ps, with the table pointers into the device copy `dev` of ps.blob.
 // Leaves the launch shape (vchunk, nchunk) to choose_launch_shape.
 void bind_tables(const ProblemSetup &ps, const lbc_params &p, const void *dev, DevTables &T);
-// Sets the stage kernel's attributes on the current device and picks T.vchunk,
-// T.nchunk. LBC_ECUDA without a device; LBC_EINVAL if no cluster shape fits.
+// Velocity chunk of an instance split over `cluster` chunk CTAs (multiple of kSubV rows).
+inline int chunk_rows(int V, int cluster) { return (V + kSubV * cluster - 1) / (kSubV * cluster) * kSubV; }
+// Sets the stage kernel's attributes on the current device and picks the
+// cluster size for one instance (T.nchunk) and its chunk rows (T.vchunk).
+// LBC_ECUDA without a device; LBC_EINVAL if no cluster shape fits.
 lbc_status choose_launch_shape(bool fp32, DevTables &T);
+// Cluster size and stage shared memory of a batch (sets every T.nchunk, T.vchunk);
+// cluster_in > 0 forces the cluster size.
+lbc_status choose_batch_shape(bool fp32, std::vector<DevTables> &Ts, int cluster_in, int &cluster, size_t &smem);
+// Dynamic shared memory of the stage kernel for T's launch shape.
+size_t stage_launch_smem(bool fp32, const DevTables &T);
+// Errors and parameter checks shared by every entry point.
+lbc_status fail(lbc_status st, const std::string &msg);
+const char *last_error();
+// Validates p (defaults already applied) and resolves the expansion orders.
+lbc_status validate(const lbc_params &p, int &Nxe, int &Nye);
 // TMA descriptor of a state buffer viewed as [2V rows][Nxp columns], box box_cols x kSubV.
 lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_cols);
 
 template <typename R>
-size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk);
-template <typename R>
-cudaError_t stage_kernel_attributes(cudaFuncAttributes *fa);
+size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster);
 template <typename R>
 size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K);
-// Clusters of `nchunk` stage CTAs that can be resident at once (0: not launchable).
+// Clusters of `cluster` stage CTAs that can be resident at once (0: not launchable).
 template <typename R>
-cudaError_t stage_active_clusters(size_t smem, int nchunk, int *nclusters);
+cudaError_t stage_active_clusters(size_t smem, int cluster, int *nclusters);
 template <typename R>
 cudaError_t configure_kernels();   // per-device kernel attributes; call before capture
+// One RK stage of one instance: grid (ntile, nchunk), cluster dims (1, nchunk, 1);
+// the descriptor travels as a kernel parameter.
 template <typename R>
-cudaError_t launch_stage(const DevTables &T, const DevState &S, const StateMaps &M, int stage, int rel,
-                         double stop_eps, cudaStream_t st);
+cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStream_t st);
+// One RK stage of every work item: grid (nwork, cluster), cluster dims (1, cluster, 1);
+// work[i] = (instance, tile) with descriptors in device memory, instance < 0 for an empty slot.
+template <typename R>
+cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, int cluster, size_t smem, int stage,
+                               int rel, cudaStream_t st);
 template <typename R>
 cudaError_t launch_moments_partial(const DevTables &T, const DevState &S, int buf, cudaStream_t st);
 template <typename R>
 cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int buf, cudaStream_t st);
 template <typename R>
 cudaError_t launch_finalize_moments(const DevTables &T, const DevState &S, cudaStream_t st);
-cudaError_t launch_ctl_set(Ctl *ctl, long long base, long long check_from, int stopped, cudaStream_t st);
-cudaError_t launch_ctl_bump(Ctl *ctl, long long k, cudaStream_t st);
+cudaError_t launch_ctl_bump(Ctl *ctl, int n, long long k, cudaStream_t st);
+// last[i] = residual of instance i's last step taken (its stop step - 1 if stopped, else base - 1)
+cudaError_t launch_last_residuals(const Inst *insts, int n, double *last, cudaStream_t st);
 
 }  // namespace lbc

@@ -646,7 +646,7 @@ __device__ void block_wall_density(const DevTables &T, const R *phi, bool right,
 template <typename R>
 struct Layout {
     size_t bar, pipe, fin, f0, g, eqm, vrow, xch, misc, total;
-    __host__ __device__ Layout(int Qx, int Qy, int N, int Ny, int K, int vchunk)
+    __host__ __device__ Layout(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster)
     {
         size_t o = 0;
         bar = o;  o = al(o + (kPipe + 2) * sizeof(uint64_t));
@@ -654,7 +654,7 @@ struct Layout {
         fin = o;
         f0 = fin + (size_t)kPipe * 2 * kSubV * kRowLen * sizeof(R);
         size_t m = f0 + (size_t)kPipe * 2 * kSubV * kF0Len * sizeof(R) - pipe;
-        const size_t eq_bytes = EqScratch<R>(K, N, Ny, Qx, Qy, node_cap(Qx, Qy, vchunk)).total;
+        const size_t eq_bytes = EqScratch<R>(K, N, Ny, Qx, Qy, node_cap(cluster)).total;
         m = m > eq_bytes ? m : eq_bytes;
         o = al(o + m);
         g = o;    o = al(o + (size_t)(2 * Qx + Qy) * kLanes * sizeof(R));
@@ -665,23 +665,22 @@ struct Layout {
         total = o + 128;   // slack for aligning the dynamic base
     }
     __host__ __device__ static size_t al(size_t x) { return (x + 127) / 128 * 128; }
-    // nodes per CTA in the cluster's equilibrium step: ceil(kTile / nchunk)
-    __host__ __device__ static int node_cap(int Qx, int Qy, int vchunk)
-    {
-        const int nch = (2 * Qx * Qy + vchunk - 1) / vchunk;
-        return (kTile + nch - 1) / nch;
-    }
+    // nodes per CTA in the cluster's equilibrium step
+    __host__ __device__ static int node_cap(int cluster) { return (kTile + cluster - 1) / cluster; }
 };
 
+// One RK stage of tile `tile` of instance I, for the CTA's velocity chunk
+// blockIdx.y (body of both stage kernels below).
 template <typename R>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
-stage_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevState S,
-             const __grid_constant__ StateMaps M, int stage, int rel, double stop_eps)
+__device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, int rel)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
+    const DevTables &T = I.T;
+    const DevState &S = I.S;
+    const StateMaps &M = I.M;
     // TMA destinations want 128-byte aligned shared memory: align the base explicitly
     unsigned char *smem = smem_dyn + ((128 - (smem_addr(smem_dyn) & 127)) & 127);
-    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk);
+    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk, T.nchunk);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);   // [kPipe] rows, data, tables
     uint64_t *bar_data = bar + kPipe, *bar_tab = bar + kPipe + 1;
     R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][2][kSubV][kRowLen]
@@ -693,25 +692,32 @@ stage_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevSta
     double *s_misc = reinterpret_cast<double *>(smem + L.misc);   // wsum[8], nwL, nwR
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x, c0 = tile * kTile, chunk = blockIdx.y;
+    const int c0 = tile * kTile, chunk = blockIdx.y;
     const int in = stage, out = (stage + 1) % 3;
-    const long long step = S.ctl->base + rel;
+    Ctl *ctl = S.ctl;
+    const long long step = ctl->base + rel;
     const int V = T.V, G = 2 * T.Qx + T.Qy;
+    const bool lead = tile == 0 && chunk == 0 && tid == 0;   // one thread per instance
 
-    // ---- early stop (run-to-steady): every block takes the same decision ----
+    // ---- early stop (run-to-steady): every block of the instance takes the same decision ----
+    const double stop_eps = ctl->stop_eps;
     if (stop_eps > 0.0) {
-        if (S.ctl->stopped) return;
-        if (step - 1 >= S.ctl->check_from) {
+        if (ctl->stopped) return;
+        if (step - 1 >= ctl->check_from) {
             double rprev = __longlong_as_double((long long)S.resid[(step - 1) % kResidRing]);
             if (rprev < stop_eps) {
-                if (stage == 0 && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) S.ctl->stopped = 1;
+                if (stage == 0 && lead) {
+                    ctl->stop_step = step;
+                    ctl->stopped = 1;
+                }
                 return;
             }
         }
     }
-    if (stage == 0 && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) S.resid[step % kResidRing] = 0ull;
+    if (stage == 0 && lead) S.resid[step % kResidRing] = 0ull;
 
-    const int vbeg = chunk * T.vchunk;
+    // this CTA's velocity rows [vbeg, vend): may be empty for a small instance in a wide cluster
+    const int vbeg = min(V, chunk * T.vchunk);
     const int vend = min(V, vbeg + T.vchunk);
     const int nsub = (vend - vbeg + kSubV - 1) / kSubV;
     const int nloc = min(kTile, T.Nx - c0);   // nodes of this tile inside the channel
@@ -721,7 +727,7 @@ stage_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevSta
     // TMA x coordinates must be 16-byte aligned: start the boxes at multiples of 4 nodes
     const int x0 = ((c0 - 3) >> 2) << 2, off = c0 - 3 - x0;     // node s <-> column s - x0
     const int xf = (c0 >> 2) << 2, offf = c0 - xf;
-    const int ncap = Layout<R>::node_cap(T.Qx, T.Qy, T.vchunk);
+    const int ncap = Layout<R>::node_cap(T.nchunk);
     const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, ncap);
     const uint32_t tab_bytes = (uint32_t)(EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy).len * sizeof(R));
 
@@ -753,7 +759,7 @@ stage_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevSta
         mbar_expect_tx(bar_data, gb + eb + vb);
         bulk_load(s_g, static_cast<const R *>(S.eqg[in]) + (size_t)tile * G * kLanes, gb, bar_data);
         bulk_load(s_eqm, static_cast<const R *>(S.eqm[in]) + (size_t)c0 * kEqM, eb, bar_data);
-        bulk_load(s_vrow, Tabs<R>::vrow(T) + (size_t)vbeg * kVRow, vb, bar_data);
+        if (vb > 0) bulk_load(s_vrow, Tabs<R>::vrow(T) + (size_t)vbeg * kVRow, vb, bar_data);
     }
 
     const R *Fin = static_cast<const R *>(S.F[in]);
@@ -993,7 +999,7 @@ stage_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevSta
         // give up: record it and let in-flight copies land (bounded); the CTA
         // still takes part in the cluster barriers below, without touching data
         if (tid == 0) {
-            atomicExch(&S.ctl->timeout, 1);
+            atomicExch(&ctl->timeout, 1);
             for (int p = 0; p < kPipe; ++p) {
                 mbar_wait(&bar[p], 0);
                 mbar_wait(&bar[p], 1);
@@ -1050,10 +1056,28 @@ stage_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevSta
     }
     const bool tab_late = __syncthreads_or(!mbar_wait(bar_tab, 0));
     if (tab_late) {
-        if (tid == 0) atomicExch(&S.ctl->timeout, 1);
+        if (tid == 0) atomicExch(&ctl->timeout, 1);
         return;
     }
     node_equilibrium<R>(T, S, out, tile, rank, nch, nn, ncap, scr);
+}
+
+// Single instance: the descriptor is a kernel parameter (constant bank), grid (ntile, nchunk).
+template <typename R>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
+stage_kernel(const __grid_constant__ Inst I, int stage, int rel)
+{
+    stage_body<R>(I, blockIdx.x, stage, rel);
+}
+
+// Batch: descriptors in device memory, one cluster per work item (instance, tile).
+template <typename R>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
+stage_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int stage, int rel)
+{
+    const int2 wk = work[blockIdx.x];
+    if (wk.x < 0) return;   // empty work slot: the whole cluster leaves
+    stage_body<R>(insts[wk.x], wk.y, stage, rel);
 }
 
 // Stage data of every tile of buffer `buf` from the chunk partials of
@@ -1140,29 +1164,26 @@ __global__ void finalize_moments_kernel(DevTables T, DevState S)
     for (int k = 0; k < LBC_NMOM; ++k) S.mom_out[(size_t)k * T.Nxp + s] = mo[k];
 }
 
-__global__ void ctl_set_kernel(Ctl *ctl, long long base, long long check_from, int stopped)
+__global__ void ctl_bump_kernel(Ctl *ctl, int n, long long k)
 {
-    ctl->base = base;
-    ctl->check_from = check_from;
-    ctl->stopped = stopped;
-    ctl->nonfinite = 0;
-    ctl->timeout = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) ctl[i].base += k;
 }
 
-__global__ void ctl_bump_kernel(Ctl *ctl, long long k) { ctl->base += k; }
+__global__ void last_residuals_kernel(const Inst *insts, int n, double *last)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Ctl *c = insts[i].S.ctl;
+        const long long st = (c->stopped ? c->stop_step : c->base) - 1;
+        last[i] = st >= 0 ? __longlong_as_double((long long)insts[i].S.resid[st % kResidRing]) : 0.0;
+    }
+}
 
 }  // namespace
 
 template <typename R>
-size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk)
+size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster)
 {
-    return Layout<R>(Qx, Qy, N, Ny, K, vchunk).total;
-}
-
-template <typename R>
-cudaError_t stage_kernel_attributes(cudaFuncAttributes *fa)
-{
-    return cudaFuncGetAttributes(fa, stage_kernel<R>);
+    return Layout<R>(Qx, Qy, N, Ny, K, vchunk, cluster).total;
 }
 
 template <typename R>
@@ -1174,6 +1195,10 @@ cudaError_t configure_kernels()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage_batch_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tile_equilibrium_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     return e;
 }
@@ -1184,39 +1209,65 @@ size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K)
     return EqScratch<R>(K, N, Ny, Qx, Qy).total;
 }
 
-// One cluster per tile: the tile's nchunk chunk CTAs (cluster dimension y).
-template <typename R>
-cudaError_t launch_stage(const DevTables &T, const DevState &S, const StateMaps &M, int stage, int rel,
-                         double stop_eps, cudaStream_t st)
+namespace {
+cudaLaunchConfig_t cluster_config(unsigned nx, int cluster, size_t smem, cudaStream_t st, cudaLaunchAttribute *at)
 {
-    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(T.ntile, T.nchunk, 1);
+    cfg.gridDim = dim3(nx, (unsigned)cluster, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = L.total;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = (unsigned)cluster;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+}  // namespace
+
+// One cluster per tile of one instance: its nchunk chunk CTAs (cluster dimension y).
+template <typename R>
+cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStream_t st)
+{
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cluster_config((unsigned)I.T.ntile, I.T.nchunk, smem, st, at);
+    return cudaLaunchKernelEx(&cfg, stage_kernel<R>, I, stage, rel);
+}
+
+// One cluster per work item (instance, tile): its `cluster` chunk CTAs (cluster dimension y).
+template <typename R>
+cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, int cluster, size_t smem, int stage,
+                               int rel, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nwork, (unsigned)cluster, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 1;
-    at[0].val.clusterDim.y = (unsigned)T.nchunk;
+    at[0].val.clusterDim.y = (unsigned)cluster;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, stage_kernel<R>, T, S, M, stage, rel, stop_eps);
+    return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R>, insts, work, stage, rel);
 }
 
 template <typename R>
-cudaError_t stage_active_clusters(size_t smem, int nchunk, int *nclusters)
+cudaError_t stage_active_clusters(size_t smem, int cluster, int *nclusters)
 {
     *nclusters = 0;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(1, nchunk, 1);
+    cfg.gridDim = dim3(1, cluster, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 1;
-    at[0].val.clusterDim.y = (unsigned)nchunk;
+    at[0].val.clusterDim.y = (unsigned)cluster;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
@@ -1245,28 +1296,27 @@ cudaError_t launch_finalize_moments(const DevTables &T, const DevState &S, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_ctl_set(Ctl *ctl, long long base, long long check_from, int stopped, cudaStream_t st)
+cudaError_t launch_ctl_bump(Ctl *ctl, int n, long long k, cudaStream_t st)
 {
-    ctl_set_kernel<<<1, 1, 0, st>>>(ctl, base, check_from, stopped);
+    ctl_bump_kernel<<<(n + 255) / 256, 256, 0, st>>>(ctl, n, k);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ctl_bump(Ctl *ctl, long long k, cudaStream_t st)
+cudaError_t launch_last_residuals(const Inst *insts, int n, double *last, cudaStream_t st)
 {
-    ctl_bump_kernel<<<1, 1, 0, st>>>(ctl, k);
+    last_residuals_kernel<<<(n + 255) / 256, 256, 0, st>>>(insts, n, last);
     return cudaGetLastError();
 }
 
 #define LBC_INSTANTIATE(R)                                                                                      \
-    template size_t stage_smem_bytes<R>(int, int, int, int, int, int);                                                    \
-    template cudaError_t stage_kernel_attributes<R>(cudaFuncAttributes *);                                      \
+    template size_t stage_smem_bytes<R>(int, int, int, int, int, int, int);                                     \
     template cudaError_t configure_kernels<R>();                                                                \
-    template cudaError_t launch_stage<R>(const DevTables &, const DevState &, const StateMaps &, int, int, double, \
-                                         cudaStream_t);                                                         \
+    template cudaError_t launch_stage<R>(const Inst &, size_t, int, int, cudaStream_t);                          \
+    template cudaError_t launch_stage_batch<R>(const Inst *, const int2 *, int, int, size_t, int, int, cudaStream_t); \
     template cudaError_t launch_tile_equilibrium<R>(const DevTables &, const DevState &, int, cudaStream_t);     \
     template cudaError_t launch_moments_partial<R>(const DevTables &, const DevState &, int, cudaStream_t);      \
-    template cudaError_t launch_finalize_moments<R>(const DevTables &, const DevState &, cudaStream_t);            \
-    template cudaError_t stage_active_clusters<R>(size_t, int, int *);                                             \
+    template cudaError_t launch_finalize_moments<R>(const DevTables &, const DevState &, cudaStream_t);          \
+    template cudaError_t stage_active_clusters<R>(size_t, int, int *);                                          \
     template size_t equilibrium_smem_bytes<R>(int, int, int, int, int);
 LBC_INSTANTIATE(float)
 LBC_INSTANTIATE(double)

@@ -32,11 +32,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
 
-lbc_status fail_na(lbc_status st, const std::string &msg)
-{
-    set_error(msg);
-    return st;
-}
+lbc_status fail_na(lbc_status st, const std::string &msg) { return fail(st, msg); }
 
 // Device address of the scratch array on the current device (first call per
 // device resolves it and sets the kernels' shared-memory limits).
@@ -107,10 +103,12 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
     ProblemSetup ps;
     std::string err;
     if (!setup_problem(p, Nxe, Nye, ps, err)) return fail_na(LBC_EINVAL, err);
-    DevTables T{};
+    Inst I{};
+    DevTables &T = I.T;
     bind_tables(ps, p, scratch, T);   // the tables sit at the start of the array
     st = choose_launch_shape(fp32, T);
     if (st != LBC_OK) return st;
+    const size_t smem = stage_launch_smem(fp32, T);
     const int V = T.V, Nx = T.Nx;
 
     // ---- layout of the scratch array: tables, then the state ----
@@ -118,7 +116,7 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
     cv.take(ps.blob.size());
     const size_t table_bytes = cv.off;
     const size_t esz = sizeof(R);
-    DevState S{};
+    DevState &S = I.S;
     for (int k = 0; k < 3; ++k) S.F[k] = cv.take(2 * (size_t)V * T.Nxp * esz);
     for (int k = 0; k < 3; ++k) S.eqm[k] = cv.take((size_t)T.Nxp * kEqM * esz);
     for (int k = 0; k < 3; ++k) S.eqg[k] = cv.take((size_t)T.ntile * (2 * p.Qx + p.Qy) * kLanes * esz);
@@ -131,7 +129,7 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
                                        " bytes of working memory; the allocation-free path has " +
                                        std::to_string(kScratchBytes));
 
-    StateMaps M{};
+    StateMaps &M = I.M;
     for (int k = 0; k < 3 && st == LBC_OK; ++k) st = encode_state_map(&M.in[k], S.F[k], fp32, V, T.Nxp, kRowLen);
     if (st == LBC_OK) st = encode_state_map(&M.f0, S.F[0], fp32, V, T.Nxp, kF0Len);
     if (st != LBC_OK) return st;
@@ -150,9 +148,9 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
     NA_TRY(cudaGetLastError());
     NA_TRY(launch_moments_partial<R>(T, S, 0, stream));
     NA_TRY(launch_tile_equilibrium<R>(T, S, 0, stream));
-    NA_TRY(launch_ctl_set(S.ctl, 0, 0, 0, stream));
+    // the control block starts zeroed (the clear above): step 0, no early stop
     for (long k = 0; k < nsteps; ++k)
-        for (int stage = 0; stage < 3; ++stage) NA_TRY(launch_stage<R>(T, S, M, stage, (int)k, 0.0, stream));
+        for (int stage = 0; stage < 3; ++stage) NA_TRY(launch_stage<R>(I, smem, stage, (int)k, stream));
     state_out_kernel<R><<<grid, 256, 0, stream>>>(static_cast<const R *>(S.F[0]), d_state, T.frest, V, Nx, T.Nxp);
     NA_TRY(cudaGetLastError());
     Ctl h_ctl;

@@ -88,8 +88,20 @@ def lib():
         L.lbc_quadrature.argtypes = [C.c_int, C.c_int, dp, dp]
         L.lbc_equilibrium.argtypes = [C.POINTER(Params), C.c_double, C.c_double, C.c_double, dp, dp]
         L.lbc_step_noalloc.argtypes = [C.POINTER(Params), C.c_void_p, C.c_long, vp]
+        L.lbc_batch_create.argtypes = [C.POINTER(Params), C.c_int, C.c_int, vp, C.POINTER(vp)]
+        L.lbc_batch_step.argtypes = [vp, C.c_long]
+        L.lbc_batch_run_to_steady.argtypes = [vp, C.c_double, C.c_long, C.POINTER(C.c_long), dp]
+        L.lbc_batch_moments.argtypes = [vp, C.c_int, dp, dp]
+        L.lbc_batch_get_state.argtypes = [vp, C.c_int, dp]
+        L.lbc_batch_set_state.argtypes = [vp, C.c_int, dp]
+        L.lbc_batch_info.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), dp, C.POINTER(C.c_long)]
+        L.lbc_batch_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
+        L.lbc_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+        L.lbc_batch_step_timed.argtypes = [vp, C.c_long, dp]
+        L.lbc_batch_destroy.argtypes = [vp]
+        L.lbc_batch_destroy.restype = None
         for name in declared_functions():
-            if name not in ("lbc_destroy", "lbc_last_error"):
+            if name not in ("lbc_destroy", "lbc_last_error", "lbc_batch_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -196,3 +208,91 @@ class Solver:
     def set_state(self, f: np.ndarray):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(2, self.V, self.Nx)
         _check(lib().lbc_set_state(self._h, _dptr(f)))
+
+
+class Batch:
+    """Many Couette problems stepped together (include/lbc.h, lbc_batch_*)."""
+
+    def __init__(self, params_list, cluster: int = 0, stream=None):
+        self.params = []
+        for d in params_list:
+            q = dict(DEFAULTS)
+            q.update(d)
+            self.params.append(q)
+        n = len(self.params)
+        arr = (Params * n)(*[make_params(q) for q in self.params])
+        self._arr = arr
+        h = C.c_void_p()
+        st = stream if stream is not None else current_stream_handle()
+        _check(lib().lbc_batch_create(arr, n, int(cluster), C.c_void_p(st) if st else None, C.byref(h)))
+        self._h = h
+        self.n = n
+        self.Nx, self.V, self.dt = [], [], []
+        for i in range(n):
+            nx, nv, dt = C.c_int(), C.c_int(), C.c_double()
+            _check(lib().lbc_batch_info(self._h, i, C.byref(nx), C.byref(nv), C.byref(dt), None))
+            self.Nx.append(nx.value)
+            self.V.append(nv.value)
+            self.dt.append(dt.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbc_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def shape(self):
+        """(cluster size, work items, stage shared-memory bytes)."""
+        c, w, m = C.c_int(), C.c_int(), C.c_size_t()
+        _check(lib().lbc_batch_shape(self._h, C.byref(c), C.byref(w), C.byref(m)))
+        return c.value, w.value, m.value
+
+    def steps(self, i: int) -> int:
+        steps = C.c_long()
+        _check(lib().lbc_batch_info(self._h, i, None, None, None, C.byref(steps)))
+        return steps.value
+
+    def step(self, nsteps: int = 1):
+        _check(lib().lbc_batch_step(self._h, int(nsteps)))
+
+    def run_to_steady(self, residual: float, max_steps: int, raise_notconv: bool = True):
+        """Returns (steps taken, last residual) per instance."""
+        done = (C.c_long * self.n)()
+        res = (C.c_double * self.n)()
+        st = lib().lbc_batch_run_to_steady(self._h, residual, int(max_steps), done, res)
+        if st != OK and not (st == ENOTCONV and not raise_notconv):
+            _check(st)
+        return list(done), list(res)
+
+    def step_timed(self, nsteps: int = 1) -> float:
+        """Steps like step() and returns the summed duration (ms) of the stage launches."""
+        ms = C.c_double()
+        _check(lib().lbc_batch_step_timed(self._h, int(nsteps), C.byref(ms)))
+        return ms.value
+
+    def autotune(self, trial_steps: int = 3) -> int:
+        c = C.c_int()
+        _check(lib().lbc_batch_autotune(self._h, int(trial_steps), C.byref(c)))
+        return c.value
+
+    def moments(self, i: int):
+        out = np.zeros((NMOM, self.Nx[i]))
+        x = np.zeros(self.Nx[i])
+        _check(lib().lbc_batch_moments(self._h, i, _dptr(out), _dptr(x)))
+        return out
+
+    def get_state(self, i: int) -> np.ndarray:
+        f = np.zeros((2, self.V[i], self.Nx[i]))
+        _check(lib().lbc_batch_get_state(self._h, i, _dptr(f)))
+        return f
+
+    def set_state(self, i: int, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(2, self.V[i], self.Nx[i])
+        _check(lib().lbc_batch_set_state(self._h, i, _dptr(f)))
