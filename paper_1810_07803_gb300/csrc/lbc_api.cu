@@ -440,11 +440,15 @@ lbc_status batch_get_state(lbc_batch *b, int i, double *state)
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     const std::vector<double> &frest = b->ih[i].frest;
+    // device rows [V][Nxp][2] (phi, chi adjacent) -> host [2][V][Nx]
     for (size_t r = 0; r < 2 * (size_t)V; ++r) {
-        const double fr = frest[r % V];
-        for (int c = 0; c < Nx; ++c)
-            state[r * Nx + c] = fr + (b->fp32 ? (double)reinterpret_cast<float *>(tmp.data())[r * Nxp + c]
-                                              : reinterpret_cast<double *>(tmp.data())[r * Nxp + c]);
+        const size_t v = r % V, fld = r / V;
+        const double fr = frest[v];
+        for (int c = 0; c < Nx; ++c) {
+            const size_t k = 2 * (v * Nxp + c) + fld;
+            state[r * Nx + c] = fr + (b->fp32 ? (double)reinterpret_cast<float *>(tmp.data())[k]
+                                              : reinterpret_cast<double *>(tmp.data())[k]);
+        }
     }
     for (int k = 0; k < b->n; ++k)
         if (b->h_ctl[k].timeout) return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
@@ -463,11 +467,13 @@ lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
     const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
     std::vector<unsigned char> tmp(2 * (size_t)V * Nxp * esz, 0);
     const std::vector<double> &frest = b->ih[i].frest;
-    for (size_t r = 0; r < 2 * (size_t)V; ++r) {
-        const double fr = frest[r % V];
+    for (size_t r = 0; r < 2 * (size_t)V; ++r) {   // host [2][V][Nx] -> device [V][Nxp][2]
+        const size_t v = r % V, fld = r / V;
+        const double fr = frest[v];
         for (int c = 0; c < Nx; ++c) {
-            if (b->fp32) reinterpret_cast<float *>(tmp.data())[r * Nxp + c] = (float)(state[r * Nx + c] - fr);
-            else reinterpret_cast<double *>(tmp.data())[r * Nxp + c] = state[r * Nx + c] - fr;
+            const size_t k = 2 * (v * Nxp + c) + fld;
+            if (b->fp32) reinterpret_cast<float *>(tmp.data())[k] = (float)(state[r * Nx + c] - fr);
+            else reinterpret_cast<double *>(tmp.data())[k] = state[r * Nx + c] - fr;
         }
     }
     // control blocks: keep the others' flags, clear this instance's

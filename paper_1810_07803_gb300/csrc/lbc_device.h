@@ -70,8 +70,11 @@ struct DevTables {
 enum { VC_PX = 0, VC_PY, VC_W, VC_FR, VC_FWL, VC_FWLT, VC_FWR, VC_FWRT, kVelCols };
 // Per-velocity rows [V][kVRow] (both precisions), copied per velocity chunk into
 // shared memory: p_x, p_y, w, ft_rest, unit-density wall Maxwellians (phi, chi;
-// left, right), and the indices a, j (small integers, exact in either precision).
-enum { VR_PX = 0, VR_PY, VR_W, VR_FR, VR_FWL, VR_FWLT, VR_FWR, VR_FWRT, VR_A, VR_J, kVRow };
+// left, right), and the shared-memory row offsets of g_x(a) and g_y(j) in the
+// tile's equilibrium block, a kLanes and (2 Qx + j) kLanes, stored as integer
+// bit patterns (int32 in the FP32 table, int64 in the FP64 table). 12 values:
+// three 16-byte groups per FP32 row.
+enum { VR_PX = 0, VR_PY, VR_W, VR_FR, VR_FWL, VR_FWLT, VR_FWR, VR_FWRT, VR_GA, VR_GJ, VR_PAD0, VR_PAD1, kVRow };
 
 // Tables of the equilibrium construction, one contiguous block per precision,
 // each piece padded to 4 elements (16-byte pieces in FP32): recurrence of h_l,
@@ -108,7 +111,7 @@ struct Ctl {
 
 // Mutable device state; arrays marked (R) hold the state precision.
 struct DevState {
-    void *F[3];            // (R) [2][V][Nxp] deviation from the rest state
+    void *F[3];            // (R) [V][Nxp][2] deviation from the rest state, (phi, chi) adjacent per node
     void *part;            // (R) [nchunk][kNumRaw][Nxp] raw moment sums (about p = 0) of the deviation per
                            //     velocity chunk (set-up and lbc_moments only; the stage kernel exchanges its
                            //     partials inside the tile's cluster)
@@ -119,10 +122,10 @@ struct DevState {
     double *mom_out;       // [LBC_NMOM][Nxp] scratch for lbc_moments
 };
 
-// TMA descriptors of the state buffers, viewed as 2-D [2V rows][Nxp columns].
+// TMA descriptors of the state buffers, viewed as 2-D [V rows][2 Nxp columns].
 struct StateMaps {
-    CUtensorMap in[3];     // box kRowLen x kSubV (stage input with halo)
-    CUtensorMap f0;        // box kF0Len x kSubV (RK base state, buffer 0)
+    CUtensorMap in[3];     // box 2 kRowLen x kSubV (stage input with halo, both fields)
+    CUtensorMap f0;        // box 2 kF0Len x kSubV (RK base state, buffer 0)
 };
 
 // Everything the stage kernel needs about one instance (one Couette problem),
@@ -166,8 +169,8 @@ lbc_status fail(lbc_status st, const std::string &msg);
 const char *last_error();
 // Validates p (defaults already applied) and resolves the expansion orders.
 lbc_status validate(const lbc_params &p, int &Nxe, int &Nye);
-// TMA descriptor of a state buffer viewed as [2V rows][Nxp columns], box box_cols x kSubV.
-lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_cols);
+// TMA descriptor of a state buffer viewed as [V rows][2 Nxp columns], box 2 box_nodes x kSubV.
+lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_nodes);
 
 template <typename R>
 size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster);

@@ -187,6 +187,19 @@ __device__ __forceinline__ f2 max2(f2 a, f2 b)
     return mk2(fmaxf(al, bl), fmaxf(ah, bh));
 }
 
+// One (phi, chi) pair of an interleaved row: a single 64-bit access.
+__device__ __forceinline__ f2 ld2(const float *p)
+{
+    f2 r;
+    r.v = *reinterpret_cast<const unsigned long long *>(p);
+    return r;
+}
+__device__ __forceinline__ void st2(float *p, f2 a) { *reinterpret_cast<unsigned long long *>(p) = a.v; }
+
+// Integer bit pattern stored in a per-velocity row entry.
+__device__ __forceinline__ int row_bits(float x) { return __float_as_int(x); }
+__device__ __forceinline__ int row_bits(double x) { return (int)__double_as_longlong(x); }
+
 // WENO-5 (Jiang & Shu) on a packed pair, face between c and d, upwind cell c.
 // Nonlinear weights in product form, d_k prod_{m != k} E_m / sum, with the
 // E_m = (eps + beta_m)^2 first scaled by 1/max E_m (no overflow, two
@@ -283,6 +296,14 @@ __device__ __forceinline__ void raw_to_moments(const double *r, double sx, doubl
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory counter increment with acquire-release ordering at CTA scope.
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t *p, uint32_t v)
+{
+    uint32_t old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_addr(p)), "r"(v) : "memory");
+    return old;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
@@ -508,12 +529,17 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             e[6] = nu; e[7] = cS; e[8] = R(1) / (R(5) * Tc); e[9] = Tabs<R>::ijd(T)[s];
         }
         const R ip0 = Tabs<R>::sc(T, SC_IP0), Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
-        R *x = sc + tid * 8;
-        x[0] = sT; x[1] = a; x[2] = R(0.5) * a * a;
-        // g_y coefficients b_l = E[He_l(u' + sqrt(T') Y)] / l!: b_{l+1} = (u' b_l + (T'-1) b_{l-1}) / (l+1)
-        const R uq = uy * ip0, tm1 = Tp - R(1);
+        R *x = sc + tid * 8;   // sT a a^2/2 u'_y T'-1
+        x[0] = sT; x[1] = a; x[2] = R(0.5) * a * a; x[3] = uy * ip0; x[4] = Tp - R(1);
+    }
+    __syncthreads();
+    // g_y coefficients b_l = E[He_l(u' + sqrt(T') Y)] / l!: b_{l+1} = (u' b_l + (T'-1) b_{l-1}) / (l+1),
+    // by the last warp while the others run the g_x projection
+    if (tid >= kThreads - nn) {
+        const int i = tid - (kThreads - nn);
+        const R uq = sc[i * 8 + 3], tm1 = sc[i * 8 + 4];
         const R *invl = tab + E.invl;
-        R *b = bb + tid * (Ny + 1);
+        R *b = bb + i * (Ny + 1);
         R bm = R(1), bl = uq;
         b[0] = R(1);
         b[1] = uq;
@@ -524,7 +550,6 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             b[l + 1] = bn;
         }
     }
-    __syncthreads();
     // weights r_k^{+-} = W_k exp(+-a Y_k - a^2/2) of every (node, projection node)
     const R *Yk = tab + E.Yk, *Wk = tab + E.Wk;
     const int nk = nn * K;
@@ -538,6 +563,7 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
     // projection coefficients c^{+-}_l = sum_k r_k^{+-} h_l(sqrt(T') Y_k), in blocks of kLB orders:
     // recurrence state per (node, projection node) kept in registers across blocks
     constexpr int kItems = (kTile * kMaxK + kThreads - 1) / kThreads;
+    const int nit = (nk + kThreads - 1) / kThreads;   // items in use: the rest is skipped, not computed
     R zt[kItems], h[kItems], hp[kItems];
     const R *alpha = tab + E.alpha, *sbeta = tab + E.sbeta, *isbeta = tab + E.isbeta;
     const R h0 = Tabs<R>::sc(T, SC_H0);
@@ -546,7 +572,7 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
         const int idx = tid + it * kThreads;
         const int i = idx / K, k = idx - i * K;
         zt[it] = R(0);
-        if (idx < nk) zt[it] = sc[i * 8] * Yk[k];
+        if (it < nit && idx < nk) zt[it] = sc[i * 8] * Yk[k];
         h[it] = h0;
         hp[it] = R(0);
     }
@@ -556,11 +582,13 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             const R al = alpha[l], sb = sbeta[l], isb1 = isbeta[l + 1];
 #pragma unroll
             for (int it = 0; it < kItems; ++it) {
-                const int idx = tid + it * kThreads;
-                if (idx < nk) H[(l - lb) * nk + idx] = h[it];
-                const R hn = ((zt[it] - al) * h[it] - sb * hp[it]) * isb1;
-                hp[it] = h[it];
-                h[it] = hn;
+                if (it < nit) {
+                    const int idx = tid + it * kThreads;
+                    if (idx < nk) H[(l - lb) * nk + idx] = h[it];
+                    const R hn = ((zt[it] - al) * h[it] - sb * hp[it]) * isb1;
+                    hp[it] = h[it];
+                    h[it] = hn;
+                }
             }
         }
         __syncthreads();
@@ -602,14 +630,15 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
     }
 }
 
-// Outgoing WENO-5 wall face of a deviation row at the left (px < 0) or right
-// (px > 0) wall; two ghost nodes by cubic extrapolation in eta.
+// Outgoing WENO-5 wall face of the phi deviation of a state row (interleaved
+// (phi, chi) per node) at the left (px < 0) or right (px > 0) wall; two ghost
+// nodes by cubic extrapolation in eta.
 template <typename R>
 __device__ __forceinline__ R outgoing_wall_face(const R *row, int Nx, bool right)
 {
     R f1, f2, f3, f4;
-    if (right) { f1 = row[Nx - 1]; f2 = row[Nx - 2]; f3 = row[Nx - 3]; f4 = row[Nx - 4]; }
-    else       { f1 = row[0];      f2 = row[1];      f3 = row[2];      f4 = row[3]; }
+    if (right) { f1 = row[2 * (Nx - 1)]; f2 = row[2 * (Nx - 2)]; f3 = row[2 * (Nx - 3)]; f4 = row[2 * (Nx - 4)]; }
+    else       { f1 = row[0];            f2 = row[2];            f3 = row[4];            f4 = row[6]; }
     R g1 = R(4) * f1 - R(6) * f2 + R(4) * f3 - f4;
     R g2 = R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
     return weno5<R>(f3, f2, f1, g1, g2);
@@ -624,7 +653,7 @@ __device__ void block_wall_density(const DevTables &T, const R *phi, bool right,
     const R *vel = Tabs<R>::vel(T);
     double acc = 0.0;
     for (int v = vbeg + threadIdx.x; v < vbeg + half; v += blockDim.x) {
-        R f = outgoing_wall_face<R>(phi + (size_t)v * T.Nxp, T.Nx, right);
+        R f = outgoing_wall_face<R>(phi + 2 * (size_t)v * T.Nxp, T.Nx, right);
         acc += (double)(vel[VC_PX * T.V + v] * vel[VC_W * T.V + v] * f);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -649,7 +678,7 @@ struct Layout {
     __host__ __device__ Layout(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster)
     {
         size_t o = 0;
-        bar = o;  o = al(o + (kPipe + 2) * sizeof(uint64_t));
+        bar = o;  o = al(o + (kPipe + 2) * sizeof(uint64_t) + (kPipe + 1) * sizeof(uint32_t));
         pipe = o;
         fin = o;
         f0 = fin + (size_t)kPipe * 2 * kSubV * kRowLen * sizeof(R);
@@ -683,8 +712,10 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk, T.nchunk);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);   // [kPipe] rows, data, tables
     uint64_t *bar_data = bar + kPipe, *bar_tab = bar + kPipe + 1;
-    R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][2][kSubV][kRowLen]
-    R *s_f0 = reinterpret_cast<R *>(smem + L.f0);         // [kPipe][2][kSubV][kF0Len]
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(bar + kPipe + 2);   // [kPipe] warps done with a slot
+    int *s_abort = reinterpret_cast<int *>(s_cnt + kPipe);              // a warp gave up waiting
+    R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][kSubV][2 kRowLen]: (phi, chi) per node
+    R *s_f0 = reinterpret_cast<R *>(smem + L.f0);         // [kPipe][kSubV][2 kF0Len]
     R *s_g = reinterpret_cast<R *>(smem + L.g);           // [2Qx + Qy][kLanes]
     R *s_eqm = reinterpret_cast<R *>(smem + L.eqm);       // [kTile][kEqM]
     R *s_vrow = reinterpret_cast<R *>(smem + L.vrow);     // [vchunk][kVRow]
@@ -731,21 +762,19 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, ncap);
     const uint32_t tab_bytes = (uint32_t)(EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy).len * sizeof(R));
 
+    // rows v0 .. v0 + kSubV - 1 of the stage input (nodes x0 .. x0 + kRowLen - 1) and of the
+    // RK base (nodes xf ..), both fields; rows past V read as zeros
     auto issue = [&](int sub) {
         int p = sub % kPipe, v0 = vbeg + sub * kSubV;
-        R *fin = s_fin + (size_t)p * 2 * kSubV * kRowLen;
         mbar_expect_tx(&bar[p], tx_bytes);
-        tma_load_2d(fin, in_map, x0, v0, &bar[p]);
-        tma_load_2d(fin + kSubV * kRowLen, in_map, x0, V + v0, &bar[p]);
-        if (stage > 0) {
-            R *f0 = s_f0 + (size_t)p * 2 * kSubV * kF0Len;
-            tma_load_2d(f0, &M.f0, xf, v0, &bar[p]);
-            tma_load_2d(f0 + kSubV * kF0Len, &M.f0, xf, V + v0, &bar[p]);
-        }
+        tma_load_2d(s_fin + (size_t)p * kSubV * 2 * kRowLen, in_map, 2 * x0, v0, &bar[p]);
+        if (stage > 0) tma_load_2d(s_f0 + (size_t)p * kSubV * 2 * kF0Len, &M.f0, 2 * xf, v0, &bar[p]);
     };
 
     if (tid == 0) {
         for (int p = 0; p < kPipe + 2; ++p) mbar_init(&bar[p], 1);
+        for (int p = 0; p < kPipe; ++p) s_cnt[p] = 0;
+        *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -764,7 +793,6 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
 
     const R *Fin = static_cast<const R *>(S.F[in]);
     R *Fout = static_cast<R *>(S.F[out]);
-    const size_t fstride = (size_t)V * T.Nxp;
 
     // ---- (2) wall densities (tiles whose stencil reaches a wall), while the copies land ----
     const bool needL = c0 == 0;
@@ -784,29 +812,32 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     }
     const R nwL = R(needL ? s_misc[8] : 0.0), nwR = R(needR ? s_misc[9] : 0.0);
 
-    // ---- (3) stream the chunk's velocity rows ----
+    // ---- (3) stream the chunk's velocity rows: every warp runs its own rows of each
+    // pipeline slot; the last warp to release a slot issues its refill ----
     const R ca = R(stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0));
     const R cb = R(stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0));
     const R dt = Tabs<R>::sc(T, SC_DT);
     const bool wall = needL || needR;
-    const int ck = lane + 3 + off;          // column of node c0 + lane
+    const int ck = lane + 3 + off;          // node column of node c0 + lane
+    const int Nxp = T.Nxp, Nx = T.Nx;
+    R *Fout_s = Fout + 2 * (size_t)s;       // this lane's node in row v: Fout_s + 2 Nxp v
 
     R acc[kNumRaw];
 #pragma unroll
     for (int m = 0; m < kNumRaw; ++m) acc[m] = R(0);
     R res = R(0);
+    constexpr int NQ = kSubV / kWarps;      // rows per warp and slot: rows warp + kWarps q
+    bool my_timeout = false;
 
     for (int sub = 0; sub < nsub && !timed_out; ++sub) {
         const int p = sub % kPipe;
-        if (__syncthreads_or(!mbar_wait(&bar[p], (uint32_t)((sub / kPipe) & 1)))) {
-            timed_out = true;
+        if (__any_sync(0xffffffffu, !mbar_wait(&bar[p], (uint32_t)((sub / kPipe) & 1))) ||
+            *reinterpret_cast<volatile int *>(s_abort)) {
+            my_timeout = true;
             break;
         }
-        R *fin = s_fin + (size_t)p * 2 * kSubV * kRowLen;
-        const R *f0 = s_f0 + (size_t)p * 2 * kSubV * kF0Len;
-        // the warp's two velocities (rows warp and warp + kWarps) are processed
-        // together: four independent WENO-5 chains per lane
-        constexpr int NQ = kSubV / kWarps;
+        R *fin = s_fin + (size_t)p * kSubV * 2 * kRowLen;
+        const R *f0 = s_f0 + (size_t)p * kSubV * 2 * kF0Len;
         int kq[NQ];
         bool ok[NQ];
 #pragma unroll
@@ -816,84 +847,94 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
             if (!ok[q]) kq[q] = vend - vbeg - 1;   // the chunk's last velocity row; results are discarded
         }
         if (wall) {
-            // ghost nodes: lanes 0-15 -> (velocity, field, side, node)
-            if (lane < 8 * NQ) {
-                const int q = lane >> 3, fld = (lane >> 2) & 1, side = (lane >> 1) & 1, gi = lane & 1;
-                const int r = warp + kWarps * q;
+            // ghost nodes, both fields at once: lanes 0-7 -> (row, side, node)
+            if (lane < 4 * NQ) {
+                const int q = lane >> 2, side = (lane >> 1) & 1, gi = lane & 1;
                 int kqq = kq[0];
                 bool okq = ok[0];
 #pragma unroll
                 for (int qq = 1; qq < NQ; ++qq)   // select, not a dynamic index (keeps kq, ok in registers)
                     if (q == qq) { kqq = kq[qq]; okq = ok[qq]; }
                 const R *x = s_vrow + kqq * kVRow;
-                const bool pos = (int)x[VR_A] < T.Qx;
-                R *row = fin + (size_t)(fld * kSubV + r) * kRowLen;
+                const bool pos = x[VR_PX] > R(0);
+                R *row = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen;
                 if (okq && side == 0 && needL) {          // nodes -1 (gi 0), -2 (gi 1)
-                    R g;
-                    if (pos) g = nwL * x[VR_FWL + fld] - x[VR_FR];
-                    else {
-                        const int cz = -x0;      // column of node 0
-                        R f1 = row[cz], f2 = row[cz + 1], f3 = row[cz + 2], f4 = row[cz + 3];
-                        g = gi == 0 ? R(4) * f1 - R(6) * f2 + R(4) * f3 - f4
-                                    : R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
+                    R g0, g1;
+                    if (pos) {
+                        g0 = nwL * x[VR_FWL] - x[VR_FR];
+                        g1 = nwL * x[VR_FWLT] - x[VR_FR];
+                    } else {
+                        const R *f = row + 2 * (-x0);     // node 0
+                        const R c1 = gi == 0 ? R(4) : R(10), c2 = gi == 0 ? R(-6) : R(-20);
+                        const R c3 = gi == 0 ? R(4) : R(15), c4 = gi == 0 ? R(-1) : R(-4);
+                        g0 = c1 * f[0] + c2 * f[2] + c3 * f[4] + c4 * f[6];
+                        g1 = c1 * f[1] + c2 * f[3] + c3 * f[5] + c4 * f[7];
                     }
-                    row[-1 - gi - x0] = g;
+                    R *gp = row + 2 * (-1 - gi - x0);
+                    gp[0] = g0;
+                    gp[1] = g1;
                 } else if (okq && side == 1 && needR) {   // nodes Nx (gi 0), Nx+1 (gi 1)
-                    R g;
-                    if (!pos) g = nwR * x[VR_FWR + fld] - x[VR_FR];
-                    else {
-                        const int cl = T.Nx - 1 - x0;
-                        R f1 = row[cl], f2 = row[cl - 1], f3 = row[cl - 2], f4 = row[cl - 3];
-                        g = gi == 0 ? R(4) * f1 - R(6) * f2 + R(4) * f3 - f4
-                                    : R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
+                    R g0, g1;
+                    if (!pos) {
+                        g0 = nwR * x[VR_FWR] - x[VR_FR];
+                        g1 = nwR * x[VR_FWRT] - x[VR_FR];
+                    } else {
+                        const R *f = row + 2 * (Nx - 1 - x0);   // node Nx - 1
+                        const R c1 = gi == 0 ? R(4) : R(10), c2 = gi == 0 ? R(-6) : R(-20);
+                        const R c3 = gi == 0 ? R(4) : R(15), c4 = gi == 0 ? R(-1) : R(-4);
+                        g0 = c1 * f[0] + c2 * f[-2] + c3 * f[-4] + c4 * f[-6];
+                        g1 = c1 * f[1] + c2 * f[-1] + c3 * f[-3] + c4 * f[-5];
                     }
-                    const int colR = T.Nx + gi - x0;   // beyond the box only if never referenced
-                    if (colR < kRowLen) row[colR] = g;
+                    const int colR = Nx + gi - x0;       // beyond the box only if never referenced
+                    if (colR < kRowLen) {
+                        row[2 * colR] = g0;
+                        row[2 * colR + 1] = g1;
+                    }
                 }
             }
             __syncwarp();
         }
         if constexpr (std::is_same<R, float>::value) {
-            // FP32: (phi, chi) as packed pairs
+            // FP32: (phi, chi) as packed pairs, loaded and stored as one 64-bit access each
             f2 fl[NQ], dd[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const R *x = s_vrow + kq[q] * kVRow;
-                const bool pos = (int)x[VR_A] < T.Qx;
+                const float4 xa = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow);   // px py w fr
+                const bool pos = xa.x > 0.f;
                 const int base = pos ? ck - 3 : ck + 2, st = pos ? 1 : -1;   // upwind stencil order
-                const R *r0 = fin + (size_t)(warp + kWarps * q) * kRowLen;
-                const R *r1 = fin + (size_t)(kSubV + warp + kWarps * q) * kRowLen;
+                const float *row = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen;
                 f2 v[5];
 #pragma unroll
-                for (int i = 0; i < 5; ++i) v[i] = mk2(r0[base + i * st], r1[base + i * st]);
+                for (int i = 0; i < 5; ++i) v[i] = ld2(row + 2 * (base + i * st));
                 fl[q] = weno5_2(v[0], v[1], v[2], v[3], v[4]);   // face c0 + lane
-                dd[q] = mk2(r0[ck], r1[ck]);
+                dd[q] = pos ? v[3] : v[2];                        // the node itself
                 if (wall) {
-                    const R fr = x[VR_FR];
-                    if (pos && s == 0) fl[q] = mk2(nwL * x[VR_FWL] - fr, nwL * x[VR_FWLT] - fr);
-                    if (!pos && s == T.Nx) fl[q] = mk2(nwR * x[VR_FWR] - fr, nwR * x[VR_FWRT] - fr);
+                    const float4 xw = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow + 4);
+                    if (pos && s == 0) fl[q] = mk2(nwL * xw.x - xa.w, nwL * xw.y - xa.w);
+                    if (!pos && s == Nx) fl[q] = mk2(nwR * xw.z - xa.w, nwR * xw.w - xa.w);
                 }
             }
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const R *x = s_vrow + kq[q] * kVRow;
-                const int a = (int)x[VR_A], j = (int)x[VR_J], r = warp + kWarps * q, v = vbeg + kq[q];
-                const R px = x[VR_PX], py = x[VR_PY], w = x[VR_W], fr = x[VR_FR];
-                const R feq = n_c * s_g[a * kLanes + lane] * s_g[(2 * T.Qx + j) * kLanes + lane];
-                const R xx = px - ux_c, xy = py - uy_c;
-                const R qxi = qx_c * xx + qy_c * xy;
-                const R x2 = (xx * xx + xy * xy) * i5T;
+                const float4 xa = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow);   // px py w fr
+                const float4 xg = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow + 8);
+                const int ga = __float_as_int(xg.x), gj = __float_as_int(xg.y);
+                const int r = warp + kWarps * q, v = vbeg + kq[q];
+                const float px = xa.x, py = xa.y, w = xa.z, fr = xa.w;
+                const float feq = n_c * s_g[ga + lane] * s_g[gj + lane];
+                const float xx = px - ux_c, xy = py - uy_c;
+                const float qxi = qx_c * xx + qy_c * xy;
+                const float e2 = xx * xx + xy * xy;
                 float fll, flh;
                 un2(fl[q], fll, flh);
                 const f2 frt = mk2(__shfl_down_sync(0xffffffffu, fll, 1), __shfl_down_sync(0xffffffffu, flh, 1));
                 const f2 adv = (fl[q] - frt) * bc2(px * ijd);
                 // Shakhov targets minus the rest state: (phi_eq (1 + S_phi), chi_eq (1 + S_chi)) - ft_rest
-                const f2 sh = fma2(bc2(cS_c * qxi), bc2(x2) - mk2(0.8f, 0.4f), bc2(1.f));
+                const f2 sh = fma2(bc2(cS_c * qxi), bc2(e2 * i5T) - mk2(0.8f, 0.4f), bc2(1.f));
                 const f2 tgt = fma2(mk2(feq, T_c * feq), sh, bc2(-fr));
                 f2 dn = fma2(bc2(dt), fma2(bc2(-nu_c), dd[q] - tgt, adv), dd[q]);
-                float o0, o1;
                 if (stage > 0) {
-                    const f2 d0 = mk2(f0[r * kF0Len + lane + offf], f0[(kSubV + r) * kF0Len + lane + offf]);
+                    const f2 d0 = ld2(f0 + (size_t)r * 2 * kF0Len + 2 * (lane + offf));
                     dn = fma2(bc2(ca), d0, bc2(cb) * dn);
                     if (stage == 2 && active && ok[q]) {
                         float e0, e1;
@@ -901,12 +942,11 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                         res = fmaxf(res, w * fmaxf(fabsf(e0), fabsf(e1)));
                     }
                 }
-                un2(dn, o0, o1);
                 if (active && ok[q]) {
-                    Fout[(size_t)v * T.Nxp + s] = o0;
-                    Fout[fstride + (size_t)v * T.Nxp + s] = o1;
-                    const R fw = w * o0, gw = w * o1;
-                    const R e2 = xx * xx + xy * xy;
+                    st2(Fout_s + 2 * (size_t)Nxp * v, dn);
+                    float o0, o1;
+                    un2(dn, o0, o1);
+                    const float fw = w * o0, gw = w * o1;
                     acc[R_S0] += fw;
                     acc[R_SX] += xx * fw;
                     acc[R_SY] += xy * fw;
@@ -922,36 +962,45 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
             }
         } else {
             R fl[NQ][2], dd[NQ][2];
-            bool posq[NQ];
-    #pragma unroll
+#pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const R *x = s_vrow + kq[q] * kVRow;
-                posq[q] = (int)x[VR_A] < T.Qx;
-                const int base = posq[q] ? ck - 3 : ck + 2, st = posq[q] ? 1 : -1;   // upwind stencil order
-    #pragma unroll
+                const bool pos = x[VR_PX] > R(0);
+                const int base = pos ? ck - 3 : ck + 2, st = pos ? 1 : -1;   // upwind stencil order
+                const R *row = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen;
+                R v[5][2];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    const double2 t = *reinterpret_cast<const double2 *>(row + 2 * (base + i * st));
+                    v[i][0] = t.x;
+                    v[i][1] = t.y;
+                }
+#pragma unroll
                 for (int fld = 0; fld < 2; ++fld) {
-                    const R *row = fin + (size_t)(fld * kSubV + warp + kWarps * q) * kRowLen;
                     // face c0 + lane (left of node c0 + lane)
-                    fl[q][fld] = weno5<R>(row[base], row[base + st], row[base + 2 * st], row[base + 3 * st],
-                                          row[base + 4 * st]);
-                    dd[q][fld] = row[ck];
+                    fl[q][fld] = weno5<R>(v[0][fld], v[1][fld], v[2][fld], v[3][fld], v[4][fld]);
+                    dd[q][fld] = pos ? v[3][fld] : v[2][fld];
                     if (wall) {
-                        if (posq[q] && s == 0) fl[q][fld] = nwL * x[VR_FWL + fld] - x[VR_FR];
-                        if (!posq[q] && s == T.Nx) fl[q][fld] = nwR * x[VR_FWR + fld] - x[VR_FR];
+                        if (pos && s == 0) fl[q][fld] = nwL * x[VR_FWL + fld] - x[VR_FR];
+                        if (!pos && s == Nx) fl[q][fld] = nwR * x[VR_FWR + fld] - x[VR_FR];
                     }
                 }
             }
-    #pragma unroll
+#pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const R *x = s_vrow + kq[q] * kVRow;
-                const int a = (int)x[VR_A], j = (int)x[VR_J], r = warp + kWarps * q, v = vbeg + kq[q];
+                const int ga = row_bits(x[VR_GA]), gj = row_bits(x[VR_GJ]);
+                const int r = warp + kWarps * q, v = vbeg + kq[q];
                 const R px = x[VR_PX], py = x[VR_PY], w = x[VR_W], fr = x[VR_FR];
-                const R feq = n_c * s_g[a * kLanes + lane] * s_g[(2 * T.Qx + j) * kLanes + lane];
+                const R feq = n_c * s_g[ga + lane] * s_g[gj + lane];
                 const R xx = px - ux_c, xy = py - uy_c;
                 const R qxi = qx_c * xx + qy_c * xy;
                 const R x2 = (xx * xx + xy * xy) * i5T;
                 R fo[2];
-    #pragma unroll
+                const double2 d0 = stage > 0 ? *reinterpret_cast<const double2 *>(f0 + (size_t)r * 2 * kF0Len +
+                                                                                 2 * (lane + offf))
+                                             : make_double2(0.0, 0.0);
+#pragma unroll
                 for (int fld = 0; fld < 2; ++fld) {
                     const R frt = __shfl_down_sync(0xffffffffu, fl[q][fld], 1);
                     const R d = dd[q][fld];
@@ -961,14 +1010,14 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                                       : feq * (R(1) + cS_c * (x2 - R(0.8)) * qxi) - fr;
                     R dn = d + dt * (adv - nu_c * (d - tgt));
                     if (stage > 0) {
-                        const R d0 = f0[(fld * kSubV + r) * kF0Len + lane + offf];
-                        dn = ca * d0 + cb * dn;
-                        if (stage == 2 && active && ok[q]) res = fmax(res, w * fabs(dn - d0));
+                        const R b0 = fld ? d0.y : d0.x;
+                        dn = ca * b0 + cb * dn;
+                        if (stage == 2 && active && ok[q]) res = fmax(res, w * fabs(dn - b0));
                     }
-                    if (active && ok[q]) Fout[fld * fstride + (size_t)v * T.Nxp + s] = dn;
                     fo[fld] = dn;
                 }
                 if (active && ok[q]) {
+                    *reinterpret_cast<double2 *>(Fout_s + 2 * (size_t)Nxp * v) = make_double2(fo[0], fo[1]);
                     const R fw = w * fo[0], gw = w * fo[1];
                     const R e2 = xx * xx + xy * xy;
                     acc[R_S0] += fw;
@@ -985,11 +1034,17 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                 }
             }
         }
-        // order this thread's generic accesses to buffer p before the next TMA write into it
+        // release slot p: order this warp's accesses to it before the refill's async writes;
+        // the warp that completes the round issues the refill
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();   // every warp is done with buffer p
-        if (tid == 0 && sub + kPipe < nsub) issue(sub + kPipe);
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t ticket = atom_add_acq_rel(&s_cnt[p], 1u);
+            if (ticket == (uint32_t)((sub / kPipe + 1) * kWarps - 1) && sub + kPipe < nsub) issue(sub + kPipe);
+        }
     }
+    if (my_timeout && lane == 0) *reinterpret_cast<volatile int *>(s_abort) = 1;
+    timed_out = __syncthreads_or(timed_out || my_timeout);
 
     const int rank = (int)cluster_ctarank(), nch = T.nchunk;
     const int nn = (kTile - rank + nch - 1) / nch;          // nodes rank, rank + nch, ... of the tile
@@ -1117,15 +1172,14 @@ moments_partial_kernel(const __grid_constant__ DevTables T, const __grid_constan
     const int c0 = blockIdx.x * kTile, chunk = blockIdx.y, s = c0 + lane;
     const bool active = lane < kTile && s < T.Nx;
     const R *F = static_cast<const R *>(S.F[buf]);
-    const size_t fstride = (size_t)T.V * T.Nxp;
     double acc[kNumRaw];
 #pragma unroll
     for (int m = 0; m < kNumRaw; ++m) acc[m] = 0.0;
     const int vbeg = chunk * T.vchunk, vend = min(T.V, vbeg + T.vchunk);
     for (int v = vbeg + warp; v < vend && active; v += kWarps) {
         const double px = T.d_vel[VC_PX * T.V + v], py = T.d_vel[VC_PY * T.V + v], w = T.d_vel[VC_W * T.V + v];
-        const double fw = w * (double)F[(size_t)v * T.Nxp + s];
-        const double gw = w * (double)F[fstride + (size_t)v * T.Nxp + s];
+        const double fw = w * (double)F[2 * ((size_t)v * T.Nxp + s)];
+        const double gw = w * (double)F[2 * ((size_t)v * T.Nxp + s) + 1];
         const double e2 = px * px + py * py;
         acc[R_S0] += fw; acc[R_SX] += px * fw; acc[R_SY] += py * fw;
         acc[R_SXX] += px * px * fw; acc[R_SXY] += px * py * fw; acc[R_SYY] += py * py * fw;

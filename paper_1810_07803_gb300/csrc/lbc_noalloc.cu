@@ -57,15 +57,15 @@ lbc_status scratch_on_current_device(void **out)
     return LBC_OK;
 }
 
-// Caller's weight-divided FP64 state [2][V][Nx] <-> deviation buffer [2][V][Nxp] (state precision).
+// Caller's weight-divided FP64 state [2][V][Nx] <-> deviation buffer [V][Nxp][2] (state precision).
 template <typename R>
 __global__ void state_in_kernel(const double *src, R *dst, const double *frest, int V, int Nx, int Nxp)
 {
     const size_t n = 2 * (size_t)V * Nx;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i / Nx;
+        const size_t row = i / Nx, v = row % V, fld = row / V;
         const int s = (int)(i - row * Nx);
-        dst[row * Nxp + s] = R(src[i] - frest[row % V]);
+        dst[2 * (v * Nxp + s) + fld] = R(src[i] - frest[v]);
     }
 }
 
@@ -74,9 +74,9 @@ __global__ void state_out_kernel(const R *src, double *dst, const double *frest,
 {
     const size_t n = 2 * (size_t)V * Nx;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i / Nx;
+        const size_t row = i / Nx, v = row % V, fld = row / V;
         const int s = (int)(i - row * Nx);
-        dst[i] = frest[row % V] + (double)src[row * Nxp + s];
+        dst[i] = frest[v] + (double)src[2 * (v * Nxp + s) + fld];
     }
 }
 

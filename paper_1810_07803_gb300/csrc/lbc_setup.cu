@@ -123,8 +123,8 @@ bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std:
     for (int v = 0; v < V; ++v) {
         const int cols[8] = {VC_PX, VC_PY, VC_W, VC_FR, VC_FWL, VC_FWLT, VC_FWR, VC_FWRT};
         for (int c = 0; c < 8; ++c) ps.vrow[(size_t)v * kVRow + c] = ps.vel[(size_t)cols[c] * V + v];
-        ps.vrow[(size_t)v * kVRow + VR_A] = ps.aj[v];
-        ps.vrow[(size_t)v * kVRow + VR_J] = ps.aj[V + v];
+        ps.vrow[(size_t)v * kVRow + VR_GA] = ps.aj[v] * kLanes;                  // integer bits, below
+        ps.vrow[(size_t)v * kVRow + VR_GJ] = (2 * p.Qx + ps.aj[V + v]) * kLanes;
     }
     if ((int)t.alpha.size() < Nxe + 2 || (int)t.sbeta.size() < Nxe + 2) {
         err = "internal: recurrence table too short";
@@ -163,6 +163,27 @@ bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std:
         off += pad_f(pc.src->size());
     }
     std::memcpy(ps.blob.data() + dbytes + fbytes, ps.aj.data(), ps.aj.size() * sizeof(int));
+    // the row offsets of the per-velocity rows as integer bit patterns in both copies
+    off = 0;
+    for (auto &pc : dpieces(ps, dummy)) {
+        if (pc.src == &ps.vrow)
+            for (int v = 0; v < V; ++v)
+                for (int c : {VR_GA, VR_GJ}) {
+                    const long long bits = (long long)ps.vrow[(size_t)v * kVRow + c];
+                    std::memcpy(ps.blob.data() + (off + (size_t)v * kVRow + c) * sizeof(double), &bits, 8);
+                }
+        off += pad_d(pc.src->size());
+    }
+    off = 0;
+    for (auto &pc : fpieces(ps, dummy)) {
+        if (pc.src == &ps.vrow)
+            for (int v = 0; v < V; ++v)
+                for (int c : {VR_GA, VR_GJ}) {
+                    const int bits = (int)ps.vrow[(size_t)v * kVRow + c];
+                    std::memcpy(ps.blob.data() + dbytes + (off + (size_t)v * kVRow + c) * sizeof(float), &bits, 4);
+                }
+        off += pad_f(pc.src->size());
+    }
     return true;
 }
 
@@ -210,7 +231,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_cols)
+lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_nodes)
 {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -222,9 +243,9 @@ lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int 
         fn = reinterpret_cast<EncodeTiledFn>(ptr);
     }
     const size_t esz = fp32 ? 4 : 8;
-    cuuint64_t dims[2] = {(cuuint64_t)Nxp, (cuuint64_t)(2 * V)};
-    cuuint64_t strides[1] = {(cuuint64_t)Nxp * esz};
-    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)kSubV};
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * Nxp), (cuuint64_t)V};
+    cuuint64_t strides[1] = {(cuuint64_t)(2 * Nxp) * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * box_nodes), (cuuint32_t)kSubV};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
