@@ -257,8 +257,12 @@ def main():
     units = nsol * V * Nx
     value = units * world / (ms / 1e3)
 
-    # end to end through the public API: host states in, host moments out, every step
-    host_states = [batch.get_state(i) for i in range(nsol)]
+    # end to end through the public API: host states in (pinned), host moments out, every step
+    host_states = []
+    for i in range(nsol):
+        t = torch.empty((2, V, Nx), dtype=torch.float64, pin_memory=True)
+        batch.get_state(i, out=t)
+        host_states.append(t)
     e2e_steps = min(args.steps, 10)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -270,7 +274,7 @@ def main():
             batch.moments(i)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    h2d = sum(hs.nbytes for hs in host_states)
+    h2d = sum(hs.numel() * hs.element_size() for hs in host_states)
     d2h = nsol * lbc.NMOM * Nx * 8
 
     fp64 = None
@@ -295,7 +299,8 @@ def main():
                        launch="one batched stage launch per RK stage for the four solves"),
         "e2e": {"value": units * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "path": "per step and solve: lbc_set_state(host f64) + lbc_step(1) + lbc_moments(host)"},
+                "path": "per step: lbc_batch_set_state(pinned host f64) per solve + lbc_batch_step(1) + "
+                        "lbc_batch_moments(host) per solve"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.precision),
                      "kernel": "stage_batch_kernel<float>" if args.precision == "fp32" else "stage_batch_kernel<double>",

@@ -53,8 +53,11 @@ struct lbc_batch {
     void *state_block = nullptr;  // states, stage data, partials, residual rings, control
     Ctl *d_ctl = nullptr;         // [n]
     double *d_last = nullptr;     // [n] last residual of each instance
+    double *d_io = nullptr;       // staging of one instance's FP64 host-layout state
+    int *d_bad = nullptr;         // set by the state upload when a value is not finite
     Ctl *h_ctl = nullptr;         // pinned [n]
     double *h_last = nullptr;     // pinned [n]
+    int *h_bad = nullptr;         // pinned
     bool steady_mode = false;     // the device control blocks hold run-to-steady settings
     bool poisoned = false;        // some instance holds a NaN/Inf
     cudaGraphExec_t graph = nullptr;
@@ -300,8 +303,11 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
         soff[i] = sbytes;
         sbytes += StateSizes(b->inst[i].T, b->fp32).total;
     }
+    size_t io_elems = 0;
+    for (int i = 0; i < n; ++i) io_elems = std::max(io_elems, 2 * (size_t)b->inst[i].T.V * b->inst[i].T.Nx);
     const size_t ctl_off = sbytes, last_off = ctl_off + r256(n * sizeof(Ctl));
-    sbytes = last_off + r256(n * sizeof(double));
+    const size_t io_off = last_off + r256(n * sizeof(double)), bad_off = io_off + r256(io_elems * sizeof(double));
+    sbytes = bad_off + 256;
     e = cudaMallocAsync(&b->state_block, sbytes, b->stream);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMallocAsync(state): ") + cudaGetErrorString(e));
@@ -312,6 +318,8 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     char *sb = static_cast<char *>(b->state_block);
     b->d_ctl = reinterpret_cast<Ctl *>(sb + ctl_off);
     b->d_last = reinterpret_cast<double *>(sb + last_off);
+    b->d_io = reinterpret_cast<double *>(sb + io_off);
+    b->d_bad = reinterpret_cast<int *>(sb + bad_off);
     for (int i = 0; i < n; ++i) {
         DevTables &T = b->inst[i].T;
         DevState &S = b->inst[i].S;
@@ -331,6 +339,7 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     }
     e = cudaMallocHost(&b->h_ctl, n * sizeof(Ctl));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_last, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_bad, sizeof(int));
     if (e != cudaSuccess) {
         set_error(std::string("cudaMallocHost: ") + cudaGetErrorString(e));
         return cleanup(e == cudaErrorMemoryAllocation ? LBC_ENOMEM : LBC_ECUDA);
@@ -415,10 +424,8 @@ lbc_status batch_moments(lbc_batch *b, int i, double *out, double *x)
     if (st != LBC_OK) return st;
     if (!out) return fail(LBC_EINVAL, "NULL argument");
     const Inst &I = b->inst[i];
-    LBC_CUDA_TRY(b->fp32 ? launch_moments_partial<float>(I.T, I.S, 0, b->stream)
-                         : launch_moments_partial<double>(I.T, I.S, 0, b->stream));
-    LBC_CUDA_TRY(b->fp32 ? launch_finalize_moments<float>(I.T, I.S, b->stream)
-                         : launch_finalize_moments<double>(I.T, I.S, b->stream));
+    LBC_CUDA_TRY(b->fp32 ? launch_moments_from_stage_data<float>(I.T, I.S, b->stream)
+                         : launch_moments_from_stage_data<double>(I.T, I.S, b->stream));
     LBC_CUDA_TRY(cudaMemcpy2DAsync(out, I.T.Nx * sizeof(double), I.S.mom_out, I.T.Nxp * sizeof(double),
                                    I.T.Nx * sizeof(double), LBC_NMOM, cudaMemcpyDeviceToHost, b->stream));
     st = read_ctl(b);
@@ -432,57 +439,43 @@ lbc_status batch_get_state(lbc_batch *b, int i, double *state)
     lbc_status st = check_index(b, i);
     if (st != LBC_OK) return st;
     if (!state) return fail(LBC_EINVAL, "NULL argument");
-    const DevTables &T = b->inst[i].T;
-    const int V = T.V, Nx = T.Nx, Nxp = T.Nxp;
-    const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
-    std::vector<unsigned char> tmp(2 * (size_t)V * Nxp * esz);
-    LBC_CUDA_TRY(cudaMemcpyAsync(tmp.data(), b->inst[i].S.F[0], tmp.size(), cudaMemcpyDeviceToHost, b->stream));
+    const Inst &I = b->inst[i];
+    const size_t bytes = 2 * (size_t)I.T.V * I.T.Nx * sizeof(double);
+    LBC_CUDA_TRY(b->fp32 ? launch_state_out<float>(I.S.F[0], b->d_io, I.T, b->stream)
+                         : launch_state_out<double>(I.S.F[0], b->d_io, I.T, b->stream));
+    LBC_CUDA_TRY(cudaMemcpyAsync(state, b->d_io, bytes, cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
-    const std::vector<double> &frest = b->ih[i].frest;
-    // device rows [V][Nxp][2] (phi, chi adjacent) -> host [2][V][Nx]
-    for (size_t r = 0; r < 2 * (size_t)V; ++r) {
-        const size_t v = r % V, fld = r / V;
-        const double fr = frest[v];
-        for (int c = 0; c < Nx; ++c) {
-            const size_t k = 2 * (v * Nxp + c) + fld;
-            state[r * Nx + c] = fr + (b->fp32 ? (double)reinterpret_cast<float *>(tmp.data())[k]
-                                              : reinterpret_cast<double *>(tmp.data())[k]);
-        }
-    }
     for (int k = 0; k < b->n; ++k)
         if (b->h_ctl[k].timeout) return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
     return LBC_OK;
 }
 
+// The host state goes to the device as it is (one copy); a kernel converts it
+// into the second RK buffer, which is free between steps, and checks it, so a
+// rejected state leaves the instance unchanged.
 lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
 {
     lbc_status st = check_index(b, i);
     if (st != LBC_OK) return st;
     if (!state) return fail(LBC_EINVAL, "NULL argument");
-    const DevTables &T = b->inst[i].T;
-    const int V = T.V, Nx = T.Nx, Nxp = T.Nxp;
-    for (size_t k = 0; k < 2 * (size_t)V * Nx; ++k)
-        if (!std::isfinite(state[k])) return fail(LBC_EINVAL, "state holds a NaN or Inf");
-    const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
-    std::vector<unsigned char> tmp(2 * (size_t)V * Nxp * esz, 0);
-    const std::vector<double> &frest = b->ih[i].frest;
-    for (size_t r = 0; r < 2 * (size_t)V; ++r) {   // host [2][V][Nx] -> device [V][Nxp][2]
-        const size_t v = r % V, fld = r / V;
-        const double fr = frest[v];
-        for (int c = 0; c < Nx; ++c) {
-            const size_t k = 2 * (v * Nxp + c) + fld;
-            if (b->fp32) reinterpret_cast<float *>(tmp.data())[k] = (float)(state[r * Nx + c] - fr);
-            else reinterpret_cast<double *>(tmp.data())[k] = state[r * Nx + c] - fr;
-        }
-    }
-    // control blocks: keep the others' flags, clear this instance's
+    const Inst &I = b->inst[i];
+    const size_t bytes = 2 * (size_t)I.T.V * I.T.Nx * sizeof(double);
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->d_io, state, bytes, cudaMemcpyHostToDevice, b->stream));
+    LBC_CUDA_TRY(cudaMemsetAsync(b->d_bad, 0, sizeof(int), b->stream));
+    LBC_CUDA_TRY(b->fp32 ? launch_state_in<float>(b->d_io, I.S.F[1], I.T, b->d_bad, b->stream)
+                         : launch_state_in<double>(b->d_io, I.S.F[1], I.T, b->d_bad, b->stream));
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->h_bad, b->d_bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (*b->h_bad) return fail(LBC_EINVAL, "state holds a NaN or Inf");
+    // control blocks: keep the others' flags, clear this instance's
     b->h_ctl[i].nonfinite = 0;
     bool any = false;
     for (int k = 0; k < b->n; ++k) any = any || b->h_ctl[k].nonfinite;
-    LBC_CUDA_TRY(cudaMemcpyAsync(b->inst[i].S.F[0], tmp.data(), tmp.size(), cudaMemcpyHostToDevice, b->stream));
+    const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
+    LBC_CUDA_TRY(cudaMemcpyAsync(I.S.F[0], I.S.F[1], 2 * (size_t)I.T.V * I.T.Nxp * esz, cudaMemcpyDeviceToDevice,
+                                 b->stream));
     st = upload_ctl(b, i, 1);
     if (st == LBC_OK) st = rebuild_stage_data(b, i);
     if (st != LBC_OK) return st;
@@ -667,6 +660,7 @@ void lbc_batch_destroy(lbc_batch *b)
     if (b->h_ctl || b->h_last) cudaStreamSynchronize(b->stream);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
     if (b->h_last) cudaFreeHost(b->h_last);
+    if (b->h_bad) cudaFreeHost(b->h_bad);
     delete b;
 }
 

@@ -18,8 +18,8 @@ constexpr int kWarps = 8;          // warps per CTA
 constexpr int kThreads = kWarps * 32;
 constexpr int kSubV = 16;          // velocities per pipeline stage (two per warp)
 constexpr int kPipe = 4;           // pipeline depth (stages in flight)
-constexpr int kEqM = 12;           // per-node stage data: n ux uy T qx qy 1/tau cS 1/(5T) 1/(J deta), 2 pad
-                                   // (48 B per FP32 node: a tile's block is one 16-byte-aligned bulk copy)
+constexpr int kEqM = 16;           // per-node stage data: n ux uy T qx qy 1/tau cS 1/(5T) 1/(J deta)
+                                   // Pxx Pyy Pzz Pxy, 2 pad (64 B per FP32 node: 16-byte-aligned bulk copies)
 constexpr int kMaxVChunk = 256;    // velocities per CTA at most (per-velocity data is staged in smem)
 constexpr int kMaxCluster = 16;    // chunk CTAs of a tile form one thread-block cluster (non-portable size 16)
 constexpr int kMaxV = kMaxCluster * kMaxVChunk;   // largest velocity set 2 Qx Qy
@@ -176,9 +176,10 @@ template <typename R>
 size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster);
 template <typename R>
 size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K);
-// Clusters of `cluster` stage CTAs that can be resident at once (0: not launchable).
+// Clusters of `cluster` stage CTAs that can be resident at once (0: not launchable),
+// for the single-instance (batch = false) or the batch stage kernel.
 template <typename R>
-cudaError_t stage_active_clusters(size_t smem, int cluster, int *nclusters);
+cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, int *nclusters);
 template <typename R>
 cudaError_t configure_kernels();   // per-device kernel attributes; call before capture
 // One RK stage of one instance: grid (ntile, nchunk), cluster dims (1, nchunk, 1);
@@ -194,8 +195,15 @@ template <typename R>
 cudaError_t launch_moments_partial(const DevTables &T, const DevState &S, int buf, cudaStream_t st);
 template <typename R>
 cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int buf, cudaStream_t st);
+// Moments of buffer 0 (FP64, [LBC_NMOM][Nxp] in S.mom_out) from its stage data.
 template <typename R>
-cudaError_t launch_finalize_moments(const DevTables &T, const DevState &S, cudaStream_t st);
+cudaError_t launch_moments_from_stage_data(const DevTables &T, const DevState &S, cudaStream_t st);
+// FP64 [2][V][Nx] weight-divided state in device memory -> deviation rows of buffer `dst`
+// (sets *bad, if not NULL, when a value is not finite); and back.
+template <typename R>
+cudaError_t launch_state_in(const double *src, void *dst, const DevTables &T, int *bad, cudaStream_t st);
+template <typename R>
+cudaError_t launch_state_out(const void *src, double *dst, const DevTables &T, cudaStream_t st);
 cudaError_t launch_ctl_bump(Ctl *ctl, int n, long long k, cudaStream_t st);
 // last[i] = residual of instance i's last step taken (its stop step - 1 if stopped, else base - 1)
 cudaError_t launch_last_residuals(const Inst *insts, int n, double *last, cudaStream_t st);

@@ -23,6 +23,7 @@
 // Maxwellian (n = 1, u = 0, T = 1): WENO-5, the ghost extrapolation and the RK
 // combination are affine-invariant, so they act on d unchanged, and the FP32
 // path keeps ~1e-8 absolute resolution for near-equilibrium flows.
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -249,49 +250,6 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
     return fdiv<R>(a0 * q0 + a1 * q1 + a2 * q2, R(6) * (a0 + a1 + a2));
 }
 
-// Raw sums of the rest Maxwellian about shift (sx, sy), from its power sums P_ab.
-__device__ __forceinline__ void rest_raw(const double *P, double sx, double sy, double *r)
-{
-    const double P00 = P[0], P10 = P[1], P01 = P[2], P20 = P[3], P11 = P[4], P02 = P[5];
-    const double P30 = P[6], P21 = P[7], P12 = P[8], P03 = P[9];
-    r[R_S0] = P00;
-    r[R_SX] = P10 - sx * P00;
-    r[R_SY] = P01 - sy * P00;
-    r[R_SXX] = P20 - 2 * sx * P10 + sx * sx * P00;
-    r[R_SXY] = P11 - sx * P01 - sy * P10 + sx * sy * P00;
-    r[R_SYY] = P02 - 2 * sy * P01 + sy * sy * P00;
-    r[R_CZ] = P00;                       // chi_rest = T_rest phi_rest, T_rest = 1
-    double a3 = P30 - 3 * sx * P20 + 3 * sx * sx * P10 - sx * sx * sx * P00;
-    double ab2 = P12 - 2 * sy * P11 + sy * sy * P10 - sx * P02 + 2 * sx * sy * P01 - sx * sy * sy * P00;
-    double b3 = P03 - 3 * sy * P02 + 3 * sy * sy * P01 - sy * sy * sy * P00;
-    double ba2 = P21 - 2 * sx * P11 + sx * sx * P01 - sy * P20 + 2 * sx * sy * P10 - sy * sx * sx * P00;
-    r[R_R3X] = a3 + ab2;
-    r[R_R3Y] = b3 + ba2;
-    r[R_GX] = P10 - sx * P00;
-    r[R_GY] = P01 - sy * P00;
-}
-
-// n, u_x, u_y, T, P_xx, P_yy, P_zz, P_xy, q_x, q_y from raw sums about (sx, sy).
-__device__ __forceinline__ void raw_to_moments(const double *r, double sx, double sy, double *m)
-{
-    double n = r[R_S0], in = 1.0 / n;
-    double bx = r[R_SX] * in, by = r[R_SY] * in;
-    double pxx = r[R_SXX] - n * bx * bx;
-    double pxy = r[R_SXY] - n * bx * by;
-    double pyy = r[R_SYY] - n * by * by;
-    double pzz = r[R_CZ];
-    double r2 = r[R_SXX] + r[R_SYY], b2 = bx * bx + by * by;
-    double hx = r[R_R3X] - bx * r2 - 2.0 * (bx * r[R_SXX] + by * r[R_SXY]) + 2.0 * n * bx * b2;
-    double hy = r[R_R3Y] - by * r2 - 2.0 * (bx * r[R_SXY] + by * r[R_SYY]) + 2.0 * n * by * b2;
-    m[0] = n;
-    m[1] = sx + bx;
-    m[2] = sy + by;
-    m[3] = (pxx + pyy + pzz) * in * (1.0 / 3.0);
-    m[4] = pxx; m[5] = pyy; m[6] = pzz; m[7] = pxy;
-    m[8] = 0.5 * hx + 0.5 * (r[R_GX] - bx * pzz);
-    m[9] = 0.5 * hy + 0.5 * (r[R_GY] - by * pzz);
-}
-
 // ---- TMA and mbarrier (inline PTX) ----
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -449,6 +407,7 @@ __device__ __forceinline__ void raw_to_moments_r(const R *r, R sx, R sy, R *m)
     m[1] = sx + bx;
     m[2] = sy + by;
     m[3] = (pxx + pyy + pzz) * in * R(1.0 / 3.0);
+    m[4] = pxx; m[5] = pyy; m[6] = pzz; m[7] = r[R_SXY] - n * bx * by;
     m[8] = R(0.5) * hx + R(0.5) * (r[R_GX] - bx * pzz);
     m[9] = R(0.5) * hy + R(0.5) * (r[R_GY] - by * pzz);
 }
@@ -518,7 +477,7 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
                 !(m[3] > R(0)))
                 S.ctl->nonfinite = 1;
         } else {
-            m[0] = R(1); m[1] = m[2] = R(0); m[3] = R(1); m[8] = m[9] = R(0);
+            m[0] = R(1); m[1] = m[2] = R(0); m[3] = R(1); m[4] = m[5] = m[6] = R(1); m[7] = m[8] = m[9] = R(0);
         }
         const R n = m[0], ux = m[1], uy = m[2], Tc = m[3];
         const R nu = n * Tabs<R>::sc(T, SC_NU) * pow(Tc, Tabs<R>::sc(T, SC_EXPO));   // 1/tau, Eq. tau
@@ -527,6 +486,7 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             R *e = eqm + (size_t)s * kEqM;
             e[0] = n; e[1] = ux; e[2] = uy; e[3] = Tc; e[4] = m[8]; e[5] = m[9];
             e[6] = nu; e[7] = cS; e[8] = R(1) / (R(5) * Tc); e[9] = Tabs<R>::ijd(T)[s];
+            e[10] = m[4]; e[11] = m[5]; e[12] = m[6]; e[13] = m[7];
         }
         const R ip0 = Tabs<R>::sc(T, SC_IP0), Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
         R *x = sc + tid * 8;   // sT a a^2/2 u'_y T'-1
@@ -1126,8 +1086,11 @@ stage_kernel(const __grid_constant__ Inst I, int stage, int rel)
 }
 
 // Batch: descriptors in device memory, one cluster per work item (instance, tile).
+// Three CTAs per SM in FP32: the descriptor fields live in registers here (in the
+// single-instance kernel they are constant-bank operands), and measured on GB300
+// the unspilled 3-CTA form is faster than a spilling 4-CTA form.
 template <typename R>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
 stage_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int stage, int rel)
 {
     const int2 wk = work[blockIdx.x];
@@ -1162,60 +1125,79 @@ tile_equilibrium_kernel(const __grid_constant__ DevTables T, const __grid_consta
     node_equilibrium<R>(T, S, buf, blockIdx.x, 0, 1, kTile, kTile, smem_eq);
 }
 
-// Raw moment sums (about p = 0) of the deviation in buffer `buf`, per velocity chunk.
+// Raw moment sums (about p = 0) of the deviation in buffer `buf`, per velocity
+// chunk, in the state precision (compensated sums in FP32).
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 moments_partial_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevState S, int buf)
 {
-    __shared__ double red[kWarps][kNumRaw][kLanes];
+    __shared__ R red[kWarps][kNumRaw][kLanes];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0 = blockIdx.x * kTile, chunk = blockIdx.y, s = c0 + lane;
     const bool active = lane < kTile && s < T.Nx;
     const R *F = static_cast<const R *>(S.F[buf]);
-    double acc[kNumRaw];
-#pragma unroll
-    for (int m = 0; m < kNumRaw; ++m) acc[m] = 0.0;
+    const R *vel = Tabs<R>::vel(T);
+    CSum<R> acc[kNumRaw];
     const int vbeg = chunk * T.vchunk, vend = min(T.V, vbeg + T.vchunk);
     for (int v = vbeg + warp; v < vend && active; v += kWarps) {
-        const double px = T.d_vel[VC_PX * T.V + v], py = T.d_vel[VC_PY * T.V + v], w = T.d_vel[VC_W * T.V + v];
-        const double fw = w * (double)F[2 * ((size_t)v * T.Nxp + s)];
-        const double gw = w * (double)F[2 * ((size_t)v * T.Nxp + s) + 1];
-        const double e2 = px * px + py * py;
-        acc[R_S0] += fw; acc[R_SX] += px * fw; acc[R_SY] += py * fw;
-        acc[R_SXX] += px * px * fw; acc[R_SXY] += px * py * fw; acc[R_SYY] += py * py * fw;
-        acc[R_CZ] += gw; acc[R_R3X] += e2 * px * fw; acc[R_R3Y] += e2 * py * fw;
-        acc[R_GX] += px * gw; acc[R_GY] += py * gw;
+        const R px = vel[VC_PX * T.V + v], py = vel[VC_PY * T.V + v], w = vel[VC_W * T.V + v];
+        const R fw = w * F[2 * ((size_t)v * T.Nxp + s)];
+        const R gw = w * F[2 * ((size_t)v * T.Nxp + s) + 1];
+        const R e2 = px * px + py * py;
+        acc[R_S0].add(fw); acc[R_SX].add(px * fw); acc[R_SY].add(py * fw);
+        acc[R_SXX].add(px * px * fw); acc[R_SXY].add(px * py * fw); acc[R_SYY].add(py * py * fw);
+        acc[R_CZ].add(gw); acc[R_R3X].add(e2 * px * fw); acc[R_R3Y].add(e2 * py * fw);
+        acc[R_GX].add(px * gw); acc[R_GY].add(py * gw);
     }
 #pragma unroll
-    for (int m = 0; m < kNumRaw; ++m) red[warp][m][lane] = acc[m];
+    for (int m = 0; m < kNumRaw; ++m) red[warp][m][lane] = acc[m].value();
     __syncthreads();
     R *part = static_cast<R *>(S.part);
     for (int idx = tid; idx < kLanes * kNumRaw; idx += kThreads) {
         const int c = idx & 31, m = idx >> 5, sn = c0 + c;
-        double t = 0.0;
-        for (int w2 = 0; w2 < kWarps; ++w2) t += red[w2][m][c];
-        if (c < kTile && sn < T.Nx) part[((size_t)chunk * kNumRaw + m) * T.Nxp + sn] = R(t);
+        CSum<R> t;
+        for (int w2 = 0; w2 < kWarps; ++w2) t.add(red[w2][m][c]);
+        if (c < kTile && sn < T.Nx) part[((size_t)chunk * kNumRaw + m) * T.Nxp + sn] = t.value();
     }
 }
 
-// FP64 moments per node from the chunk partials of moments_partial_kernel.
+// Moments of buffer 0 per node, FP64 [LBC_NMOM][Nxp], from its stage data (the
+// stage kernel and the set-up build them for every node of every stage).
 template <typename R>
-__global__ void finalize_moments_kernel(DevTables T, DevState S)
+__global__ void moments_from_stage_data_kernel(const R *eqm, int Nx, int Nxp, double *out)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= T.Nx) return;
-    const R *part = static_cast<const R *>(S.part);
-    const double sx = 0.0, sy = 0.0;
-    double r[kNumRaw];
-    rest_raw(T.restP, sx, sy, r);
-    for (int m = 0; m < kNumRaw; ++m) {
-        double acc = 0.0;
-        for (int ch = 0; ch < T.nchunk; ++ch) acc += (double)part[((size_t)ch * kNumRaw + m) * T.Nxp + s];
-        r[m] += acc;
+    if (s >= Nx) return;
+    const R *e = eqm + (size_t)s * kEqM;
+    const int src[LBC_NMOM] = {0, 1, 2, 3, 10, 11, 12, 13, 4, 5};   // n ux uy T Pxx Pyy Pzz Pxy qx qy
+#pragma unroll
+    for (int k = 0; k < LBC_NMOM; ++k) out[(size_t)k * Nxp + s] = (double)e[src[k]];
+}
+
+// Caller's weight-divided FP64 state [2][V][Nx] (in device memory) <-> deviation
+// rows [V][Nxp][2] in the state precision. state_in sets *bad if a value is not finite.
+template <typename R>
+__global__ void state_in_kernel(const double *src, R *dst, const double *frest, int V, int Nx, int Nxp, int *bad)
+{
+    const size_t n = 2 * (size_t)V * Nx;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i / Nx, v = row % V, fld = row / V;
+        const int s = (int)(i - row * Nx);
+        const double x = src[i];
+        if (bad && !isfinite(x)) *bad = 1;
+        dst[2 * (v * Nxp + s) + fld] = R(x - frest[v]);
     }
-    double mo[10];
-    raw_to_moments(r, sx, sy, mo);
-    for (int k = 0; k < LBC_NMOM; ++k) S.mom_out[(size_t)k * T.Nxp + s] = mo[k];
+}
+
+template <typename R>
+__global__ void state_out_kernel(const R *src, double *dst, const double *frest, int V, int Nx, int Nxp)
+{
+    const size_t n = 2 * (size_t)V * Nx;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i / Nx, v = row % V, fld = row / V;
+        const int s = (int)(i - row * Nx);
+        dst[i] = frest[v] + (double)src[2 * (v * Nxp + s) + fld];
+    }
 }
 
 __global__ void ctl_bump_kernel(Ctl *ctl, int n, long long k)
@@ -1311,7 +1293,7 @@ cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, i
 }
 
 template <typename R>
-cudaError_t stage_active_clusters(size_t smem, int cluster, int *nclusters)
+cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, int *nclusters)
 {
     *nclusters = 0;
     cudaLaunchConfig_t cfg = {};
@@ -1325,7 +1307,8 @@ cudaError_t stage_active_clusters(size_t smem, int cluster, int *nclusters)
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(nclusters, stage_kernel<R>, &cfg);
+    return batch ? cudaOccupancyMaxActiveClusters(nclusters, stage_batch_kernel<R>, &cfg)
+                 : cudaOccupancyMaxActiveClusters(nclusters, stage_kernel<R>, &cfg);
 }
 
 template <typename R>
@@ -1344,9 +1327,26 @@ cudaError_t launch_moments_partial(const DevTables &T, const DevState &S, int bu
 }
 
 template <typename R>
-cudaError_t launch_finalize_moments(const DevTables &T, const DevState &S, cudaStream_t st)
+cudaError_t launch_moments_from_stage_data(const DevTables &T, const DevState &S, cudaStream_t st)
 {
-    finalize_moments_kernel<R><<<(T.Nx + 127) / 128, 128, 0, st>>>(T, S);
+    moments_from_stage_data_kernel<R><<<(T.Nx + 127) / 128, 128, 0, st>>>(static_cast<const R *>(S.eqm[0]), T.Nx,
+                                                                           T.Nxp, S.mom_out);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_state_in(const double *src, void *dst, const DevTables &T, int *bad, cudaStream_t st)
+{
+    const int grid = (int)std::min<size_t>(4096, (2 * (size_t)T.V * T.Nx + 255) / 256);
+    state_in_kernel<R><<<grid, 256, 0, st>>>(src, static_cast<R *>(dst), T.frest, T.V, T.Nx, T.Nxp, bad);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_state_out(const void *src, double *dst, const DevTables &T, cudaStream_t st)
+{
+    const int grid = (int)std::min<size_t>(4096, (2 * (size_t)T.V * T.Nx + 255) / 256);
+    state_out_kernel<R><<<grid, 256, 0, st>>>(static_cast<const R *>(src), dst, T.frest, T.V, T.Nx, T.Nxp);
     return cudaGetLastError();
 }
 
@@ -1369,9 +1369,11 @@ cudaError_t launch_last_residuals(const Inst *insts, int n, double *last, cudaSt
     template cudaError_t launch_stage_batch<R>(const Inst *, const int2 *, int, int, size_t, int, int, cudaStream_t); \
     template cudaError_t launch_tile_equilibrium<R>(const DevTables &, const DevState &, int, cudaStream_t);     \
     template cudaError_t launch_moments_partial<R>(const DevTables &, const DevState &, int, cudaStream_t);      \
-    template cudaError_t launch_finalize_moments<R>(const DevTables &, const DevState &, cudaStream_t);          \
-    template cudaError_t stage_active_clusters<R>(size_t, int, int *);                                          \
-    template size_t equilibrium_smem_bytes<R>(int, int, int, int, int);
+    template cudaError_t stage_active_clusters<R>(size_t, int, bool, int *);                                          \
+    template size_t equilibrium_smem_bytes<R>(int, int, int, int, int);                                         \
+    template cudaError_t launch_moments_from_stage_data<R>(const DevTables &, const DevState &, cudaStream_t);  \
+    template cudaError_t launch_state_in<R>(const double *, void *, const DevTables &, int *, cudaStream_t);     \
+    template cudaError_t launch_state_out<R>(const void *, double *, const DevTables &, cudaStream_t);
 LBC_INSTANTIATE(float)
 LBC_INSTANTIATE(double)
 

@@ -57,29 +57,6 @@ lbc_status scratch_on_current_device(void **out)
     return LBC_OK;
 }
 
-// Caller's weight-divided FP64 state [2][V][Nx] <-> deviation buffer [V][Nxp][2] (state precision).
-template <typename R>
-__global__ void state_in_kernel(const double *src, R *dst, const double *frest, int V, int Nx, int Nxp)
-{
-    const size_t n = 2 * (size_t)V * Nx;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i / Nx, v = row % V, fld = row / V;
-        const int s = (int)(i - row * Nx);
-        dst[2 * (v * Nxp + s) + fld] = R(src[i] - frest[v]);
-    }
-}
-
-template <typename R>
-__global__ void state_out_kernel(const R *src, double *dst, const double *frest, int V, int Nx, int Nxp)
-{
-    const size_t n = 2 * (size_t)V * Nx;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t row = i / Nx, v = row % V, fld = row / V;
-        const int s = (int)(i - row * Nx);
-        dst[i] = frest[v] + (double)src[2 * (v * Nxp + s) + fld];
-    }
-}
-
 struct Carve {
     char *base;
     size_t off = 0;
@@ -143,16 +120,13 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
     NA_TRY(cudaMemcpyAsync(scratch, ps.blob.data(), ps.blob.size(), cudaMemcpyHostToDevice, stream));
     // the array keeps the previous call's contents: clear everything that must start at zero
     NA_TRY(cudaMemsetAsync(static_cast<char *>(scratch) + table_bytes, 0, cv.off - table_bytes, stream));
-    const int grid = std::max(1, std::min(1024, (int)((2 * (size_t)V * Nx + 255) / 256)));
-    state_in_kernel<R><<<grid, 256, 0, stream>>>(d_state, static_cast<R *>(S.F[0]), T.frest, V, Nx, T.Nxp);
-    NA_TRY(cudaGetLastError());
+    NA_TRY(launch_state_in<R>(d_state, S.F[0], T, nullptr, stream));
     NA_TRY(launch_moments_partial<R>(T, S, 0, stream));
     NA_TRY(launch_tile_equilibrium<R>(T, S, 0, stream));
     // the control block starts zeroed (the clear above): step 0, no early stop
     for (long k = 0; k < nsteps; ++k)
         for (int stage = 0; stage < 3; ++stage) NA_TRY(launch_stage<R>(I, smem, stage, (int)k, stream));
-    state_out_kernel<R><<<grid, 256, 0, stream>>>(static_cast<const R *>(S.F[0]), d_state, T.frest, V, Nx, T.Nxp);
-    NA_TRY(cudaGetLastError());
+    NA_TRY(launch_state_out<R>(S.F[0], d_state, T, stream));
     Ctl h_ctl;
     NA_TRY(cudaMemcpyAsync(&h_ctl, S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
     NA_TRY(cudaStreamSynchronize(stream));

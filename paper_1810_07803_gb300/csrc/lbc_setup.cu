@@ -266,11 +266,11 @@ size_t stage_smem(bool fp32, const DevTables &T, int vchunk, int cluster)
                 : stage_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vchunk, cluster);
 }
 
-int active_clusters(bool fp32, size_t smem, int cluster)
+int active_clusters(bool fp32, size_t smem, int cluster, bool batch)
 {
     int ncl = 0;
-    cudaError_t e = fp32 ? stage_active_clusters<float>(smem, cluster, &ncl)
-                         : stage_active_clusters<double>(smem, cluster, &ncl);
+    cudaError_t e = fp32 ? stage_active_clusters<float>(smem, cluster, batch, &ncl)
+                         : stage_active_clusters<double>(smem, cluster, batch, &ncl);
     if (e != cudaSuccess) {
         cudaGetLastError();   // an unschedulable cluster shape is not an error of the solver
         return 0;
@@ -316,7 +316,7 @@ lbc_status choose_launch_shape(bool fp32, DevTables &T)
         if (nch > kMaxCluster) continue;
         const size_t smem = stage_smem(fp32, T, vch, nch);
         if (smem > (size_t)optin) continue;
-        const int ncl = active_clusters(fp32, smem, nch);
+        const int ncl = active_clusters(fp32, smem, nch, false);
         if (ncl <= 0) continue;
         const double waves = std::ceil((double)T.ntile / ncl);
         const double cost = waves * (vch + kCtaOverheadRows);
@@ -354,7 +354,7 @@ lbc_status choose_batch_shape(bool fp32, std::vector<DevTables> &Ts, int cluster
             longest = std::max(longest, vch + kCtaOverheadRows);
         }
         if (!fits || smax > (size_t)optin) continue;
-        const int ncl = active_clusters(fp32, smax, C);
+        const int ncl = active_clusters(fp32, smax, C, true);
         if (ncl <= 0) continue;
         const double cost = rows / ((double)ncl * C) + longest;
         if (cost < best - 1e-9) { best = cost; cluster = C; smem = smax; }

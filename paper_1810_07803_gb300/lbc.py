@@ -116,6 +116,19 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _state_ptr(f, V: int, Nx: int):
+    """(pointer, keep-alive) of a host state [2][V][Nx] float64: a numpy array or a
+    contiguous CPU torch tensor (pinned memory makes the upload a direct copy)."""
+    n = 2 * V * Nx
+    if hasattr(f, "data_ptr") and hasattr(f, "is_cuda"):
+        import torch
+        if f.is_cuda or f.dtype != torch.float64 or not f.is_contiguous() or f.numel() != n:
+            raise ValueError("state tensor must be a contiguous float64 CPU tensor of 2*V*Nx values")
+        return C.cast(C.c_void_p(f.data_ptr()), C.POINTER(C.c_double)), f
+    a = np.ascontiguousarray(f, dtype=np.float64).reshape(2, V, Nx)
+    return _dptr(a), a
+
+
 def quadrature(Q: int, half_range: bool):
     z = np.zeros(Q)
     w = np.zeros(Q)
@@ -200,14 +213,17 @@ class Solver:
         self.x = x
         return out
 
-    def get_state(self) -> np.ndarray:
-        f = np.zeros((2, self.V, self.Nx))
-        _check(lib().lbc_get_state(self._h, _dptr(f)))
-        return f
+    def get_state(self, out=None):
+        """The state [2][V][Nx] float64, into `out` (numpy array or CPU tensor) if given."""
+        if out is None:
+            out = np.zeros((2, self.V, self.Nx))
+        ptr, keep = _state_ptr(out, self.V, self.Nx)
+        _check(lib().lbc_get_state(self._h, ptr))
+        return out
 
-    def set_state(self, f: np.ndarray):
-        f = np.ascontiguousarray(f, dtype=np.float64).reshape(2, self.V, self.Nx)
-        _check(lib().lbc_set_state(self._h, _dptr(f)))
+    def set_state(self, f):
+        ptr, keep = _state_ptr(f, self.V, self.Nx)
+        _check(lib().lbc_set_state(self._h, ptr))
 
 
 class Batch:
@@ -288,11 +304,14 @@ class Batch:
         _check(lib().lbc_batch_moments(self._h, i, _dptr(out), _dptr(x)))
         return out
 
-    def get_state(self, i: int) -> np.ndarray:
-        f = np.zeros((2, self.V[i], self.Nx[i]))
-        _check(lib().lbc_batch_get_state(self._h, i, _dptr(f)))
-        return f
+    def get_state(self, i: int, out=None):
+        """Instance i's state [2][V][Nx] float64, into `out` (numpy array or CPU tensor) if given."""
+        if out is None:
+            out = np.zeros((2, self.V[i], self.Nx[i]))
+        ptr, keep = _state_ptr(out, self.V[i], self.Nx[i])
+        _check(lib().lbc_batch_get_state(self._h, i, ptr))
+        return out
 
-    def set_state(self, i: int, f: np.ndarray):
-        f = np.ascontiguousarray(f, dtype=np.float64).reshape(2, self.V[i], self.Nx[i])
-        _check(lib().lbc_batch_set_state(self._h, i, _dptr(f)))
+    def set_state(self, i: int, f):
+        ptr, keep = _state_ptr(f, self.V[i], self.Nx[i])
+        _check(lib().lbc_batch_set_state(self._h, i, ptr))
