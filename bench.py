@@ -182,6 +182,23 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(values, device):
+    """Element-wise max of per-rank timings (ms) over the process group, or the
+    values themselves on a single rank: the job is as slow as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_value(units_per_rank, world, ms_per_step):
+    """Whole-job throughput: every rank's units over the slowest rank's step time."""
+    return units_per_rank * world / (ms_per_step / 1e3)
+
+
 def time_steps(solvers, steps, warmup, flush):
     """ms per step of single solvers stepped one after the other (L2 flushed between steps)."""
     import torch
@@ -250,12 +267,9 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         ms, launch_ms = time_batch(batch, args.steps, args.warmup, flush)
-    if world > 1:
-        t = torch.tensor([ms, launch_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, launch_ms = (float(v) for v in t.tolist())
+    ms, launch_ms = max_over_ranks([ms, launch_ms], "cuda")
     units = nsol * V * Nx
-    value = units * world / (ms / 1e3)
+    value = whole_job_value(units, world, ms)
 
     # end to end through the public API: host states in (pinned), host moments out, every step
     host_states = []
@@ -273,7 +287,7 @@ def main():
         for i in range(nsol):
             batch.moments(i)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks([(time.perf_counter() - t0) / e2e_steps], "cuda")[0]
     h2d = sum(hs.numel() * hs.element_size() for hs in host_states)
     d2h = nsol * lbc.NMOM * Nx * 8
 
