@@ -72,9 +72,16 @@ typedef struct {
     double u_left, u_right;  /* wall velocities along y (v_ref units) */
     double T_left, T_right;  /* wall temperatures (T_ref units), > 0 */
     double Pr;               /* Prandtl number of the Shakhov model (Sec. II) */
-    lbc_mu_law mu_law;       /* LBC_MU_POWER: mu = T^omega (Eq. mu) */
-    double omega;            /* viscosity index */
-    const double *tab_T, *tab_mu, *tab_Pr;  /* LBC_MU_TABLE (Eqs. mun, interp); tab_n entries */
+    lbc_mu_law mu_law;       /* LBC_MU_POWER: mu = T^omega (Eq. mu), Pr constant;
+                                LBC_MU_TABLE: Eqs. mun, interp (below) */
+    double omega;            /* viscosity index of the power law */
+    /* LBC_MU_TABLE: tab_n in [2, 256] entries (copied at creation) of temperatures
+     * tab_T (T_ref units, > 0, strictly increasing), viscosities tab_mu (> 0, any
+     * unit) and Prandtl numbers tab_Pr (> 0). On [T_n, T_{n+1}) mu is the power
+     * law through both points, the first and last intervals extend below T_2 and
+     * above T_{N-1}; Pr = Pr_1 below T_2, Pr_n on [T_n, T_{n+1}), Pr_N from T_N on.
+     * delta refers to mu(T_ref = 1) of this law: 1/tau = n T delta sqrt(2) / (mu(T)/mu(1)). */
+    const double *tab_T, *tab_mu, *tab_Pr;
     int tab_n;
     int Nx;                  /* grid nodes across the full channel, >= 8 */
     double stretch_A;        /* Eq. stretch parameter A in [0, 1); 0 = uniform grid */
@@ -95,8 +102,8 @@ typedef struct {
  *           temperature), Nx >= 8, delta >= 0, T_w > 0, 0 <= stretch_A < 1,
  *           p0 > 0; the largest orders must also fit one CTA's shared memory.
  *   Automatic time step: dt = min(cfl * min_s(J_s deta) / max|p_x|, tau_min / 2),
- *   with tau_min the smallest relaxation time (Eq. tau) of the initial state
- *   and of the two walls at n = 1.
+ *   with tau_min the smallest relaxation time (Eq. tau, with the problem's
+ *   viscosity law) of the initial state and of the two walls at n = 1.
  *   cuda_stream: a cudaStream_t (NULL = the legacy default stream).
  *   out: receives the handle; unchanged on failure.
  * Errors: LBC_EINVAL, LBC_ENOMEM, LBC_ECUDA.

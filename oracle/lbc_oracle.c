@@ -40,6 +40,8 @@
 typedef struct {
     int Nx, Qx, Qy, Nxe, Nye;       /* grid size, quadrature orders, expansion orders */
     double p0, delta, Pr, omega;
+    int law, tab_n;                 /* law 0: mu = T^omega, Pr; law 1: the table of Eqs. mun, interp */
+    const double *tab_T, *tab_mu, *tab_Pr;   /* [tab_n] temperatures (increasing), viscosities, Prandtl */
     double uL, uR, TL, TR;          /* wall velocities (along y) and temperatures */
     double dt, deta, eps;           /* time step, eta spacing, WENO epsilon */
     const double *J;                /* [Nx] dx/deta at the nodes */
@@ -194,13 +196,48 @@ void orc_equilibrium_factors(const orc_problem *P, double ux, double uy, double 
 /* ---- relaxation target (phi_eq (1 + S_phi), chi_eq (1 + S_chi)) -------- */
 /* Sec. II: phi_eq = n g_x g_y, chi_eq = T phi_eq,
  * S_phi = (1-Pr)/(n T^2) ((xi_x^2+xi_y^2)/(5T) - 4/5)(q . xi), S_chi with 2/5. */
+/* ---- viscosity and Prandtl number --------------------------------------- */
+/* Number of table temperatures T_n <= T (0 .. tab_n). */
+static int table_index(const orc_problem *P, double T)
+{
+    int k = 0;
+    while (k < P->tab_n && P->tab_T[k] <= T) ++k;
+    return k;
+}
+
+/* Eq. mun on the segment of Eq. interp that holds T (0-based segment c covers
+ * [T_c, T_{c+1}); the first and last segments extend to T -> 0 and T -> inf). */
+double orc_table_mu(const orc_problem *P, double T)
+{
+    int c = table_index(P, T) - 1;
+    if (c < 0) c = 0;
+    if (c > P->tab_n - 2) c = P->tab_n - 2;
+    double w = log(P->tab_mu[c + 1] / P->tab_mu[c]) / log(P->tab_T[c + 1] / P->tab_T[c]);
+    return P->tab_mu[c] * pow(T / P->tab_T[c], w);
+}
+
+/* mu(T) / mu(T_ref = 1): delta is defined with mu(T_ref). */
+double orc_mu_ratio(const orc_problem *P, double T)
+{
+    if (P->law == 0) return pow(T, P->omega);
+    return orc_table_mu(P, T) / orc_table_mu(P, 1.0);
+}
+
+/* Eq. interp for Pr: Pr_1 below T_2, Pr_n on [T_n, T_{n+1}), Pr_N from T_N on. */
+double orc_prandtl(const orc_problem *P, double T)
+{
+    if (P->law == 0) return P->Pr;
+    int k = table_index(P, T);
+    return P->tab_Pr[k < 1 ? 0 : k - 1];
+}
+
 void orc_target(const orc_problem *P, const double *m, double *tphi, double *tchi)
 {
     int V = nvel(P), Qy = P->Qy;
     double *gx = malloc(sizeof(double) * 2 * P->Qx), *gy = malloc(sizeof(double) * Qy);
     double n = m[M_N], ux = m[M_UX], uy = m[M_UY], T = m[M_T];
     orc_equilibrium_factors(P, ux, uy, T, gx, gy);
-    double c = (1.0 - P->Pr) / (n * T * T);
+    double c = (1.0 - orc_prandtl(P, T)) / (n * T * T);
     for (int v = 0; v < V; ++v) {
         double feq = n * gx[v / Qy] * gy[v % Qy];
         double xx = px_of(P, v) - ux, xy = py_of(P, v) - uy;
@@ -212,10 +249,11 @@ void orc_target(const orc_problem *P, const double *m, double *tphi, double *tch
     free(gx); free(gy);
 }
 
-/* Eq. tau with mu = T^omega, T_ref = n_ref = 1: 1/tau = n T^{1-omega} delta sqrt(2). */
+/* Eq. tau with T_ref = n_ref = 1: 1/tau = n T delta sqrt(2) / (mu(T)/mu(T_ref));
+ * for mu = T^omega (Eq. mu) that is n T^{1-omega} delta sqrt(2). */
 static double collision_rate(const orc_problem *P, double n, double T)
 {
-    return n * pow(T, 1.0 - P->omega) * P->delta * sqrt(2.0);
+    return n * T / orc_mu_ratio(P, T) * P->delta * sqrt(2.0);
 }
 
 /* ---- WENO-5 (Jiang & Shu) face value, upwind cell is c ------------------ */

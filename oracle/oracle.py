@@ -44,6 +44,8 @@ class _Problem(C.Structure):
     _fields_ = [
         ("Nx", C.c_int), ("Qx", C.c_int), ("Qy", C.c_int), ("Nxe", C.c_int), ("Nye", C.c_int),
         ("p0", C.c_double), ("delta", C.c_double), ("Pr", C.c_double), ("omega", C.c_double),
+        ("law", C.c_int), ("tab_n", C.c_int), ("tab_T", C.c_void_p), ("tab_mu", C.c_void_p),
+        ("tab_Pr", C.c_void_p),
         ("uL", C.c_double), ("uR", C.c_double), ("TL", C.c_double), ("TR", C.c_double),
         ("dt", C.c_double), ("deta", C.c_double), ("eps", C.c_double),
         ("J", C.c_void_p), ("zx", C.c_void_p), ("wx", C.c_void_p), ("yy", C.c_void_p),
@@ -70,6 +72,12 @@ def lib():
         L.orc_target.argtypes = [C.c_void_p, dp, dp, dp]
         L.orc_rest_state.argtypes = [C.c_void_p, dp]
         L.orc_gx_bracket.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp, C.c_void_p]
+        L.orc_mu_ratio.restype = C.c_double
+        L.orc_mu_ratio.argtypes = [C.c_void_p, C.c_double]
+        L.orc_prandtl.restype = C.c_double
+        L.orc_prandtl.argtypes = [C.c_void_p, C.c_double]
+        L.orc_table_mu.restype = C.c_double
+        L.orc_table_mu.argtypes = [C.c_void_p, C.c_double]
         L.orc_weno5.restype = C.c_double
         L.orc_weno5.argtypes = [C.c_double] * 6
         L.orc_ssprk3.argtypes = [C.c_long, dp, C.c_double, RHS_FN, C.c_void_p]
@@ -99,18 +107,20 @@ def grid(Nx: int, A: float):
     return np.tanh(eta) / (2.0 * A), 1.0 / (np.cosh(eta) ** 2 * 2.0 * A), deta
 
 
-def time_step(p: dict, J: np.ndarray, deta: float, zmax: float) -> float:
+def time_step(p: dict, J: np.ndarray, deta: float, zmax: float, mu_ratio=None) -> float:
     """dt = min(cfl min_s(J_s deta) / max|p_x|, tau_min / 2) (reading; the paper is silent).
 
-    tau_min is the smallest relaxation time of Eq. tau over the initial state
-    (n = 1, T = 1) and the two walls (n = 1, T = T_w).
+    tau_min is the smallest relaxation time of Eq. tau, tau = (mu(T)/mu(T_ref)) / (n T delta
+    sqrt(2)), over the initial state (n = 1, T = 1) and the two walls (n = 1, T = T_w);
+    mu_ratio(T) = mu(T)/mu(T_ref), T^omega by default (Eq. mu).
     """
     if p["dt"] > 0:
         return float(p["dt"])
     dt = p["cfl"] * float(np.min(J)) * deta / (p["p0"] * zmax)
+    if mu_ratio is None:
+        mu_ratio = lambda T: T ** p["omega"]   # noqa: E731
     if p["delta"] > 0:
-        taus = [T ** (p["omega"] - 1.0) / (p["delta"] * np.sqrt(2.0))
-                for T in (1.0, p["T_left"], p["T_right"])]
+        taus = [mu_ratio(T) / (T * p["delta"] * np.sqrt(2.0)) for T in (1.0, p["T_left"], p["T_right"])]
         dt = min(dt, 0.5 * min(taus))
     return dt
 
@@ -131,19 +141,32 @@ class Oracle:
         self.V = 2 * Qx * Qy
         self.x, J, self.deta = grid(self.Nx, float(p["stretch_A"]))
         self.J = np.ascontiguousarray(J)
-        self.dt = time_step(p, self.J, self.deta, float(self.tab["zx"].max()))
         pr = _Problem()
         pr.Nx, pr.Qx, pr.Qy, pr.Nxe, pr.Nye = self.Nx, Qx, Qy, self.Nxe, self.Nye
         pr.p0, pr.delta, pr.Pr, pr.omega = p["p0"], p["delta"], p["Pr"], p["omega"]
+        # viscosity law: Eq. mu (power law), or the table of Eqs. mun, interp
+        if p.get("mu_law", "power") == "table":
+            self._table = [np.ascontiguousarray(p[k], dtype=np.float64) for k in ("tab_T", "tab_mu", "tab_Pr")]
+            pr.law, pr.tab_n = 1, len(self._table[0])
+            pr.tab_T, pr.tab_mu, pr.tab_Pr = (a.ctypes.data for a in self._table)
+        self._pr = pr
+        self.dt = time_step(p, self.J, self.deta, float(self.tab["zx"].max()), self.mu_ratio)
         pr.uL, pr.uR, pr.TL, pr.TR = p["u_left"], p["u_right"], p["T_left"], p["T_right"]
         pr.dt, pr.deta, pr.eps = self.dt, self.deta, WENO_EPS
         pr.J = self.J.ctypes.data
         for k in ("zx", "wx", "yy", "wy", "Phi", "Phi_lo", "He", "He_lo"):
             setattr(pr, k, self.tab[k].ctypes.data)
-        self._pr = pr
         self.f = np.zeros((2, self.V, self.Nx))
         lib().orc_rest_state(C.byref(pr), _ptr(self.f))
         self.steps = 0
+
+    def mu_ratio(self, T: float) -> float:
+        """mu(T)/mu(T_ref) of the problem's viscosity law."""
+        return lib().orc_mu_ratio(C.byref(self._pr), float(T))
+
+    def prandtl(self, T: float) -> float:
+        """Pr(T) of the problem's law (constant for the power law)."""
+        return lib().orc_prandtl(C.byref(self._pr), float(T))
 
     # velocity set -----------------------------------------------------------
     @property

@@ -23,6 +23,7 @@ constexpr int kEqM = 16;           // per-node stage data: n ux uy T qx qy 1/tau
 constexpr int kMaxVChunk = 256;    // velocities per CTA at most (per-velocity data is staged in smem)
 constexpr int kMaxCluster = 16;    // chunk CTAs of a tile form one thread-block cluster (non-portable size 16)
 constexpr int kMaxV = kMaxCluster * kMaxVChunk;   // largest velocity set 2 Qx Qy
+constexpr int kMaxTable = 256;     // entries of a viscosity table
 
 // Scalars derived from the parameters, in both precisions (no FP64 arithmetic in the FP32 kernels).
 enum { SC_NU = 0,      // delta sqrt(2): 1/tau = SC_NU n T^(1 - omega)   (Eq. tau)
@@ -40,6 +41,7 @@ enum { SC_NU = 0,      // delta sqrt(2): 1/tau = SC_NU n T^(1 - omega)   (Eq. ta
 struct DevTables {
     int Nx, Nxp, Qx, Qy, Nxe, Nye, K, V;
     int ntile, nchunk, vchunk;
+    int law, tab_n;                // viscosity law (LBC_MU_POWER / LBC_MU_TABLE), table entries
     double p0, dt, delta, Pr, omega, TL, TR;
     double inL, inR;               // sum_{incoming} p_x w_v fw_v (signed) for a unit wall density
     double restOutL, restOutR;     // sum_{outgoing} p_x w_v ft_rest_v at each wall
@@ -78,10 +80,12 @@ enum { VR_PX = 0, VR_PY, VR_W, VR_FR, VR_FWL, VR_FWLT, VR_FWR, VR_FWRT, VR_GA, V
 
 // Tables of the equilibrium construction, one contiguous block per precision,
 // each piece padded to 4 elements (16-byte pieces in FP32): recurrence of h_l,
-// 1/l, projection rule, h_l(z_i) [N+1][Qx] and He_l(y_j) [Ny+1][Qy].
+// 1/l, projection rule, h_l(z_i) [N+1][Qx] and He_l(y_j) [Ny+1][Qy]; and, for
+// the table viscosity law (Eqs. mun, interp), ntab temperatures T_n, viscosities
+// mu_n / mu(T_ref), segment exponents omega_n and Prandtl numbers Pr_n.
 struct EqTab {
-    int alpha, sbeta, isbeta, invl, Yk, Wk, hz, He, len;
-    __host__ __device__ EqTab(int N, int Ny, int K, int Qx, int Qy)
+    int alpha, sbeta, isbeta, invl, Yk, Wk, hz, He, lawT, lawMu, lawW, lawPr, len;
+    __host__ __device__ EqTab(int N, int Ny, int K, int Qx, int Qy, int ntab)
     {
         alpha = 0;
         sbeta = alpha + r4(N + 2);
@@ -91,7 +95,11 @@ struct EqTab {
         Wk = Yk + r4(K);
         hz = Wk + r4(K);
         He = hz + r4((N + 1) * Qx);
-        len = He + r4((Ny + 1) * Qy);
+        lawT = He + r4((Ny + 1) * Qy);
+        lawMu = lawT + r4(ntab);
+        lawW = lawMu + r4(ntab);
+        lawPr = lawW + r4(ntab);
+        len = lawPr + r4(ntab);
     }
     __host__ __device__ static int r4(int x) { return (x + 3) / 4 * 4; }
 };
@@ -144,6 +152,7 @@ struct ProblemSetup {
     std::vector<double> x, inv_jdeta;
     double deta = 0, min_jdeta = 0, dt = 0;
     std::vector<double> fwL, fwR, frest, vel, isb, invl, vrow, eqtab;
+    std::vector<double> tabT, tabMu, tabW, tabPr;   // table viscosity law: mu_n / mu(T_ref), exponents
     std::vector<int> aj;
     double inL = 0, inR = 0, restOutL = 0, restOutR = 0, restP[10] = {0};
     std::vector<unsigned char> blob;   // device table block contents
@@ -173,9 +182,9 @@ lbc_status validate(const lbc_params &p, int &Nxe, int &Nye);
 lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_nodes);
 
 template <typename R>
-size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster);
+size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster, int ntab);
 template <typename R>
-size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K);
+size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int ntab);
 // Clusters of `cluster` stage CTAs that can be resident at once (0: not launchable),
 // for the single-instance (batch = false) or the batch stage kernel.
 template <typename R>

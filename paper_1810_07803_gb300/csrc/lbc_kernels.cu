@@ -348,12 +348,12 @@ template <typename R>
 struct EqScratch {
     size_t red, tab, raw, shf, sc, rpm, bb, cb, H, total;
     int cstride;
-    __host__ __device__ EqScratch(int K, int N, int Ny, int Qx, int Qy, int ncap = kTile)
+    __host__ __device__ EqScratch(int K, int N, int Ny, int Qx, int Qy, int ntab, int ncap = kTile)
     {
         cstride = 2 * (N + 1) + 1;   // odd stride: conflict-free rows per node
         red = (size_t)kWarps * kNumRaw * kLanes * sizeof(R);
         tab = al16(red);
-        raw = al16(tab + (size_t)EqTab(N, Ny, K, Qx, Qy).len * sizeof(R));
+        raw = al16(tab + (size_t)EqTab(N, Ny, K, Qx, Qy, ntab).len * sizeof(R));
         shf = al16(raw + (size_t)ncap * kNumRaw * sizeof(R));
         sc = al16(shf + (size_t)2 * kLanes * sizeof(R));
         rpm = al16(sc + (size_t)ncap * 8 * sizeof(R));
@@ -446,8 +446,8 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
 {
     const int tid = threadIdx.x, c0 = tile * kTile;
     const int N = T.Nxe, K = T.K, G = 2 * T.Qx + T.Qy, Ny = T.Nye;
-    const EqScratch<R> L(K, N, Ny, T.Qx, T.Qy, ncap);
-    const EqTab E(N, Ny, K, T.Qx, T.Qy);
+    const EqScratch<R> L(K, N, Ny, T.Qx, T.Qy, T.tab_n, ncap);
+    const EqTab E(N, Ny, K, T.Qx, T.Qy, T.tab_n);
     const R *tab = reinterpret_cast<const R *>(scratch + L.tab);
     const R *raw = reinterpret_cast<const R *>(scratch + L.raw);   // [nn][kNumRaw]
     const R *shf = reinterpret_cast<const R *>(scratch + L.shf);   // [2][kLanes]
@@ -480,8 +480,25 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             m[0] = R(1); m[1] = m[2] = R(0); m[3] = R(1); m[4] = m[5] = m[6] = R(1); m[7] = m[8] = m[9] = R(0);
         }
         const R n = m[0], ux = m[1], uy = m[2], Tc = m[3];
-        const R nu = n * Tabs<R>::sc(T, SC_NU) * pow(Tc, Tabs<R>::sc(T, SC_EXPO));   // 1/tau, Eq. tau
-        const R cS = Tabs<R>::sc(T, SC_1MPR) / (n * Tc * Tc);                        // Shakhov prefactor
+        R nu, cS;   // 1/tau (Eq. tau) and the Shakhov prefactor (1 - Pr)/(n T^2)
+        if (T.law == LBC_MU_TABLE) {
+            // Eqs. mun, interp: k = number of table temperatures <= T; viscosity on segment
+            // clamp(k - 1, 0, ntab - 2) (end segments extrapolate), Pr_{max(k - 1, 0)}
+            const R *lT = tab + E.lawT;
+            int lo = 0, hi = T.tab_n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (lT[mid] <= Tc) lo = mid + 1;
+                else hi = mid;
+            }
+            const int c = min(max(lo - 1, 0), T.tab_n - 2);
+            const R mu = tab[E.lawMu + c] * pow(Tc / lT[c], tab[E.lawW + c]);   // mu(T) / mu(T_ref)
+            nu = n * Tc / mu * Tabs<R>::sc(T, SC_NU);
+            cS = (R(1) - tab[E.lawPr + max(lo - 1, 0)]) / (n * Tc * Tc);
+        } else {
+            nu = n * Tabs<R>::sc(T, SC_NU) * pow(Tc, Tabs<R>::sc(T, SC_EXPO));   // mu = T^omega (Eq. mu)
+            cS = Tabs<R>::sc(T, SC_1MPR) / (n * Tc * Tc);
+        }
         if (live) {
             R *e = eqm + (size_t)s * kEqM;
             e[0] = n; e[1] = ux; e[2] = uy; e[3] = Tc; e[4] = m[8]; e[5] = m[9];
@@ -635,7 +652,7 @@ __device__ void block_wall_density(const DevTables &T, const R *phi, bool right,
 template <typename R>
 struct Layout {
     size_t bar, pipe, fin, f0, g, eqm, vrow, xch, misc, total;
-    __host__ __device__ Layout(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster)
+    __host__ __device__ Layout(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster, int ntab)
     {
         size_t o = 0;
         bar = o;  o = al(o + (kPipe + 2) * sizeof(uint64_t) + (kPipe + 1) * sizeof(uint32_t));
@@ -643,7 +660,7 @@ struct Layout {
         fin = o;
         f0 = fin + (size_t)kPipe * 2 * kSubV * kRowLen * sizeof(R);
         size_t m = f0 + (size_t)kPipe * 2 * kSubV * kF0Len * sizeof(R) - pipe;
-        const size_t eq_bytes = EqScratch<R>(K, N, Ny, Qx, Qy, node_cap(cluster)).total;
+        const size_t eq_bytes = EqScratch<R>(K, N, Ny, Qx, Qy, ntab, node_cap(cluster)).total;
         m = m > eq_bytes ? m : eq_bytes;
         o = al(o + m);
         g = o;    o = al(o + (size_t)(2 * Qx + Qy) * kLanes * sizeof(R));
@@ -669,7 +686,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     const StateMaps &M = I.M;
     // TMA destinations want 128-byte aligned shared memory: align the base explicitly
     unsigned char *smem = smem_dyn + ((128 - (smem_addr(smem_dyn) & 127)) & 127);
-    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk, T.nchunk);
+    const Layout<R> L(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.vchunk, T.nchunk, T.tab_n);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);   // [kPipe] rows, data, tables
     uint64_t *bar_data = bar + kPipe, *bar_tab = bar + kPipe + 1;
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(bar + kPipe + 2);   // [kPipe] warps done with a slot
@@ -719,8 +736,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     const int x0 = ((c0 - 3) >> 2) << 2, off = c0 - 3 - x0;     // node s <-> column s - x0
     const int xf = (c0 >> 2) << 2, offf = c0 - xf;
     const int ncap = Layout<R>::node_cap(T.nchunk);
-    const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, ncap);
-    const uint32_t tab_bytes = (uint32_t)(EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy).len * sizeof(R));
+    const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, T.tab_n, ncap);
+    const uint32_t tab_bytes = (uint32_t)(EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy, T.tab_n).len * sizeof(R));
 
     // rows v0 .. v0 + kSubV - 1 of the stage input (nodes x0 .. x0 + kRowLen - 1) and of the
     // RK base (nodes xf ..), both fields; rows past V read as zeros
@@ -1105,13 +1122,13 @@ __global__ void __launch_bounds__(kThreads)
 tile_equilibrium_kernel(const __grid_constant__ DevTables T, const __grid_constant__ DevState S, int buf)
 {
     extern __shared__ __align__(16) unsigned char smem_eq[];
-    const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy);
+    const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, T.tab_n);
     R *tab = reinterpret_cast<R *>(smem_eq + E.tab);
     R *raw = reinterpret_cast<R *>(smem_eq + E.raw);
     R *shf = reinterpret_cast<R *>(smem_eq + E.shf);
     const R *part = static_cast<const R *>(S.part);
     const int c0 = blockIdx.x * kTile;
-    const int tlen = EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy).len;
+    const int tlen = EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy, T.tab_n).len;
     for (int k = threadIdx.x; k < tlen; k += kThreads) tab[k] = Tabs<R>::eqtab(T)[k];
     for (int idx = threadIdx.x; idx < kTile * kNumRaw; idx += kThreads) {
         const int c = idx / kNumRaw, m = idx - c * kNumRaw, s = c0 + c;
@@ -1217,9 +1234,9 @@ __global__ void last_residuals_kernel(const Inst *insts, int n, double *last)
 }  // namespace
 
 template <typename R>
-size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster)
+size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster, int ntab)
 {
-    return Layout<R>(Qx, Qy, N, Ny, K, vchunk, cluster).total;
+    return Layout<R>(Qx, Qy, N, Ny, K, vchunk, cluster, ntab).total;
 }
 
 template <typename R>
@@ -1240,9 +1257,9 @@ cudaError_t configure_kernels()
 }
 
 template <typename R>
-size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K)
+size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int ntab)
 {
-    return EqScratch<R>(K, N, Ny, Qx, Qy).total;
+    return EqScratch<R>(K, N, Ny, Qx, Qy, ntab).total;
 }
 
 namespace {
@@ -1314,7 +1331,7 @@ cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, int *ncl
 template <typename R>
 cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int buf, cudaStream_t st)
 {
-    tile_equilibrium_kernel<R><<<T.ntile, kThreads, EqScratch<R>(T.K, T.Nxe, T.Nye, T.Qx, T.Qy).total, st>>>(T, S, buf);
+    tile_equilibrium_kernel<R><<<T.ntile, kThreads, EqScratch<R>(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, T.tab_n).total, st>>>(T, S, buf);
     return cudaGetLastError();
 }
 
@@ -1363,14 +1380,14 @@ cudaError_t launch_last_residuals(const Inst *insts, int n, double *last, cudaSt
 }
 
 #define LBC_INSTANTIATE(R)                                                                                      \
-    template size_t stage_smem_bytes<R>(int, int, int, int, int, int, int);                                     \
+    template size_t stage_smem_bytes<R>(int, int, int, int, int, int, int, int);                                     \
     template cudaError_t configure_kernels<R>();                                                                \
     template cudaError_t launch_stage<R>(const Inst &, size_t, int, int, cudaStream_t);                          \
     template cudaError_t launch_stage_batch<R>(const Inst *, const int2 *, int, int, size_t, int, int, cudaStream_t); \
     template cudaError_t launch_tile_equilibrium<R>(const DevTables &, const DevState &, int, cudaStream_t);     \
     template cudaError_t launch_moments_partial<R>(const DevTables &, const DevState &, int, cudaStream_t);      \
     template cudaError_t stage_active_clusters<R>(size_t, int, bool, int *);                                          \
-    template size_t equilibrium_smem_bytes<R>(int, int, int, int, int);                                         \
+    template size_t equilibrium_smem_bytes<R>(int, int, int, int, int, int);                                         \
     template cudaError_t launch_moments_from_stage_data<R>(const DevTables &, const DevState &, cudaStream_t);  \
     template cudaError_t launch_state_in<R>(const double *, void *, const DevTables &, int *, cudaStream_t);     \
     template cudaError_t launch_state_out<R>(const void *, double *, const DevTables &, cudaStream_t);

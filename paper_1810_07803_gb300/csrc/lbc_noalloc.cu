@@ -148,13 +148,9 @@ extern "C" lbc_status lbc_step_noalloc(const lbc_params *params, double *d_state
     lbc_params p = *params;
     if (p.p0 == 0.0) p.p0 = 1.0;
     if (p.cfl == 0.0) p.cfl = 0.5;
-    if (p.Qx < 1 || p.Qx > kMaxQ || p.Qy < 1 || p.Qy > kMaxQ) return fail_na(LBC_EINVAL, "Qx and Qy must be in [1, 64]");
-    const int Nxe = p.Nexp_x ? p.Nexp_x : p.Qx - 1, Nye = p.Nexp_y ? p.Nexp_y : p.Qy - 1;
-    if (Nxe < 2 || Nxe >= p.Qx || Nye < 2 || Nye >= p.Qy) return fail_na(LBC_EINVAL, "expansion orders must satisfy 2 <= N < Q");
-    if (p.Nx < 8 || p.Nx > (1 << 24)) return fail_na(LBC_EINVAL, "Nx must be in [8, 2^24]");
-    if (!(p.delta >= 0.0) || !(p.T_left > 0.0) || !(p.T_right > 0.0) || !(p.stretch_A >= 0.0 && p.stretch_A < 1.0) ||
-        !(p.p0 > 0.0) || p.cfl < 0.0 || p.dt < 0.0 || !(p.Pr > 0.0) || p.mu_law != LBC_MU_POWER)
-        return fail_na(LBC_EINVAL, "invalid physical parameters");
+    int Nxe = 0, Nye = 0;
+    lbc_status st = validate(p, Nxe, Nye);
+    if (st != LBC_OK) return st;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     return p.precision == LBC_FP32_STATE ? run_noalloc<float>(p, Nxe, Nye, d_state, nsteps, stream)
                                          : run_noalloc<double>(p, Nxe, Nye, d_state, nsteps, stream);

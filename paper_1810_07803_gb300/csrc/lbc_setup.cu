@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -39,7 +40,20 @@ lbc_status validate(const lbc_params &p, int &Nxe, int &Nye)
     if (p.p0 < 0.0 || !std::isfinite(p.p0)) return fail(LBC_EINVAL, "p0 must be > 0 (0 selects 1)");
     if (p.cfl < 0.0 || p.dt < 0.0) return fail(LBC_EINVAL, "cfl and dt must be >= 0");
     if (!std::isfinite(p.Pr) || p.Pr <= 0.0) return fail(LBC_EINVAL, "Pr must be > 0");
-    if (p.mu_law != LBC_MU_POWER) return fail(LBC_EINVAL, "only the power-law viscosity (LBC_MU_POWER) is built");
+    if (p.mu_law == LBC_MU_TABLE) {
+        if (p.tab_n < 2 || p.tab_n > kMaxTable || !p.tab_T || !p.tab_mu || !p.tab_Pr)
+            return fail(LBC_EINVAL, "a viscosity table needs 2 to 256 entries of T, mu and Pr");
+        for (int k = 0; k < p.tab_n; ++k) {
+            if (!(p.tab_T[k] > 0.0) || !std::isfinite(p.tab_T[k]) || (k > 0 && !(p.tab_T[k] > p.tab_T[k - 1])))
+                return fail(LBC_EINVAL, "table temperatures must be finite, > 0 and strictly increasing");
+            if (!(p.tab_mu[k] > 0.0) || !std::isfinite(p.tab_mu[k]))
+                return fail(LBC_EINVAL, "table viscosities must be finite and > 0");
+            if (!(p.tab_Pr[k] > 0.0) || !std::isfinite(p.tab_Pr[k]))
+                return fail(LBC_EINVAL, "table Prandtl numbers must be finite and > 0");
+        }
+    } else if (p.mu_law != LBC_MU_POWER) {
+        return fail(LBC_EINVAL, "unknown viscosity law");
+    }
     if (!std::isfinite(p.omega)) return fail(LBC_EINVAL, "omega must be finite");
     if (p.precision != LBC_FP64 && p.precision != LBC_FP32_STATE) return fail(LBC_EINVAL, "unknown precision");
     return LBC_OK;
@@ -83,11 +97,38 @@ bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std:
     }
     make_grid(p.Nx, p.stretch_A, ps.x, ps.inv_jdeta, ps.deta, ps.min_jdeta);
 
+    // table viscosity law (Eqs. mun, interp): segment exponents omega_n, and mu_n
+    // divided by mu(T_ref = 1), the viscosity that defines delta
+    auto mu_ratio = [&](double Tv) { return std::pow(Tv, p.omega); };
+    std::function<double(double)> mu_of = mu_ratio;
+    if (p.mu_law == LBC_MU_TABLE) {
+        const int nt = p.tab_n;
+        ps.tabT.assign(p.tab_T, p.tab_T + nt);
+        ps.tabPr.assign(p.tab_Pr, p.tab_Pr + nt);
+        ps.tabW.assign(nt, 0.0);
+        for (int k = 0; k + 1 < nt; ++k)
+            ps.tabW[k] = std::log(p.tab_mu[k + 1] / p.tab_mu[k]) / std::log(p.tab_T[k + 1] / p.tab_T[k]);
+        ps.tabW[nt - 1] = ps.tabW[nt - 2];
+        auto seg = [&ps, nt](double Tv) {   // the segment of Eq. interp that holds Tv
+            int k = (int)(std::upper_bound(ps.tabT.begin(), ps.tabT.end(), Tv) - ps.tabT.begin());
+            return std::min(std::max(k - 1, 0), nt - 2);
+        };
+        const int c1 = seg(1.0);
+        const double mu_ref = p.tab_mu[c1] * std::pow(1.0 / p.tab_T[c1], ps.tabW[c1]);
+        ps.tabMu.assign(nt, 0.0);
+        for (int k = 0; k < nt; ++k) ps.tabMu[k] = p.tab_mu[k] / mu_ref;
+        mu_of = [&ps, seg](double Tv) {
+            const int c = seg(Tv);
+            return ps.tabMu[c] * std::pow(Tv / ps.tabT[c], ps.tabW[c]);
+        };
+    }
+
     // time step: CFL on the smallest cell, and half the smallest relaxation time
+    // tau = (mu(T)/mu(T_ref)) / (n T delta sqrt(2)) at n = 1 (Eq. tau)
     double dt = p.dt > 0 ? p.dt : p.cfl * ps.min_jdeta / (t.zx.back() * p.p0);
     if (p.dt <= 0 && p.delta > 0)
         for (double Tw : {1.0, p.T_left, p.T_right})
-            dt = std::min(dt, 0.5 * std::pow(Tw, p.omega - 1.0) / (p.delta * std::sqrt(2.0)));
+            dt = std::min(dt, 0.5 * mu_of(Tw) / (Tw * p.delta * std::sqrt(2.0)));
     ps.dt = dt;
 
     // wall Maxwellians (unit density), incoming unit fluxes, rest Maxwellian
@@ -130,8 +171,15 @@ bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std:
         err = "internal: recurrence table too short";
         return false;
     }
-    const EqTab E(Nxe, Nye, t.K, p.Qx, p.Qy);
+    const int ntab = (int)ps.tabT.size();
+    const EqTab E(Nxe, Nye, t.K, p.Qx, p.Qy, ntab);
     ps.eqtab.assign(E.len, 0.0);
+    for (int k = 0; k < ntab; ++k) {
+        ps.eqtab[E.lawT + k] = ps.tabT[k];
+        ps.eqtab[E.lawMu + k] = ps.tabMu[k];
+        ps.eqtab[E.lawW + k] = ps.tabW[k];
+        ps.eqtab[E.lawPr + k] = ps.tabPr[k];
+    }
     for (int l = 0; l < Nxe + 2; ++l) {
         ps.eqtab[E.alpha + l] = t.alpha[l];
         ps.eqtab[E.sbeta + l] = t.sbeta[l];
@@ -208,6 +256,8 @@ void bind_tables(const ProblemSetup &ps, const lbc_params &p, const void *dev, D
     T.Nxp = (p.Nx + 31) / 32 * 32;
     T.Qx = p.Qx; T.Qy = p.Qy; T.Nxe = ps.Nxe; T.Nye = ps.Nye; T.K = t.K; T.V = t.V;
     T.ntile = (p.Nx + kTile - 1) / kTile;
+    T.law = p.mu_law;
+    T.tab_n = (int)ps.tabT.size();
     T.p0 = p.p0; T.dt = ps.dt; T.delta = p.delta; T.Pr = p.Pr; T.omega = p.omega;
     T.TL = p.T_left; T.TR = p.T_right; T.inL = ps.inL; T.inR = ps.inR;
     T.restOutL = ps.restOutL; T.restOutR = ps.restOutR;
@@ -262,8 +312,8 @@ constexpr double kCtaOverheadRows = 150.0;
 
 size_t stage_smem(bool fp32, const DevTables &T, int vchunk, int cluster)
 {
-    return fp32 ? stage_smem_bytes<float>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vchunk, cluster)
-                : stage_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vchunk, cluster);
+    return fp32 ? stage_smem_bytes<float>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vchunk, cluster, T.tab_n)
+                : stage_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vchunk, cluster, T.tab_n);
 }
 
 int active_clusters(bool fp32, size_t smem, int cluster, bool batch)
@@ -288,8 +338,8 @@ lbc_status device_limits(bool fp32, const DevTables &T, int &optin)
     optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t eqs = fp32 ? equilibrium_smem_bytes<float>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K)
-                            : equilibrium_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K);
+    const size_t eqs = fp32 ? equilibrium_smem_bytes<float>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.tab_n)
+                            : equilibrium_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.tab_n);
     if (eqs > (size_t)optin)
         return fail(LBC_EINVAL, "quadrature orders too large for the shared memory of one CTA (" +
                                     std::to_string(eqs) + " bytes)");

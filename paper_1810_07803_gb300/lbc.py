@@ -46,16 +46,32 @@ DEFAULTS = dict(delta=1.0, u_left=0.0, u_right=0.0, T_left=1.0, T_right=1.0, Pr=
                 cfl=0.5, dt=0.0, precision="fp64")
 
 
+MU_POWER, MU_TABLE = 0, 1
+
+
 def make_params(d: dict) -> Params:
+    """lbc_params from a dict (DEFAULTS filled in). mu_law "table" takes the arrays
+    tab_T, tab_mu, tab_Pr (Eqs. mun, interp); the returned struct keeps them alive."""
     p = dict(DEFAULTS)
     p.update(d)
     prec = p["precision"]
     prec = {"fp64": FP64, "fp32": FP32_STATE}.get(prec, prec)
-    return Params(delta=p["delta"], u_left=p["u_left"], u_right=p["u_right"], T_left=p["T_left"],
-                  T_right=p["T_right"], Pr=p["Pr"], mu_law=0, omega=p["omega"], tab_T=None, tab_mu=None,
-                  tab_Pr=None, tab_n=0, Nx=int(p["Nx"]), stretch_A=p["stretch_A"], Qx=int(p["Qx"]),
-                  Qy=int(p["Qy"]), Nexp_x=int(p["Nexp_x"]), Nexp_y=int(p["Nexp_y"]), p0=p["p0"],
-                  cfl=p["cfl"], dt=p["dt"], precision=int(prec))
+    law = p.get("mu_law", "power")
+    law = {"power": MU_POWER, "table": MU_TABLE}.get(law, law)
+    keep = []
+    tabs = [None, None, None]
+    n = 0
+    if law == MU_TABLE:
+        keep = [np.ascontiguousarray(p[k], dtype=np.float64) for k in ("tab_T", "tab_mu", "tab_Pr")]
+        n = len(keep[0])
+        tabs = [a.ctypes.data for a in keep]
+    out = Params(delta=p["delta"], u_left=p["u_left"], u_right=p["u_right"], T_left=p["T_left"],
+                 T_right=p["T_right"], Pr=p["Pr"], mu_law=int(law), omega=p["omega"], tab_T=tabs[0],
+                 tab_mu=tabs[1], tab_Pr=tabs[2], tab_n=n, Nx=int(p["Nx"]), stretch_A=p["stretch_A"],
+                 Qx=int(p["Qx"]), Qy=int(p["Qy"]), Nexp_x=int(p["Nexp_x"]), Nexp_y=int(p["Nexp_y"]),
+                 p0=p["p0"], cfl=p["cfl"], dt=p["dt"], precision=int(prec))
+    out._keep = keep
+    return out
 
 
 _lib = None
@@ -236,7 +252,9 @@ class Batch:
             q.update(d)
             self.params.append(q)
         n = len(self.params)
-        arr = (Params * n)(*[make_params(q) for q in self.params])
+        structs = [make_params(q) for q in self.params]
+        self._keep = [st._keep for st in structs]   # table arrays referenced by the structs
+        arr = (Params * n)(*structs)
         self._arr = arr
         h = C.c_void_p()
         st = stream if stream is not None else current_stream_handle()

@@ -63,6 +63,24 @@ def c4(seed: int = 4, n: int = 512, precision: str = "fp32") -> list[dict]:
     return out
 
 
+def synthetic_viscosity_table(seed: int = 7, n: int = 24, T_lo: float = 0.05, T_hi: float = 20.0) -> dict:
+    """A seeded stand-in for an ab initio viscosity/conductivity table (the paper's
+    3He/4He tables are not available): n temperatures log-spaced over [T_lo, T_hi]
+    (T_ref units, jittered), viscosities whose local index d ln mu / d ln T drifts
+    from ~0.6 at low T to ~0.8 at high T with seeded noise, in arbitrary units, and
+    Prandtl numbers within a few percent of 2/3. Returns the lbc_params fields of
+    the table law (Eqs. mun, interp)."""
+    rng = np.random.default_rng(seed)
+    lnT = np.linspace(math.log(T_lo), math.log(T_hi), n)
+    step = lnT[1] - lnT[0]
+    lnT[1:-1] += rng.uniform(-0.25, 0.25, n - 2) * step
+    omega = 0.7 + 0.1 * np.tanh(0.5 * (lnT[:-1] + lnT[1:])) + rng.normal(0.0, 0.02, n - 1)
+    lnmu = np.concatenate([[0.0], np.cumsum(omega * np.diff(lnT))])
+    phase = rng.uniform(0.0, 2.0 * math.pi)
+    Pr = 2.0 / 3.0 + 0.015 * np.sin(np.linspace(0.0, 3.0 * math.pi, n) + phase)
+    return dict(mu_law="table", tab_T=np.exp(lnT), tab_mu=19.6 * np.exp(lnmu), tab_Pr=Pr)
+
+
 def perturbed_state(V: int, Nx: int, base: np.ndarray, seed: int, amplitude: float = 0.05) -> np.ndarray:
     """A smooth seeded perturbation of a weight-divided state `base` [2][V][Nx]:
     base * (1 + amplitude * sum of a few low Fourier modes in x, random per velocity)."""

@@ -84,3 +84,16 @@ def test_library_is_not_a_cpu_fallback():
     with pytest.raises(lbc.LbcError) as e:
         lbc.Solver(dict(Qx=4, Qy=4, Nx=16))
     assert e.value.status == lbc.ECUDA
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (dict(tab_T=[1.0], tab_mu=[1.0], tab_Pr=[0.7]), "2 to 256 entries"),
+    (dict(tab_T=[1.0, 0.5], tab_mu=[1.0, 1.2], tab_Pr=[0.7, 0.7]), "strictly increasing"),
+    (dict(tab_T=[0.5, 1.0], tab_mu=[1.0, -1.2], tab_Pr=[0.7, 0.7]), "viscosities"),
+    (dict(tab_T=[0.5, 1.0], tab_mu=[1.0, 1.2], tab_Pr=[0.7, 0.0]), "Prandtl"),
+])
+def test_create_rejects_bad_viscosity_tables(bad, msg):
+    with pytest.raises(lbc.LbcError) as e:
+        lbc.Solver(dict(mu_law="table", **bad))
+    assert e.value.status == lbc.EINVAL
+    assert msg in str(e.value)
