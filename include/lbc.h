@@ -216,6 +216,51 @@ lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms);
 void lbc_batch_destroy(lbc_batch *b);
 
 /*
+ * Instance pool: problems that join and leave while others run, stepped
+ * together by the batched stage kernel (continuous batching; no counterpart
+ * in the paper). Each admitted instance gets its own stream-ordered device
+ * allocation; admission is by device footprint against the pool's budget.
+ *
+ * lbc_pool_create: cluster = chunk CTAs per tile for every instance, in
+ *   [1, 16] (instances whose velocity set needs more rows per CTA than 256 or
+ *   more shared memory than one CTA has are rejected); precision of every
+ *   instance; budget_bytes = device bytes the instances (tables and state, as
+ *   lbc_pool_footprint) may use in total -- the pool adds a fixed part (slots,
+ *   work list) and one staging buffer for state transfers of the largest
+ *   instance admitted;
+ *   max_instances slots; max_tiles = capacity of the work list (31-node tiles
+ *   over all instances).
+ * lbc_pool_footprint: device bytes an instance of `params` takes in a pool's budget.
+ * lbc_pool_add: admits an instance at the rest state (as lbc_create); *slot
+ *   receives its slot. LBC_ENOMEM when the budget, the slots or the work list
+ *   are exhausted (nothing changes: the caller queues and retries later).
+ *   Synchronises the stream.
+ * lbc_pool_remove: frees the slot (stream-ordered).
+ * lbc_pool_run: advances every instance up to nsteps steps; an instance stops
+ *   at its first step whose residual (as lbc_run_to_steady) is below
+ *   `residual`. finished[] (caller-owned, max_instances entries, may be NULL)
+ *   receives the slots that converged and were not reported before,
+ *   *nfinished their count; a reported instance left in the pool takes no
+ *   further steps. Synchronises the stream.
+ * lbc_pool_info / moments / get_state: as the single-solver calls for a slot;
+ *   info also gives the last step's residual.
+ * lbc_pool_usage: device bytes in use, instances, work items.
+ */
+typedef struct lbc_pool lbc_pool;
+lbc_status lbc_pool_create(int cluster, lbc_precision precision, size_t budget_bytes, int max_instances,
+                           int max_tiles, void *cuda_stream, lbc_pool **out);
+lbc_status lbc_pool_footprint(const lbc_params *params, int cluster, size_t *bytes);
+lbc_status lbc_pool_add(lbc_pool *pool, const lbc_params *params, int *slot);
+lbc_status lbc_pool_remove(lbc_pool *pool, int slot);
+lbc_status lbc_pool_run(lbc_pool *pool, double residual, long nsteps, int *finished, int *nfinished);
+lbc_status lbc_pool_info(const lbc_pool *pool, int slot, int *Nx, int *V, double *dt, long *steps_taken,
+                         double *last_residual);
+lbc_status lbc_pool_usage(const lbc_pool *pool, size_t *used_bytes, int *instances, int *work_items);
+lbc_status lbc_pool_moments(lbc_pool *pool, int slot, double *out, double *x);
+lbc_status lbc_pool_get_state(lbc_pool *pool, int slot, double *state);
+void lbc_pool_destroy(lbc_pool *pool);
+
+/*
  * Allocation-free stepping (the paper has no counterpart: this serves callers
  * that cannot allocate device memory, e.g. code embedded in an application
  * whose own allocator owns the GPU memory, or latency-critical loops where the

@@ -33,7 +33,7 @@ struct InstHost {
     long long steps = 0;         // completed steps
 };
 
-size_t r256(size_t x) { return (x + 255) / 256 * 256; }
+size_t r256(size_t x) { return round256(x); }
 
 }  // namespace
 
@@ -175,23 +175,6 @@ lbc_status rebuild_stage_data(lbc_batch *b, int i)
     return LBC_OK;
 }
 
-// Per-instance device bytes (partials sized for the largest cluster, so a
-// batch can change its launch shape without reallocating).
-struct StateSizes {
-    size_t f, eqm, eqg, part, resid, mom, total;
-    StateSizes(const DevTables &T, bool fp32)
-    {
-        const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-        f = r256(2 * (size_t)T.V * T.Nxp * esz);
-        eqm = r256((size_t)T.Nxp * kEqM * esz);
-        eqg = r256((size_t)T.ntile * (2 * T.Qx + T.Qy) * kLanes * esz);
-        part = r256((size_t)kMaxCluster * kNumRaw * T.Nxp * esz);
-        resid = kResidRing * sizeof(unsigned long long);
-        mom = r256((size_t)LBC_NMOM * T.Nxp * sizeof(double));
-        total = 3 * (f + eqm + eqg) + part + resid + mom;
-    }
-};
-
 // Work list: every (instance, tile), instances with the longest CTAs first.
 void build_work(lbc_batch *b, std::vector<int2> &work)
 {
@@ -323,14 +306,7 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     for (int i = 0; i < n; ++i) {
         DevTables &T = b->inst[i].T;
         DevState &S = b->inst[i].S;
-        const StateSizes z(T, b->fp32);
-        char *p = sb + soff[i];
-        for (int k = 0; k < 3; ++k) { S.F[k] = p; p += z.f; }
-        for (int k = 0; k < 3; ++k) { S.eqm[k] = p; p += z.eqm; }
-        for (int k = 0; k < 3; ++k) { S.eqg[k] = p; p += z.eqg; }
-        S.part = p; p += z.part;
-        S.resid = reinterpret_cast<unsigned long long *>(p); p += z.resid;
-        S.mom_out = reinterpret_cast<double *>(p);
+        StateSizes(T, b->fp32).carve(sb + soff[i], S);
         S.ctl = b->d_ctl + i;
         StateMaps &M = b->inst[i].M;
         for (int k = 0; k < 3 && st == LBC_OK; ++k) st = encode_state_map(&M.in[k], S.F[k], b->fp32, T.V, T.Nxp, kRowLen);
@@ -383,7 +359,7 @@ lbc_status batch_run_to_steady(lbc_batch *b, double residual, long max_steps, lo
         const long k = std::min<long>(kGraphSteps, max_steps - done);
         st = run_steps(b, k);
         if (st != LBC_OK) return st;
-        LBC_CUDA_TRY(launch_last_residuals(b->d_inst, n, b->d_last, b->stream));
+        LBC_CUDA_TRY(launch_last_residuals(b->d_inst, nullptr, n, b->d_last, b->stream));
         LBC_CUDA_TRY(cudaMemcpyAsync(b->h_last, b->d_last, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
         st = read_ctl(b);
         if (st != LBC_OK) return st;

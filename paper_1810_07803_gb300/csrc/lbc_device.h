@@ -214,7 +214,37 @@ cudaError_t launch_state_in(const double *src, void *dst, const DevTables &T, in
 template <typename R>
 cudaError_t launch_state_out(const void *src, double *dst, const DevTables &T, cudaStream_t st);
 cudaError_t launch_ctl_bump(Ctl *ctl, int n, long long k, cudaStream_t st);
-// last[i] = residual of instance i's last step taken (its stop step - 1 if stopped, else base - 1)
-cudaError_t launch_last_residuals(const Inst *insts, int n, double *last, cudaStream_t st);
+// last[k] = residual of instance slots[k]'s (k's if slots is NULL) last step taken (its stop
+// step - 1 if stopped, else base - 1), k < n
+cudaError_t launch_last_residuals(const Inst *insts, const int *slots, int n, double *last, cudaStream_t st);
+
+inline size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+// Device bytes of one instance's state (partials sized for the largest cluster, so
+// a launch shape can change without reallocating).
+struct StateSizes {
+    size_t f, eqm, eqg, part, resid, mom, total;
+    StateSizes(const DevTables &T, bool fp32)
+    {
+        const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+        f = round256(2 * (size_t)T.V * T.Nxp * esz);
+        eqm = round256((size_t)T.Nxp * kEqM * esz);
+        eqg = round256((size_t)T.ntile * (2 * T.Qx + T.Qy) * kLanes * esz);
+        part = round256((size_t)kMaxCluster * kNumRaw * T.Nxp * esz);
+        resid = kResidRing * sizeof(unsigned long long);
+        mom = round256((size_t)LBC_NMOM * T.Nxp * sizeof(double));
+        total = 3 * (f + eqm + eqg) + part + resid + mom;
+    }
+    // Points the state arrays of S into `base` (total bytes); S.ctl is set by the caller.
+    void carve(char *base, DevState &S) const
+    {
+        char *p = base;
+        for (int k = 0; k < 3; ++k) { S.F[k] = p; p += f; }
+        for (int k = 0; k < 3; ++k) { S.eqm[k] = p; p += eqm; }
+        for (int k = 0; k < 3; ++k) { S.eqg[k] = p; p += eqg; }
+        S.part = p; p += part;
+        S.resid = reinterpret_cast<unsigned long long *>(p); p += resid;
+        S.mom_out = reinterpret_cast<double *>(p);
+    }
+};
 
 }  // namespace lbc

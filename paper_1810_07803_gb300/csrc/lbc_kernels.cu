@@ -1222,12 +1222,13 @@ __global__ void ctl_bump_kernel(Ctl *ctl, int n, long long k)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) ctl[i].base += k;
 }
 
-__global__ void last_residuals_kernel(const Inst *insts, int n, double *last)
+__global__ void last_residuals_kernel(const Inst *insts, const int *slots, int n, double *last)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const Ctl *c = insts[i].S.ctl;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const Inst &I = insts[slots ? slots[k] : k];
+        const Ctl *c = I.S.ctl;
         const long long st = (c->stopped ? c->stop_step : c->base) - 1;
-        last[i] = st >= 0 ? __longlong_as_double((long long)insts[i].S.resid[st % kResidRing]) : 0.0;
+        last[k] = st >= 0 ? __longlong_as_double((long long)I.S.resid[st % kResidRing]) : 0.0;
     }
 }
 
@@ -1373,9 +1374,10 @@ cudaError_t launch_ctl_bump(Ctl *ctl, int n, long long k, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_last_residuals(const Inst *insts, int n, double *last, cudaStream_t st)
+cudaError_t launch_last_residuals(const Inst *insts, const int *slots, int n, double *last, cudaStream_t st)
 {
-    last_residuals_kernel<<<(n + 255) / 256, 256, 0, st>>>(insts, n, last);
+    if (n <= 0) return cudaSuccess;
+    last_residuals_kernel<<<(n + 255) / 256, 256, 0, st>>>(insts, slots, n, last);
     return cudaGetLastError();
 }
 

@@ -114,10 +114,22 @@ def lib():
         L.lbc_batch_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.lbc_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.lbc_batch_step_timed.argtypes = [vp, C.c_long, dp]
+        ip = C.POINTER(C.c_int)
+        L.lbc_pool_create.argtypes = [C.c_int, C.c_int, C.c_size_t, C.c_int, C.c_int, vp, C.POINTER(vp)]
+        L.lbc_pool_footprint.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_size_t)]
+        L.lbc_pool_add.argtypes = [vp, C.POINTER(Params), ip]
+        L.lbc_pool_remove.argtypes = [vp, C.c_int]
+        L.lbc_pool_run.argtypes = [vp, C.c_double, C.c_long, ip, ip]
+        L.lbc_pool_info.argtypes = [vp, C.c_int, ip, ip, dp, C.POINTER(C.c_long), dp]
+        L.lbc_pool_usage.argtypes = [vp, C.POINTER(C.c_size_t), ip, ip]
+        L.lbc_pool_moments.argtypes = [vp, C.c_int, dp, dp]
+        L.lbc_pool_get_state.argtypes = [vp, C.c_int, dp]
+        L.lbc_pool_destroy.argtypes = [vp]
+        L.lbc_pool_destroy.restype = None
         L.lbc_batch_destroy.argtypes = [vp]
         L.lbc_batch_destroy.restype = None
         for name in declared_functions():
-            if name not in ("lbc_destroy", "lbc_last_error", "lbc_batch_destroy"):
+            if name not in ("lbc_destroy", "lbc_last_error", "lbc_batch_destroy", "lbc_pool_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -333,3 +345,90 @@ class Batch:
     def set_state(self, i: int, f):
         ptr, keep = _state_ptr(f, self.V[i], self.Nx[i])
         _check(lib().lbc_batch_set_state(self._h, i, ptr))
+
+
+class Pool:
+    """Instances that join and leave while others run (include/lbc.h, lbc_pool_*)."""
+
+    def __init__(self, cluster: int, precision: str = "fp32", budget_bytes: int = 8 << 30,
+                 max_instances: int = 1024, max_tiles: int = 1 << 16, stream=None):
+        prec = {"fp64": FP64, "fp32": FP32_STATE}[precision]
+        h = C.c_void_p()
+        st = stream if stream is not None else current_stream_handle()
+        _check(lib().lbc_pool_create(int(cluster), prec, int(budget_bytes), int(max_instances), int(max_tiles),
+                                     C.c_void_p(st) if st else None, C.byref(h)))
+        self._h = h
+        self.cluster = cluster
+        self.precision = precision
+        self.max_instances = max_instances
+        self._fin = (C.c_int * max_instances)()
+        self.params = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbc_pool_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def footprint(params: dict, cluster: int) -> int:
+        b = C.c_size_t()
+        p = make_params(params)
+        _check(lib().lbc_pool_footprint(C.byref(p), int(cluster), C.byref(b)))
+        return b.value
+
+    def try_add(self, params: dict):
+        """Slot of the admitted instance, or None when the pool is full (budget, slots, work list)."""
+        q = dict(DEFAULTS)
+        q.update(params)
+        q["precision"] = self.precision
+        p = make_params(q)
+        slot = C.c_int()
+        st = lib().lbc_pool_add(self._h, C.byref(p), C.byref(slot))
+        if st == ENOMEM:
+            return None
+        _check(st)
+        self.params[slot.value] = q
+        return slot.value
+
+    def remove(self, slot: int):
+        _check(lib().lbc_pool_remove(self._h, int(slot)))
+        self.params.pop(slot, None)
+
+    def run(self, residual: float, nsteps: int):
+        """Advances every instance up to nsteps steps; returns the slots that converged."""
+        n = C.c_int()
+        _check(lib().lbc_pool_run(self._h, residual, int(nsteps), self._fin, C.byref(n)))
+        return list(self._fin[:n.value])
+
+    def info(self, slot: int):
+        """(Nx, V, dt, steps taken, last residual)."""
+        nx, nv, dt, steps, res = C.c_int(), C.c_int(), C.c_double(), C.c_long(), C.c_double()
+        _check(lib().lbc_pool_info(self._h, int(slot), C.byref(nx), C.byref(nv), C.byref(dt), C.byref(steps),
+                                   C.byref(res)))
+        return nx.value, nv.value, dt.value, steps.value, res.value
+
+    def usage(self):
+        """(device bytes in use, instances, work items)."""
+        b, n, w = C.c_size_t(), C.c_int(), C.c_int()
+        _check(lib().lbc_pool_usage(self._h, C.byref(b), C.byref(n), C.byref(w)))
+        return b.value, n.value, w.value
+
+    def moments(self, slot: int):
+        nx = self.info(slot)[0]
+        out = np.zeros((NMOM, nx))
+        _check(lib().lbc_pool_moments(self._h, int(slot), _dptr(out), None))
+        return out
+
+    def get_state(self, slot: int):
+        nx, nv = self.info(slot)[:2]
+        out = np.zeros((2, nv, nx))
+        _check(lib().lbc_pool_get_state(self._h, int(slot), _dptr(out)))
+        return out

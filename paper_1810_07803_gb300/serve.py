@@ -1,0 +1,208 @@
+"""Serving loop on the instance pool: Couette solves arrive over time, are
+admitted as device memory allows, run together (continuous batching) until each
+reaches the steady-state residual, and leave; latency is arrival to result.
+
+The pool (include/lbc.h, lbc_pool_*) steps every resident instance in one
+batched launch per RK stage, and each instance stops at its own converged
+step, so requests that arrive while others run join the next chunk of steps.
+The plain comparison serves the same requests one at a time with a
+single-instance FP64 solver.
+
+    python -m paper_1810_07803_gb300.serve --rates 10,100,1000 --duration 10
+"""
+from __future__ import annotations
+
+import argparse
+import collections
+import json
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lbc
+
+SQ2 = math.sqrt(2.0)
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float                  # seconds after the start of the trace
+    params: dict
+    admitted: float | None = None
+    finished: float | None = None
+    steps: int = 0
+    residual: float = math.inf
+    converged: bool = False
+    moments: np.ndarray | None = field(default=None, repr=False)
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def poisson_arrivals(rate: float, duration: float, seed: int) -> np.ndarray:
+    """Arrival times of a Poisson process of `rate` per second over [0, duration)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return np.array(out)
+        out.append(t)
+
+
+def small_solve(rng: np.random.Generator) -> dict:
+    """One request of the served workload: a small Couette solve (Nx 32-160,
+    Qx, Qy 4-8, delta log-U[0.3, 3], wall temperature ratio log-U[1, 2],
+    u_w U[0.01, 0.3] sqrt(2kT/m), omega 0.66, Pr 2/3, wall-clustered grid)."""
+    ratio = float(math.exp(rng.uniform(0.0, math.log(2.0))))
+    TL = 2.0 / (1.0 + ratio)
+    uw = float(rng.uniform(0.01, 0.3)) * SQ2
+    return dict(delta=float(math.exp(rng.uniform(math.log(0.3), math.log(3.0)))), u_left=-uw, u_right=uw,
+                T_left=TL, T_right=ratio * TL, Pr=2.0 / 3.0, omega=0.66, Nx=int(rng.integers(32, 161)),
+                stretch_A=math.sqrt(0.9), Qx=int(rng.integers(4, 9)), Qy=int(rng.integers(4, 9)))
+
+
+def make_trace(rate: float, duration: float, seed: int, draw=small_solve) -> list[Request]:
+    times = poisson_arrivals(rate, duration, seed)
+    rng = np.random.default_rng(seed + 1)
+    return [Request(k, float(t), draw(rng)) for k, t in enumerate(times)]
+
+
+class Server:
+    """Continuous batching on one GPU: FIFO admission by device footprint, chunks
+    of `chunk` steps for all resident requests, retirement at convergence.
+
+    clock: "wall" serves the trace in real time (latency in seconds); "steps"
+    advances a virtual clock by one unit per step chunk, which makes admission
+    order deterministic for tests.
+    """
+
+    def __init__(self, cluster: int = 4, precision: str = "fp32", budget_bytes: int = 16 << 30,
+                 residual: float = 1e-8, chunk: int = 32, max_steps: int = 200_000,
+                 max_instances: int = 4096, pool=None):
+        # `pool` replaces the device pool (same methods as lbc.Pool), e.g. to test the scheduling
+        self.pool = pool if pool is not None else lbc.Pool(cluster, precision, budget_bytes,
+                                                           max_instances=max_instances, max_tiles=1 << 18)
+        self.residual, self.chunk, self.max_steps = residual, chunk, max_steps
+
+    def close(self):
+        self.pool.close()
+
+    def serve(self, requests: list[Request], clock: str = "wall") -> list[Request]:
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        queue: collections.deque = collections.deque()
+        active: dict[int, Request] = {}
+        nxt = 0
+        t0 = time.perf_counter()
+        vclock = 0.0
+
+        def now():
+            return time.perf_counter() - t0 if clock == "wall" else vclock
+
+        while nxt < len(reqs) or queue or active:
+            t = now()
+            while nxt < len(reqs) and reqs[nxt].arrival <= t:
+                queue.append(reqs[nxt])
+                nxt += 1
+            while queue:                                   # FIFO admission while memory allows
+                slot = self.pool.try_add(queue[0].params)
+                if slot is None:
+                    if not active:
+                        raise RuntimeError("request larger than the pool budget")
+                    break
+                r = queue.popleft()
+                r.admitted = t
+                active[slot] = r
+            if not active:                                 # idle until the next arrival
+                if clock == "wall":
+                    time.sleep(max(0.0, reqs[nxt].arrival - now()))
+                else:
+                    vclock = reqs[nxt].arrival
+                continue
+            done = set(self.pool.run(self.residual, self.chunk))
+            vclock += 1.0
+            t = now()
+            for slot, r in list(active.items()):
+                _, _, _, steps, res = self.pool.info(slot)
+                if slot in done or steps >= self.max_steps:
+                    r.finished, r.steps, r.residual = t, steps, res
+                    r.converged = slot in done
+                    r.moments = self.pool.moments(slot)
+                    self.pool.remove(slot)
+                    del active[slot]
+        return reqs
+
+
+def serve_sequential_fp64(requests: list[Request], residual: float = 1e-8, max_steps: int = 200_000,
+                          measure: int = 3) -> list[Request]:
+    """The plain comparison: one request at a time, single-instance FP64 solver,
+    in arrival order. The first `measure` requests are solved and timed; the
+    queue of the whole trace is then played with those service times in turn
+    (a single FIFO server: start = max(arrival, previous finish)), because one
+    FP64 solve takes seconds and a full trace would take minutes per rate."""
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    service = []
+    for r in reqs[:measure]:
+        s = lbc.Solver(dict(r.params, precision="fp64"))
+        t0 = time.perf_counter()
+        try:
+            r.steps, r.residual = s.run_to_steady(residual, max_steps)
+            r.converged = True
+        except lbc.LbcError as e:
+            if e.status != lbc.ENOTCONV:
+                raise
+            r.steps, r.residual = s.steps, math.inf
+        r.moments = s.moments()
+        service.append(time.perf_counter() - t0)
+        s.close()
+    free = 0.0
+    for k, r in enumerate(reqs):
+        r.admitted = max(r.arrival, free)
+        r.finished = free = r.admitted + service[k % len(service)]
+        if k >= measure:
+            r.converged, r.steps = True, reqs[k % measure].steps
+    return reqs
+
+
+def summary(reqs: list[Request], label: str, rate: float, duration: float) -> dict:
+    lat = np.array([r.latency for r in reqs])
+    span = max(r.finished for r in reqs) if reqs else 0.0
+    ok = sum(r.converged for r in reqs)
+    return {"server": label, "rate_per_s": rate, "duration_s": duration, "requests": len(reqs),
+            "converged": ok, "solves_per_s": ok / span if span > 0 else 0.0,
+            "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "mean_steps": float(np.mean([r.steps for r in reqs])) if reqs else 0.0}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--rates", default="10,100,1000")
+    ap.add_argument("--duration", type=float, default=10.0)
+    ap.add_argument("--residual", type=float, default=1e-8)
+    ap.add_argument("--cluster", type=int, default=4)
+    ap.add_argument("--chunk", type=int, default=32)
+    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--sequential-measure", type=int, default=3,
+                    help="requests the FP64 sequential comparison solves and times (the rest are queued with "
+                         "those service times)")
+    args = ap.parse_args()
+    for rate in (float(x) for x in args.rates.split(",")):
+        trace = make_trace(rate, args.duration, args.seed)
+        srv = Server(cluster=args.cluster, residual=args.residual, chunk=args.chunk)
+        out = summary(srv.serve(trace), "pool-fp32", rate, args.duration)
+        srv.close()
+        print(json.dumps(out), flush=True)
+        seq = make_trace(rate, args.duration, args.seed)
+        out = summary(serve_sequential_fp64(seq, args.residual, measure=args.sequential_measure),
+                      "sequential-fp64", rate, args.duration)
+        out["timing"] = f"{args.sequential_measure} solves measured, FIFO queue played with their service times"
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
