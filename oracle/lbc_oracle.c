@@ -49,6 +49,10 @@ typedef struct {
     const double *yy, *wy;          /* [Qy] full-range nodes / weights */
     const double *Phi, *Phi_lo;     /* [Nxe+1][Qx] Phi_{s,i} = Phi + Phi_lo (double-double) */
     const double *He, *He_lo;       /* [Nye+1][Qy] He_l(y_j) = He + He_lo (double-double) */
+    int local_dt;                   /* 1: time step dtn[s] per node and mass renormalisation */
+    int mirror;                     /* 1: half channel, symmetry plane instead of the left wall */
+    const double *dtn;              /* [Nx] node time steps (local_dt only) */
+    double mass_ref;                /* mass the local-step iteration keeps (local_dt only) */
 } orc_problem;
 
 enum { M_N, M_UX, M_UY, M_T, M_PXX, M_PYY, M_PZZ, M_PXY, M_QX, M_QY, M_COUNT };
@@ -289,8 +293,21 @@ static void wall_maxwellians(const orc_problem *P, double *fwl, double *fwr)
     free(gx); free(gy);
 }
 
+/* Velocity with the opposite momentum, (p_x, p_y) -> (-p_x, -p_y): the two
+ * half-range halves hold opposite nodes (a <-> a + Qx), and the full-range
+ * nodes are symmetric (j <-> Qy - 1 - j). */
+static int mirror_velocity(const orc_problem *P, int v)
+{
+    int a = v / P->Qy, j = v % P->Qy;
+    return ((a + P->Qx) % (2 * P->Qx)) * P->Qy + (P->Qy - 1 - j);
+}
+
 /* ---- right-hand side L(f) = advection + relaxation ---------------------- */
-/* nw_out (optional) receives n_w at the left and right walls. */
+/* nw_out (optional) receives n_w at the left and right walls (left: 0 on the
+ * half channel). Half channel (P->mirror, Sec. II's symmetry of Couette flow
+ * between walls of equal temperature moving in opposite directions,
+ * phi(-x, -p) = phi(x, p)): the domain is 0 < x < 1/2 and the ghost nodes left
+ * of x = 0 are the mirror images of nodes 0, 1, 2 at the opposite velocity. */
 void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
 {
     int Nx = P->Nx, V = nvel(P), Qy = P->Qy;
@@ -312,6 +329,11 @@ void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
                 ext[Nx + 2] = 4 * row[Nx - 1] - 6 * row[Nx - 2] + 4 * row[Nx - 3] - row[Nx - 4];
                 ext[Nx + 3] = 10 * row[Nx - 1] - 20 * row[Nx - 2] + 15 * row[Nx - 3] - 4 * row[Nx - 4];
                 F[Nx] = orc_weno5(ext[Nx - 1], ext[Nx], ext[Nx + 1], ext[Nx + 2], ext[Nx + 3], P->eps);
+            } else if (P->mirror) {   /* face at the symmetry plane: mirror ghosts */
+                const double *mrow = f + fld * fs + (long)mirror_velocity(P, v) * Nx;
+                ext[1] = mrow[0];
+                ext[0] = mrow[1];
+                F[0] = orc_weno5(ext[4], ext[3], ext[2], ext[1], ext[0], P->eps);
             } else {        /* outgoing at the left wall */
                 ext[1] = 4 * row[0] - 6 * row[1] + 4 * row[2] - row[3];
                 ext[0] = 10 * row[0] - 20 * row[1] + 15 * row[2] - 4 * row[3];
@@ -327,7 +349,7 @@ void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
         if (px > 0) { outR += px * w * F[Nx]; inL += px * w * fwl[v]; }
         else        { outL += px * w * F[0];  inR += px * w * fwr[v]; }
     }
-    double nwL = -outL / inL, nwR = -outR / inR;
+    double nwL = P->mirror ? 0.0 : -outL / inL, nwR = -outR / inR;
     if (nw_out) { nw_out[0] = nwL; nw_out[1] = nwR; }
 
     /* 3) remaining faces; incoming ghosts and wall faces = n_w f_w (chi: T_w n_w f_w). */
@@ -337,12 +359,18 @@ void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
             double *F = face + ((long)fld * V + v) * (Nx + 1);
             double px = px_of(P, v);
             for (int s = 0; s < Nx; ++s) ext[s + 2] = row[s];
+            const double *mrow = f + fld * fs + (long)mirror_velocity(P, v) * Nx;
             if (px > 0) {
                 double in = nwL * fwl[v] * (fld ? P->TL : 1.0);
                 ext[0] = ext[1] = in;
                 ext[Nx + 2] = 4 * row[Nx - 1] - 6 * row[Nx - 2] + 4 * row[Nx - 3] - row[Nx - 4];
                 ext[Nx + 3] = 10 * row[Nx - 1] - 20 * row[Nx - 2] + 15 * row[Nx - 3] - 4 * row[Nx - 4];
                 F[0] = in;
+                if (P->mirror) {   /* ghosts -1, -2, -3 = nodes 0, 1, 2 at the opposite velocity */
+                    ext[1] = mrow[0];
+                    ext[0] = mrow[1];
+                    F[0] = orc_weno5(mrow[2], mrow[1], mrow[0], row[0], row[1], P->eps);
+                }
                 /* face k (left of cell k), upwind cell k-1: stencil k-3..k+1 */
                 for (int k = 1; k < Nx; ++k)
                     F[k] = orc_weno5(ext[k - 1], ext[k], ext[k + 1], ext[k + 2], ext[k + 3], P->eps);
@@ -351,6 +379,10 @@ void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
                 ext[Nx + 2] = ext[Nx + 3] = in;
                 ext[1] = 4 * row[0] - 6 * row[1] + 4 * row[2] - row[3];
                 ext[0] = 10 * row[0] - 20 * row[1] + 15 * row[2] - 4 * row[3];
+                if (P->mirror) {
+                    ext[1] = mrow[0];
+                    ext[0] = mrow[1];
+                }
                 F[Nx] = in;
                 /* upwind cell k: mirrored stencil k+2..k-2 */
                 for (int k = 1; k < Nx; ++k)
@@ -394,14 +426,46 @@ void orc_ssprk3(long n, double *y, double dt, orc_rhs_fn rhs, void *ctx)
     free(y1); free(y2); free(k);
 }
 
+/* The same step with a time step per node: component i of y = [..][Nx] is node
+ * i % Nx and advances by dtn[i % Nx]. With every dtn[s] = dt it is the step above. */
+void orc_ssprk3_nodal(long n, int Nx, double *y, const double *dtn, orc_rhs_fn rhs, void *ctx)
+{
+    double *y1 = malloc(sizeof(double) * n), *y2 = malloc(sizeof(double) * n);
+    double *k = malloc(sizeof(double) * n);
+    rhs(ctx, y, k);
+    for (long i = 0; i < n; ++i) y1[i] = y[i] + dtn[i % Nx] * k[i];
+    rhs(ctx, y1, k);
+    for (long i = 0; i < n; ++i) y2[i] = 0.75 * y[i] + 0.25 * (y1[i] + dtn[i % Nx] * k[i]);
+    rhs(ctx, y2, k);
+    for (long i = 0; i < n; ++i) y[i] = y[i] / 3.0 + 2.0 / 3.0 * (y2[i] + dtn[i % Nx] * k[i]);
+    free(y1); free(y2); free(k);
+}
+
 static void problem_rhs(void *ctx, const double *y, double *dy)
 {
     orc_rhs((const orc_problem *)ctx, y, dy, NULL);
 }
 
+/* Mass per unit wall area, sum_s J_s deta n_s with n_s = sum_v w_v phi_v,s. */
+double orc_total_mass(const orc_problem *P, const double *f)
+{
+    int V = nvel(P), Nx = P->Nx;
+    double M = 0.0;
+    for (int s = 0; s < Nx; ++s) {
+        double n = 0.0;
+        for (int v = 0; v < V; ++v) n += w_of(P, v) * f[(long)v * Nx + s];
+        M += P->J[s] * P->deta * n;
+    }
+    return M;
+}
+
 /* Runs up to nsteps RK-3 steps in place on f. resid[k] (optional) receives
  * max_{fld,v,s} w_v |f^{k+1} - f^k|; stops early once it drops below stop_below
- * (if > 0). Returns the number of steps taken. */
+ * (if > 0). Returns the number of steps taken.
+ * Local steps (P->local_dt, a pseudo-time iteration for the steady state): node s
+ * advances by dtn[s]; the fluxes then no longer telescope, so each step's result
+ * is multiplied by mass_ref / M(f^k), M of the step's input state, which keeps
+ * the mass of the iteration at mass_ref (a reading: the paper uses one time step). */
 long orc_run(const orc_problem *P, double *f, long nsteps, double *resid, double stop_below)
 {
     long n = 2L * nvel(P) * P->Nx;
@@ -409,7 +473,13 @@ long orc_run(const orc_problem *P, double *f, long nsteps, double *resid, double
     long k;
     for (k = 0; k < nsteps; ++k) {
         memcpy(prev, f, sizeof(double) * n);
-        orc_ssprk3(n, f, P->dt, problem_rhs, (void *)P);
+        if (P->local_dt) {
+            orc_ssprk3_nodal(n, P->Nx, f, P->dtn, problem_rhs, (void *)P);
+            double lam = P->mass_ref / orc_total_mass(P, prev);
+            for (long i = 0; i < n; ++i) f[i] *= lam;
+        } else {
+            orc_ssprk3(n, f, P->dt, problem_rhs, (void *)P);
+        }
         double r = 0;
         for (long i = 0; i < n; ++i) {
             int v = (int)((i / P->Nx) % nvel(P));

@@ -25,7 +25,7 @@ SRC = os.path.join(HERE, "lbc_oracle.c")
 DEFAULTS = dict(
     delta=1.0, u_left=0.0, u_right=0.0, T_left=1.0, T_right=1.0, Pr=2.0 / 3.0,
     omega=0.5, Nx=64, stretch_A=0.0, Qx=4, Qy=4, Nexp_x=0, Nexp_y=0, p0=1.0,
-    cfl=0.5, dt=0.0,
+    cfl=0.5, dt=0.0, local_dt=0, half_channel=0,
 )
 WENO_EPS = 1e-6
 MOMENT_NAMES = ("n", "u_x", "u_y", "T", "P_xx", "P_yy", "P_zz", "P_xy", "q_x", "q_y")
@@ -51,6 +51,7 @@ class _Problem(C.Structure):
         ("J", C.c_void_p), ("zx", C.c_void_p), ("wx", C.c_void_p), ("yy", C.c_void_p),
         ("wy", C.c_void_p), ("Phi", C.c_void_p), ("Phi_lo", C.c_void_p), ("He", C.c_void_p),
         ("He_lo", C.c_void_p),
+        ("local_dt", C.c_int), ("mirror", C.c_int), ("dtn", C.c_void_p), ("mass_ref", C.c_double),
     ]
 
 
@@ -81,6 +82,9 @@ def lib():
         L.orc_weno5.restype = C.c_double
         L.orc_weno5.argtypes = [C.c_double] * 6
         L.orc_ssprk3.argtypes = [C.c_long, dp, C.c_double, RHS_FN, C.c_void_p]
+        L.orc_ssprk3_nodal.argtypes = [C.c_long, C.c_int, dp, dp, RHS_FN, C.c_void_p]
+        L.orc_total_mass.restype = C.c_double
+        L.orc_total_mass.argtypes = [C.c_void_p, dp]
         _lib = L
     return _lib
 
@@ -89,13 +93,18 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def grid(Nx: int, A: float):
+def grid(Nx: int, A: float, half: bool = False):
     """Cell-centred nodes of the full channel x in [-1/2, 1/2] (L = 1).
 
     Eq. stretch: x(eta) = tanh(eta) / (2A) with equidistant eta on
     [-artanh A, artanh A]; the walls sit on the outer faces. A = 0 is the
     uniform grid (eta = x, J = 1). Returns x_s, J_s = dx/deta, deta.
+    half: the Nx nodes of the half channel 0 < x < 1/2, which are the right
+    half of the full channel's grid of 2 Nx nodes (the paper's S nodes).
     """
+    if half:
+        x, J, deta = grid(2 * Nx, A)
+        return x[Nx:].copy(), J[Nx:].copy(), deta
     s = np.arange(Nx) + 0.5
     if A == 0.0:
         deta = 1.0 / Nx
@@ -125,6 +134,15 @@ def time_step(p: dict, J: np.ndarray, deta: float, zmax: float, mu_ratio=None) -
     return dt
 
 
+def local_time_steps(p: dict, J: np.ndarray, deta: float, zmax: float, mu_ratio=None) -> np.ndarray:
+    """Per-node pseudo-time steps dt_s = min(cfl J_s deta / max|p_x|, tau_min / 2) (reading
+    for steady states: the time step above with the CFL bound taken at each node)."""
+    if p["dt"] > 0:
+        raise ValueError("local time steps are automatic: dt must be 0")
+    dt = p["cfl"] * J * deta / (p["p0"] * zmax)
+    return np.minimum(dt, time_step(dict(p, cfl=np.inf), J, deta, zmax, mu_ratio))
+
+
 class Oracle:
     """One Couette problem on the CPU, in FP64."""
 
@@ -139,7 +157,10 @@ class Oracle:
         self.tab = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in t.items()}
         self.Nx = int(p["Nx"])
         self.V = 2 * Qx * Qy
-        self.x, J, self.deta = grid(self.Nx, float(p["stretch_A"]))
+        self.half = bool(p["half_channel"])
+        if self.half and (p["T_left"] != p["T_right"] or p["u_left"] != -p["u_right"]):
+            raise ValueError("the half channel needs symmetric walls: T_left = T_right, u_left = -u_right")
+        self.x, J, self.deta = grid(self.Nx, float(p["stretch_A"]), self.half)
         self.J = np.ascontiguousarray(J)
         pr = _Problem()
         pr.Nx, pr.Qx, pr.Qy, pr.Nxe, pr.Nye = self.Nx, Qx, Qy, self.Nxe, self.Nye
@@ -156,8 +177,15 @@ class Oracle:
         pr.J = self.J.ctypes.data
         for k in ("zx", "wx", "yy", "wy", "Phi", "Phi_lo", "He", "He_lo"):
             setattr(pr, k, self.tab[k].ctypes.data)
+        pr.mirror = int(self.half)
+        self.dtn = None
+        if p["local_dt"]:
+            self.dtn = np.ascontiguousarray(
+                local_time_steps(p, self.J, self.deta, float(self.tab["zx"].max()), self.mu_ratio))
+            pr.local_dt, pr.dtn = 1, self.dtn.ctypes.data
         self.f = np.zeros((2, self.V, self.Nx))
         lib().orc_rest_state(C.byref(pr), _ptr(self.f))
+        pr.mass_ref = self.total_mass()
         self.steps = 0
 
     def mu_ratio(self, T: float) -> float:
@@ -185,7 +213,9 @@ class Oracle:
 
     # stepping -------------------------------------------------------------
     def set_state(self, f: np.ndarray) -> None:
+        """Installs a state; with local time steps its mass becomes the one the iteration keeps."""
         self.f = np.ascontiguousarray(f, dtype=np.float64).reshape(2, self.V, self.Nx).copy()
+        self._pr.mass_ref = self.total_mass()
 
     def run(self, nsteps: int, stop_below: float = 0.0) -> np.ndarray:
         """Advance up to nsteps RK-3 steps; returns the per-step residuals."""
@@ -224,9 +254,10 @@ class Oracle:
         lib().orc_target(C.byref(self._pr), _ptr(m), _ptr(tp), _ptr(tc))
         return tp, tc
 
-    def total_mass(self) -> float:
+    def total_mass(self, f: np.ndarray | None = None) -> float:
         """Sum_s J_s deta n_s (the discrete mass per unit wall area)."""
-        return float(np.sum(self.J * self.deta * self.moments()[0]))
+        f = self.f if f is None else np.ascontiguousarray(f, dtype=np.float64)
+        return lib().orc_total_mass(C.byref(self._pr), _ptr(f))
 
 
 def gx_bracket(N: int, zeta: float, T_over_2p02: float) -> np.ndarray:
@@ -239,6 +270,22 @@ def gx_bracket(N: int, zeta: float, T_over_2p02: float) -> np.ndarray:
 
 def weno5(a, b, c, d, e, eps=WENO_EPS) -> float:
     return lib().orc_weno5(a, b, c, d, e, eps)
+
+
+def ssprk3_nodal(y: np.ndarray, dtn: np.ndarray, fn) -> np.ndarray:
+    """One oracle RK-3 step of y' = fn(y), y of shape [..., Nx], node s stepping by dtn[s]."""
+    y = np.ascontiguousarray(y, dtype=np.float64).copy()
+    dtn = np.ascontiguousarray(dtn, dtype=np.float64)
+    n, shape = y.size, y.shape
+
+    def cb(_ctx, yp, dyp):
+        yy = np.ctypeslib.as_array(yp, shape=(n,))
+        dy = np.ctypeslib.as_array(dyp, shape=(n,))
+        dy[:] = np.asarray(fn(yy.copy().reshape(shape))).ravel()
+
+    f = RHS_FN(cb)
+    lib().orc_ssprk3_nodal(n, len(dtn), _ptr(y), _ptr(dtn), f, None)
+    return y
 
 
 def ssprk3(y: np.ndarray, dt: float, fn) -> np.ndarray:
