@@ -92,7 +92,31 @@ typedef struct {
     double cfl;              /* CFL number of the time step; 0 = 0.5 */
     double dt;               /* explicit time step; 0 = automatic (see lbc_create) */
     lbc_precision precision; /* LBC_FP64, or float32 state with float64 moment sums */
+    int local_dt;            /* 0: one time step for every node (time-accurate);
+                                1: local pseudo-time steps for steady states (below) */
+    int half_channel;        /* 0: the full channel -1/2 < x < 1/2 with Nx nodes;
+                                1: the half channel 0 < x < 1/2 with Nx nodes (below) */
 } lbc_params;
+
+/*
+ * Local pseudo-time steps (local_dt = 1; dt must be 0). Only the steady state
+ * is meaningful: node s advances by dt_s = min(cfl * J_s deta / max|p_x|,
+ * tau_min / 2), the automatic step below with the CFL bound taken at each node,
+ * so nodes in the coarse centre of a stretched grid take larger steps. The
+ * fluxes then no longer telescope, so after each step the state is multiplied
+ * by M_ref / M(f^n), where M(f) = sum_s J_s deta n_s is the mass of the step's
+ * input and M_ref the mass at creation or at the last set_state. The fixed
+ * point is the steady state of the global step with mass M_ref. The residual
+ * is that of the pseudo-time iteration. lbc_step_noalloc rejects local_dt.
+ *
+ * Half channel (half_channel = 1): walls of equal temperature moving at -u_w
+ * and +u_w (T_left = T_right, u_left = -u_right, else LBC_EINVAL). The flow
+ * then has the symmetry phi(-x, -p_x, -p_y) = phi(x, p_x, p_y) (Sec. II), and
+ * the solver integrates 0 < x < 1/2 only: Nx nodes, the right half of the
+ * full-channel grid of 2 Nx nodes (the paper's S = Nx), with the ghost nodes
+ * left of x = 0 taken from nodes 0, 1, 2 at the opposite velocity. States,
+ * moments, node positions and masses refer to those Nx nodes.
+ */
 
 /*
  * Creates a solver for one Couette problem and sets the rest Maxwellian

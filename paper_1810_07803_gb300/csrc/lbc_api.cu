@@ -61,6 +61,7 @@ struct lbc_batch {
     bool steady_mode = false;     // the device control blocks hold run-to-steady settings
     bool poisoned = false;        // some instance holds a NaN/Inf
     cudaGraphExec_t graph = nullptr;
+    bool ext = false;             // some instance uses the half channel or local steps
 };
 
 struct lbc_solver {
@@ -76,7 +77,7 @@ cudaError_t launch_steps_t(lbc_batch *b, int nsteps, cudaStream_t st)
         for (int stage = 0; stage < 3; ++stage) {
             cudaError_t e = b->single ? launch_stage<R>(b->inst[0], b->smem, stage, k, st)
                                       : launch_stage_batch<R>(b->d_inst, b->d_work, b->nwork, b->cluster, b->smem,
-                                                              stage, k, st);
+                                                              stage, k, b->ext, st);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -256,7 +257,10 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     char *tb = static_cast<char *>(b->table_block);
     b->d_inst = reinterpret_cast<Inst *>(tb + inst_off);
     b->d_work = reinterpret_cast<int2 *>(tb + work_off);
-    for (int i = 0; i < n; ++i) bind_tables(setup[i], ps[i], tb + toff[i], b->inst[i].T);
+    for (int i = 0; i < n; ++i) {
+        bind_tables(setup[i], ps[i], tb + toff[i], b->inst[i].T);
+        b->ext = b->ext || ps[i].half_channel || ps[i].local_dt;
+    }
 
     // ---- launch shape ----
     lbc_status st;
@@ -605,10 +609,10 @@ lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms)
             if (e == cudaSuccess)
                 e = b->fp32 ? (b->single ? launch_stage<float>(b->inst[0], b->smem, stage, (int)k, b->stream)
                                          : launch_stage_batch<float>(b->d_inst, b->d_work, b->nwork, b->cluster,
-                                                                     b->smem, stage, (int)k, b->stream))
+                                                                     b->smem, stage, (int)k, b->ext, b->stream))
                             : (b->single ? launch_stage<double>(b->inst[0], b->smem, stage, (int)k, b->stream)
                                          : launch_stage_batch<double>(b->d_inst, b->d_work, b->nwork, b->cluster,
-                                                                      b->smem, stage, (int)k, b->stream));
+                                                                      b->smem, stage, (int)k, b->ext, b->stream));
             if (e == cudaSuccess) e = cudaEventRecord(ev[j + 1], b->stream);
         }
     if (e == cudaSuccess) e = launch_ctl_bump(b->d_ctl, b->n, nsteps, b->stream);

@@ -19,7 +19,8 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kSubV = 16;          // velocities per pipeline stage (two per warp)
 constexpr int kPipe = 4;           // pipeline depth (stages in flight)
 constexpr int kEqM = 16;           // per-node stage data: n ux uy T qx qy 1/tau cS 1/(5T) 1/(J deta)
-                                   // Pxx Pyy Pzz Pxy, 2 pad (64 B per FP32 node: 16-byte-aligned bulk copies)
+                                   // Pxx Pyy Pzz Pxy dt_s, 1 pad (64 B per FP32 node: 16-byte-aligned bulk copies)
+constexpr int kMassHdr = 32;       // doubles before the per-node mass deviations in DevState::mass
 constexpr int kMaxVChunk = 256;    // velocities per CTA at most (per-velocity data is staged in smem)
 constexpr int kMaxCluster = 16;    // chunk CTAs of a tile form one thread-block cluster (non-portable size 16)
 constexpr int kMaxV = kMaxCluster * kMaxVChunk;   // largest velocity set 2 Qx Qy
@@ -42,6 +43,9 @@ struct DevTables {
     int Nx, Nxp, Qx, Qy, Nxe, Nye, K, V;
     int ntile, nchunk, vchunk;
     int law, tab_n;                // viscosity law (LBC_MU_POWER / LBC_MU_TABLE), table entries
+    int lts;                       // local pseudo-time steps with mass renormalisation (local_dt)
+    int half;                      // half channel: symmetry plane at x = 0 instead of the left wall
+    double mrest;                  // sum_s J_s deta (the mass of the rest state n = 1)
     double p0, dt, delta, Pr, omega, TL, TR;
     double inL, inR;               // sum_{incoming} p_x w_v fw_v (signed) for a unit wall density
     double restOutL, restOutR;     // sum_{outgoing} p_x w_v ft_rest_v at each wall
@@ -50,6 +54,9 @@ struct DevTables {
     double dsc[kNumSc];
     float fsc[kNumSc];
     const double *inv_jdeta;       // [Nx] 1/(J_s deta)
+    const double *jdeta;           // [Nx] J_s deta
+    const double *dtn;             // [Nx] time step of node s (the global dt unless lts)
+    const float *f_dtn;
     const double *zx, *wx, *yy, *wy;
     const double *alpha, *sbeta;   // orthonormal recurrence of h_l
     const double *hz;              // [Nxe+1][Qx]
@@ -128,6 +135,8 @@ struct DevState {
     unsigned long long *resid;   // [kResidRing] per-step residual (bits of a double >= 0)
     Ctl *ctl;
     double *mom_out;       // [LBC_NMOM][Nxp] scratch for lbc_moments
+    double *mass;          // local steps: [0] reference mass minus the rest mass; from kMassHdr on,
+                           // [2][Nxp] J_s deta (n_s - 1) of buffer 0 after steps of parity 0 / 1
 };
 
 // TMA descriptors of the state buffers, viewed as 2-D [V rows][2 Nxp columns].
@@ -149,8 +158,8 @@ struct alignas(128) Inst {
 struct ProblemSetup {
     HostTables t;
     int Nxe = 0, Nye = 0;
-    std::vector<double> x, inv_jdeta;
-    double deta = 0, min_jdeta = 0, dt = 0;
+    std::vector<double> x, jdeta, inv_jdeta, dtn;   // dtn: time step per node
+    double deta = 0, min_jdeta = 0, dt = 0, mrest = 0;
     std::vector<double> fwL, fwR, frest, vel, isb, invl, vrow, eqtab;
     std::vector<double> tabT, tabMu, tabW, tabPr;   // table viscosity law: mu_n / mu(T_ref), exponents
     std::vector<int> aj;
@@ -197,11 +206,14 @@ template <typename R>
 cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStream_t st);
 // One RK stage of every work item: grid (nwork, cluster), cluster dims (1, cluster, 1);
 // work[i] = (instance, tile) with descriptors in device memory, instance < 0 for an empty slot.
+// ext: some instance uses the half channel or local steps (the kernel form that has them).
 template <typename R>
 cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, int cluster, size_t smem, int stage,
-                               int rel, cudaStream_t st);
+                               int rel, bool ext, cudaStream_t st);
 template <typename R>
 cudaError_t launch_moments_partial(const DevTables &T, const DevState &S, int buf, cudaStream_t st);
+// Stage data of buffer `buf` from the chunk partials of launch_moments_partial; for
+// buffer 0 with local steps also the mass deviations and the reference mass.
 template <typename R>
 cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int buf, cudaStream_t st);
 // Moments of buffer 0 (FP64, [LBC_NMOM][Nxp] in S.mom_out) from its stage data.
@@ -222,7 +234,7 @@ inline size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 // Device bytes of one instance's state (partials sized for the largest cluster, so
 // a launch shape can change without reallocating).
 struct StateSizes {
-    size_t f, eqm, eqg, part, resid, mom, total;
+    size_t f, eqm, eqg, part, resid, mom, mass, total;
     StateSizes(const DevTables &T, bool fp32)
     {
         const size_t esz = fp32 ? sizeof(float) : sizeof(double);
@@ -232,7 +244,8 @@ struct StateSizes {
         part = round256((size_t)kMaxCluster * kNumRaw * T.Nxp * esz);
         resid = kResidRing * sizeof(unsigned long long);
         mom = round256((size_t)LBC_NMOM * T.Nxp * sizeof(double));
-        total = 3 * (f + eqm + eqg) + part + resid + mom;
+        mass = round256((kMassHdr + 2 * (size_t)T.Nxp) * sizeof(double));
+        total = 3 * (f + eqm + eqg) + part + resid + mom + mass;
     }
     // Points the state arrays of S into `base` (total bytes); S.ctl is set by the caller.
     void carve(char *base, DevState &S) const
@@ -243,7 +256,8 @@ struct StateSizes {
         for (int k = 0; k < 3; ++k) { S.eqg[k] = p; p += eqg; }
         S.part = p; p += part;
         S.resid = reinterpret_cast<unsigned long long *>(p); p += resid;
-        S.mom_out = reinterpret_cast<double *>(p);
+        S.mom_out = reinterpret_cast<double *>(p); p += mom;
+        S.mass = reinterpret_cast<double *>(p);
     }
 };
 

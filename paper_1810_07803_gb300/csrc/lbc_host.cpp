@@ -276,31 +276,31 @@ void equilibrium_host(const HostTables &t, double ux, double uy, double T, doubl
     }
 }
 
-// Full-channel grid, Eq. stretch: x = tanh(eta)/(2A), equidistant cell-centred
-// eta on [-artanh A, artanh A]; A = 0 is the uniform grid (eta = x, J = 1).
-void make_grid(int Nx, double A, std::vector<double> &x, std::vector<double> &inv_jdeta,
-               double &deta, double &min_jdeta)
+// Grid of Eq. stretch: x = tanh(eta)/(2A), equidistant cell-centred eta on
+// [-artanh A, artanh A]; A = 0 is the uniform grid (eta = x, J = 1). half: the
+// Nx nodes of 0 < x < 1/2, which are the right half of the full grid of 2 Nx nodes.
+void make_grid(int Nx, double A, bool half, std::vector<double> &x, std::vector<double> &jdeta,
+               std::vector<double> &inv_jdeta, double &deta, double &min_jdeta)
 {
+    const int Nf = half ? 2 * Nx : Nx, s0 = half ? Nx : 0;
     x.resize(Nx);
+    jdeta.resize(Nx);
     inv_jdeta.resize(Nx);
     min_jdeta = 1e300;
-    if (A == 0.0) {
-        deta = 1.0 / Nx;
-        for (int s = 0; s < Nx; ++s) {
-            x[s] = -0.5 + (s + 0.5) * deta;
-            inv_jdeta[s] = 1.0 / deta;
+    const double ew = A == 0.0 ? 0.5 : std::atanh(A);
+    deta = 2.0 * ew / Nf;
+    for (int k = 0; k < Nx; ++k) {
+        const double eta = -ew + (s0 + k + 0.5) * deta;
+        double J = 1.0;
+        if (A == 0.0) {
+            x[k] = eta;
+        } else {
+            const double c = std::cosh(eta);
+            J = 1.0 / (2.0 * A * c * c);
+            x[k] = std::tanh(eta) / (2.0 * A);
         }
-        min_jdeta = deta;
-        return;
-    }
-    double ew = std::atanh(A);
-    deta = 2.0 * ew / Nx;
-    for (int s = 0; s < Nx; ++s) {
-        double eta = -ew + (s + 0.5) * deta;
-        double c = std::cosh(eta);
-        double J = 1.0 / (2.0 * A * c * c);
-        x[s] = std::tanh(eta) / (2.0 * A);
-        inv_jdeta[s] = 1.0 / (J * deta);
+        jdeta[k] = J * deta;
+        inv_jdeta[k] = 1.0 / (J * deta);
         min_jdeta = std::min(min_jdeta, J * deta);
     }
 }

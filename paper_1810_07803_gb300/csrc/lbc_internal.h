@@ -43,9 +43,10 @@ bool build_tables(int Qx, int Qy, int Nxe, int Nye, double p0, HostTables &t, st
 // Discrete equilibrium factors on the host (same algorithm as the device).
 void equilibrium_host(const HostTables &t, double ux, double uy, double T, double *gx, double *gy);
 
-// Grid (Eq. stretch over the full channel): x_s, 1/(J_s deta), deta.
-void make_grid(int Nx, double A, std::vector<double> &x, std::vector<double> &inv_jdeta,
-               double &deta, double &min_jdeta);
+// Grid (Eq. stretch over the full channel, or its right half): x_s, J_s deta,
+// 1/(J_s deta), deta, min_s J_s deta.
+void make_grid(int Nx, double A, bool half, std::vector<double> &x, std::vector<double> &jdeta,
+               std::vector<double> &inv_jdeta, double &deta, double &min_jdeta);
 
 void set_error(const std::string &msg);
 

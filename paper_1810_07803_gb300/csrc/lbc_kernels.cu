@@ -44,6 +44,7 @@ template <> struct Tabs<double> {
     __device__ static const double *Yk(const DevTables &T) { return T.Yk; }
     __device__ static const double *Wk(const DevTables &T) { return T.Wk; }
     __device__ static const double *ijd(const DevTables &T) { return T.inv_jdeta; }
+    __device__ static const double *dtn(const DevTables &T) { return T.dtn; }
     __device__ static double sbeta(const DevTables &T, int l) { return T.sbeta[l]; }
     __device__ static double isbeta(const DevTables &T, int l) { return 1.0 / T.sbeta[l]; }
     __device__ static double inv_l(const DevTables &, int l) { return 1.0 / l; }
@@ -60,6 +61,7 @@ template <> struct Tabs<float> {
     __device__ static const float *Yk(const DevTables &T) { return T.f_Yk; }
     __device__ static const float *Wk(const DevTables &T) { return T.f_Wk; }
     __device__ static const float *ijd(const DevTables &T) { return T.f_inv_jdeta; }
+    __device__ static const float *dtn(const DevTables &T) { return T.f_dtn; }
     __device__ static float sbeta(const DevTables &T, int l) { return T.f_sbeta[l]; }
     __device__ static float isbeta(const DevTables &T, int l) { return T.f_isbeta[l]; }
     __device__ static float inv_l(const DevTables &T, int l) { return T.f_inv_l[l]; }
@@ -435,14 +437,15 @@ __device__ __forceinline__ void dot_combine(Dot<R> &d, int o)
 // shf[1][c] = s_y. Adds the rest state's share, turns the sums into moments,
 // and builds the discrete equilibrium factors of Eqs. gx, gy (algorithm: see
 // equilibrium_host). Writes eqm[buf] of the nodes and their columns of the
-// tile's eqg[buf] block.
+// tile's eqg[buf] block; dm_a, dm_b (either may be NULL) receive each node's
+// mass deviation J_s deta (n_s - 1) (local steps, buffer 0).
 // Organised for latency: tables are read from shared memory, and every phase
 // spreads over all threads of the block (recurrences per (node, projection
 // node), dot products over 4 lanes per (node, order), factors per (node,
 // velocity)).
 template <typename R>
 __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf, int tile, int cfirst, int cstep,
-                                 int nn, int ncap, unsigned char *scratch)
+                                 int nn, int ncap, unsigned char *scratch, double *dm_a, double *dm_b)
 {
     const int tid = threadIdx.x, c0 = tile * kTile;
     const int N = T.Nxe, K = T.K, G = 2 * T.Qx + T.Qy, Ny = T.Nye;
@@ -472,6 +475,11 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
 #pragma unroll
             for (int k = 0; k < kNumRaw; ++k) rr[k] += raw[tid * kNumRaw + k];
             raw_to_moments_r<R>(rr, sx, sy, m);
+            if (dm_a || dm_b) {   // the deviation's own S0 is n_s - 1 (the rest state has n = 1)
+                const double dm = T.jdeta[s] * (double)raw[tid * kNumRaw + R_S0];
+                if (dm_a) dm_a[s] = dm;
+                if (dm_b) dm_b[s] = dm;
+            }
             // a NaN/Inf anywhere in the node's populations reaches its moments
             if (!isfinite(m[0]) || !isfinite(m[3]) || !isfinite(m[8]) || !isfinite(m[9]) || !(m[0] > R(0)) ||
                 !(m[3] > R(0)))
@@ -503,7 +511,7 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             R *e = eqm + (size_t)s * kEqM;
             e[0] = n; e[1] = ux; e[2] = uy; e[3] = Tc; e[4] = m[8]; e[5] = m[9];
             e[6] = nu; e[7] = cS; e[8] = R(1) / (R(5) * Tc); e[9] = Tabs<R>::ijd(T)[s];
-            e[10] = m[4]; e[11] = m[5]; e[12] = m[6]; e[13] = m[7];
+            e[10] = m[4]; e[11] = m[5]; e[12] = m[6]; e[13] = m[7]; e[14] = Tabs<R>::dtn(T)[s];
         }
         const R ip0 = Tabs<R>::sc(T, SC_IP0), Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
         R *x = sc + tid * 8;   // sT a a^2/2 u'_y T'-1
@@ -645,6 +653,22 @@ __device__ void block_wall_density(const DevTables &T, const R *phi, bool right,
     __syncthreads();
 }
 
+// sum_{s < Nx} dm[s] by the whole block (256 threads) in a fixed order, so that
+// every CTA that sums the same data obtains the same bits. red: 8 doubles of
+// shared scratch. Returns the sum in every thread.
+__device__ double block_mass_deviation(const double *dm, int Nx, double *red)
+{
+    double acc = 0.0;
+    for (int s = threadIdx.x; s < Nx; s += kThreads) acc += dm[s];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < kWarps; ++k) t += red[k];
+    __syncthreads();
+    return t;
+}
+
 // Dynamic shared memory layout of the stage kernel. The pipeline region is
 // reused after the main loop for the moment reduction and the node stage data
 // (EqScratch); `xch` receives the moment partials that the cluster's CTAs send
@@ -676,8 +700,10 @@ struct Layout {
 };
 
 // One RK stage of tile `tile` of instance I, for the CTA's velocity chunk
-// blockIdx.y (body of both stage kernels below).
-template <typename R>
+// blockIdx.y (body of both stage kernels below). kExt compiles in the half
+// channel's symmetry plane and the local steps with mass renormalisation
+// (instances without them give the same results in either form).
+template <typename R, bool kExt>
 __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, int rel)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
@@ -772,20 +798,30 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     R *Fout = static_cast<R *>(S.F[out]);
 
     // ---- (2) wall densities (tiles whose stencil reaches a wall), while the copies land ----
-    const bool needL = c0 == 0;
+    const bool mirror = kExt && c0 == 0 && T.half != 0;   // half channel: symmetry plane at x = 0
+    const bool needL = c0 == 0 && !mirror;
     const bool needR = c0 + 33 >= T.Nx;
     if (needL) block_wall_density<R>(T, Fin, false, s_misc, &s_misc[8]);
     if (needR) block_wall_density<R>(T, Fin, true, s_misc, &s_misc[9]);
+    // local steps: this step's mass correction lambda - 1 = (M_ref - M(f^n)) / M(f^n), from the
+    // mass deviations of f^n that the previous step (or the set-up) left for this step's parity
+    const bool renorm = kExt && T.lts != 0 && stage == 2;
+    double lam1 = 0.0;
+    if (renorm) {
+        const double dM = block_mass_deviation(S.mass + kMassHdr + (size_t)(step & 1) * T.Nxp, T.Nx, s_misc);
+        lam1 = (S.mass[0] - dM) / (T.mrest + dM);
+    }
     bool timed_out = __syncthreads_or(!mbar_wait(bar_data, 0));
 
     const int s = c0 + lane;
     const bool active = lane < nloc;
     R n_c = R(1), ux_c = R(0), uy_c = R(0), T_c = R(1), qx_c = R(0), qy_c = R(0), nu_c = R(0), cS_c = R(0),
-      i5T = R(0.2), ijd = R(0);
+      i5T = R(0.2), ijd = R(0), dt = R(0);
     if (active && !timed_out) {
         const R *e = s_eqm + lane * kEqM;
         n_c = e[0]; ux_c = e[1]; uy_c = e[2]; T_c = e[3]; qx_c = e[4]; qy_c = e[5];
         nu_c = e[6]; cS_c = e[7]; i5T = e[8]; ijd = e[9];
+        dt = kExt ? e[14] : Tabs<R>::sc(T, SC_DT);   // the node's time step (the global one unless lts)
     }
     const R nwL = R(needL ? s_misc[8] : 0.0), nwR = R(needR ? s_misc[9] : 0.0);
 
@@ -793,8 +829,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     // pipeline slot; the last warp to release a slot issues its refill ----
     const R ca = R(stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0));
     const R cb = R(stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0));
-    const R dt = Tabs<R>::sc(T, SC_DT);
     const bool wall = needL || needR;
+    const R lam1r = R(lam1);
     const int ck = lane + 3 + off;          // node column of node c0 + lane
     const int Nxp = T.Nxp, Nx = T.Nx;
     R *Fout_s = Fout + 2 * (size_t)s;       // this lane's node in row v: Fout_s + 2 Nxp v
@@ -805,6 +841,24 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     R res = R(0);
     constexpr int NQ = kSubV / kWarps;      // rows per warp and slot: rows warp + kWarps q
     bool my_timeout = false;
+
+    // half channel: the ghost nodes -1, -2, -3 of velocity v are nodes 0, 1, 2 of the opposite
+    // velocity (Sec. II symmetry), read from the stage input one pipeline slot ahead: lane
+    // 3 q + g holds node g of the partner of row warp + kWarps q (both fields)
+    R mg0 = R(0), mg1 = R(0);
+    auto mirror_fetch = [&](int sub) {
+        if (lane < 3 * NQ && sub < nsub) {
+            const int q = lane / 3, g = lane - 3 * q, v = vbeg + sub * kSubV + warp + kWarps * q;
+            if (v < vend) {
+                const int a = v / T.Qy, j = v - a * T.Qy;
+                const int vm = (a < T.Qx ? a + T.Qx : a - T.Qx) * T.Qy + (T.Qy - 1 - j);
+                const R *src = Fin + 2 * ((size_t)vm * T.Nxp + g);
+                mg0 = src[0];
+                mg1 = src[1];
+            }
+        }
+    };
+    if (mirror) mirror_fetch(0);
 
     for (int sub = 0; sub < nsub && !timed_out; ++sub) {
         const int p = sub % kPipe;
@@ -871,6 +925,22 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
             }
             __syncwarp();
         }
+        if (mirror) {
+            if (lane < 3 * NQ) {
+                const int q = lane / 3, g = lane - 3 * q;
+                bool okq = ok[0];
+#pragma unroll
+                for (int qq = 1; qq < NQ; ++qq)
+                    if (q == qq) okq = ok[qq];
+                if (okq) {
+                    R *gp = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen + 2 * (-1 - g - x0);   // node -1 - g
+                    gp[0] = mg0;
+                    gp[1] = mg1;
+                }
+            }
+            __syncwarp();
+            mirror_fetch(sub + 1);
+        }
         if constexpr (std::is_same<R, float>::value) {
             // FP32: (phi, chi) as packed pairs, loaded and stored as one 64-bit access each
             f2 fl[NQ], dd[NQ];
@@ -887,8 +957,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                 dd[q] = pos ? v[3] : v[2];                        // the node itself
                 if (wall) {
                     const float4 xw = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow + 4);
-                    if (pos && s == 0) fl[q] = mk2(nwL * xw.x - xa.w, nwL * xw.y - xa.w);
-                    if (!pos && s == Nx) fl[q] = mk2(nwR * xw.z - xa.w, nwR * xw.w - xa.w);
+                    if (needL && pos && s == 0) fl[q] = mk2(nwL * xw.x - xa.w, nwL * xw.y - xa.w);
+                    if (needR && !pos && s == Nx) fl[q] = mk2(nwR * xw.z - xa.w, nwR * xw.w - xa.w);
                 }
             }
 #pragma unroll
@@ -913,6 +983,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                 if (stage > 0) {
                     const f2 d0 = ld2(f0 + (size_t)r * 2 * kF0Len + 2 * (lane + offf));
                     dn = fma2(bc2(ca), d0, bc2(cb) * dn);
+                    if (renorm) dn = fma2(bc2(lam1r), dn + bc2(fr), dn);   // lambda (d + ft_rest) - ft_rest
                     if (stage == 2 && active && ok[q]) {
                         float e0, e1;
                         un2(dn - d0, e0, e1);
@@ -958,8 +1029,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                     fl[q][fld] = weno5<R>(v[0][fld], v[1][fld], v[2][fld], v[3][fld], v[4][fld]);
                     dd[q][fld] = pos ? v[3][fld] : v[2][fld];
                     if (wall) {
-                        if (pos && s == 0) fl[q][fld] = nwL * x[VR_FWL + fld] - x[VR_FR];
-                        if (!pos && s == Nx) fl[q][fld] = nwR * x[VR_FWR + fld] - x[VR_FR];
+                        if (needL && pos && s == 0) fl[q][fld] = nwL * x[VR_FWL + fld] - x[VR_FR];
+                        if (needR && !pos && s == Nx) fl[q][fld] = nwR * x[VR_FWR + fld] - x[VR_FR];
                     }
                 }
             }
@@ -989,6 +1060,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                     if (stage > 0) {
                         const R b0 = fld ? d0.y : d0.x;
                         dn = ca * b0 + cb * dn;
+                        if (renorm) dn = fma(lam1r, dn + fr, dn);   // lambda (d + ft_rest) - ft_rest
                         if (stage == 2 && active && ok[q]) res = fmax(res, w * fabs(dn - b0));
                     }
                     fo[fld] = dn;
@@ -1091,28 +1163,30 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
         if (tid == 0) atomicExch(&ctl->timeout, 1);
         return;
     }
-    node_equilibrium<R>(T, S, out, tile, rank, nch, nn, ncap, scr);
+    // local steps: the mass deviations of f^{n+1} (buffer 0) for the next step's parity
+    double *dm = renorm ? S.mass + kMassHdr + (size_t)((step + 1) & 1) * T.Nxp : nullptr;
+    node_equilibrium<R>(T, S, out, tile, rank, nch, nn, ncap, scr, dm, nullptr);
 }
 
 // Single instance: the descriptor is a kernel parameter (constant bank), grid (ntile, nchunk).
-template <typename R>
+template <typename R, bool kExt>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
 stage_kernel(const __grid_constant__ Inst I, int stage, int rel)
 {
-    stage_body<R>(I, blockIdx.x, stage, rel);
+    stage_body<R, kExt>(I, blockIdx.x, stage, rel);
 }
 
 // Batch: descriptors in device memory, one cluster per work item (instance, tile).
 // Three CTAs per SM in FP32: the descriptor fields live in registers here (in the
 // single-instance kernel they are constant-bank operands), and measured on GB300
 // the unspilled 3-CTA form is faster than a spilling 4-CTA form.
-template <typename R>
+template <typename R, bool kExt>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
 stage_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int stage, int rel)
 {
     const int2 wk = work[blockIdx.x];
     if (wk.x < 0) return;   // empty work slot: the whole cluster leaves
-    stage_body<R>(insts[wk.x], wk.y, stage, rel);
+    stage_body<R, kExt>(insts[wk.x], wk.y, stage, rel);
 }
 
 // Stage data of every tile of buffer `buf` from the chunk partials of
@@ -1139,7 +1213,18 @@ tile_equilibrium_kernel(const __grid_constant__ DevTables T, const __grid_consta
     }
     if (threadIdx.x < 2 * kLanes) shf[threadIdx.x] = R(0);   // the partials are sums about p = 0
     __syncthreads();
-    node_equilibrium<R>(T, S, buf, blockIdx.x, 0, 1, kTile, kTile, smem_eq);
+    // local steps: buffer 0's mass deviations serve the next step of either parity
+    double *dm = T.lts && buf == 0 ? S.mass + kMassHdr : nullptr;
+    node_equilibrium<R>(T, S, buf, blockIdx.x, 0, 1, kTile, kTile, smem_eq, dm, dm ? dm + T.Nxp : nullptr);
+}
+
+// Local steps: the reference mass deviation M_ref - sum_s J_s deta of a freshly
+// installed state, summed exactly as the stage kernel sums M(f^n) - sum_s J_s deta.
+__global__ void __launch_bounds__(kThreads) mass_reference_kernel(const double *dm, int Nx, double *ref)
+{
+    __shared__ double red[kWarps];
+    const double t = block_mass_deviation(dm, Nx, red);
+    if (threadIdx.x == 0) *ref = t;
 }
 
 // Raw moment sums (about p = 0) of the deviation in buffer `buf`, per velocity
@@ -1246,12 +1331,12 @@ cudaError_t configure_kernels()
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(stage_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(stage_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(stage_batch_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const void *stage_fns[4] = {(const void *)stage_kernel<R, false>, (const void *)stage_kernel<R, true>,
+                                (const void *)stage_batch_kernel<R, false>, (const void *)stage_batch_kernel<R, true>};
+    for (const void *fn : stage_fns) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tile_equilibrium_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     return e;
@@ -1287,13 +1372,14 @@ cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStr
 {
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = cluster_config((unsigned)I.T.ntile, I.T.nchunk, smem, st, at);
-    return cudaLaunchKernelEx(&cfg, stage_kernel<R>, I, stage, rel);
+    if (I.T.half || I.T.lts) return cudaLaunchKernelEx(&cfg, stage_kernel<R, true>, I, stage, rel);
+    return cudaLaunchKernelEx(&cfg, stage_kernel<R, false>, I, stage, rel);
 }
 
 // One cluster per work item (instance, tile): its `cluster` chunk CTAs (cluster dimension y).
 template <typename R>
 cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, int cluster, size_t smem, int stage,
-                               int rel, cudaStream_t st)
+                               int rel, bool ext, cudaStream_t st)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nwork, (unsigned)cluster, 1);
@@ -1307,7 +1393,8 @@ cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, i
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R>, insts, work, stage, rel);
+    if (ext) return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true>, insts, work, stage, rel);
+    return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false>, insts, work, stage, rel);
 }
 
 template <typename R>
@@ -1325,14 +1412,16 @@ cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, int *ncl
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return batch ? cudaOccupancyMaxActiveClusters(nclusters, stage_batch_kernel<R>, &cfg)
-                 : cudaOccupancyMaxActiveClusters(nclusters, stage_kernel<R>, &cfg);
+    // both forms of a kernel have the same launch bounds and shared memory: the plain one stands for both
+    return batch ? cudaOccupancyMaxActiveClusters(nclusters, stage_batch_kernel<R, false>, &cfg)
+                 : cudaOccupancyMaxActiveClusters(nclusters, stage_kernel<R, false>, &cfg);
 }
 
 template <typename R>
 cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int buf, cudaStream_t st)
 {
     tile_equilibrium_kernel<R><<<T.ntile, kThreads, EqScratch<R>(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, T.tab_n).total, st>>>(T, S, buf);
+    if (T.lts && buf == 0) mass_reference_kernel<<<1, kThreads, 0, st>>>(S.mass + kMassHdr, T.Nx, S.mass);
     return cudaGetLastError();
 }
 
@@ -1385,7 +1474,8 @@ cudaError_t launch_last_residuals(const Inst *insts, const int *slots, int n, do
     template size_t stage_smem_bytes<R>(int, int, int, int, int, int, int, int);                                     \
     template cudaError_t configure_kernels<R>();                                                                \
     template cudaError_t launch_stage<R>(const Inst &, size_t, int, int, cudaStream_t);                          \
-    template cudaError_t launch_stage_batch<R>(const Inst *, const int2 *, int, int, size_t, int, int, cudaStream_t); \
+    template cudaError_t launch_stage_batch<R>(const Inst *, const int2 *, int, int, size_t, int, int, bool,       \
+                                               cudaStream_t);                                                    \
     template cudaError_t launch_tile_equilibrium<R>(const DevTables &, const DevState &, int, cudaStream_t);     \
     template cudaError_t launch_moments_partial<R>(const DevTables &, const DevState &, int, cudaStream_t);      \
     template cudaError_t stage_active_clusters<R>(size_t, int, bool, int *);                                          \

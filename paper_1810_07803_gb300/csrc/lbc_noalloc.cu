@@ -151,6 +151,8 @@ extern "C" lbc_status lbc_step_noalloc(const lbc_params *params, double *d_state
     int Nxe = 0, Nye = 0;
     lbc_status st = validate(p, Nxe, Nye);
     if (st != LBC_OK) return st;
+    if (p.local_dt)   // the mass reference of local steps would not survive from one call to the next
+        return fail_na(LBC_EINVAL, "local_dt is not available on the allocation-free path");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     return p.precision == LBC_FP32_STATE ? run_noalloc<float>(p, Nxe, Nye, d_state, nsteps, stream)
                                          : run_noalloc<double>(p, Nxe, Nye, d_state, nsteps, stream);

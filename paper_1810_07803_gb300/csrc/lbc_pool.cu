@@ -67,6 +67,7 @@ struct lbc_pool {
     double *h_last = nullptr;    // pinned [cap]
     int *h_bad = nullptr;
     int nwork = 0;
+    bool ext = false;            // some active instance uses the half channel or local steps
     std::vector<int> active;     // slots in the work list
 };
 
@@ -93,6 +94,8 @@ lbc_status rebuild_work(lbc_pool *P)
     if ((int)work.size() > P->max_tiles) return fail(LBC_ENOMEM, "pool work list full");
     P->nwork = (int)work.size();
     P->active = order;
+    P->ext = false;
+    for (int s : order) P->ext = P->ext || P->inst[s].T.half || P->inst[s].T.lts;
     // pageable sources: the copies are complete (staged) when cudaMemcpyAsync returns
     if (!work.empty())
         POOL_TRY(cudaMemcpyAsync(P->d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, P->stream));
@@ -108,7 +111,7 @@ cudaError_t pool_steps(lbc_pool *P, long nsteps, size_t smem)
     for (long k = 0; k < nsteps; ++k)
         for (int stage = 0; stage < 3; ++stage) {
             cudaError_t e = launch_stage_batch<R>(P->d_inst, P->d_work, P->nwork, P->cluster, smem, stage, (int)k,
-                                                  P->stream);
+                                                  P->ext, P->stream);
             if (e != cudaSuccess) return e;
         }
     return launch_ctl_bump(P->d_ctl, P->cap, nsteps, P->stream);

@@ -55,6 +55,11 @@ lbc_status validate(const lbc_params &p, int &Nxe, int &Nye)
         return fail(LBC_EINVAL, "unknown viscosity law");
     }
     if (!std::isfinite(p.omega)) return fail(LBC_EINVAL, "omega must be finite");
+    if (p.local_dt != 0 && p.local_dt != 1) return fail(LBC_EINVAL, "local_dt must be 0 or 1");
+    if (p.local_dt && p.dt > 0.0) return fail(LBC_EINVAL, "local time steps are automatic: dt must be 0");
+    if (p.half_channel != 0 && p.half_channel != 1) return fail(LBC_EINVAL, "half_channel must be 0 or 1");
+    if (p.half_channel && (p.T_left != p.T_right || p.u_left != -p.u_right))
+        return fail(LBC_EINVAL, "the half channel needs symmetric walls: T_left = T_right, u_left = -u_right");
     if (p.precision != LBC_FP64 && p.precision != LBC_FP32_STATE) return fail(LBC_EINVAL, "unknown precision");
     return LBC_OK;
 }
@@ -68,7 +73,7 @@ struct FPiece { const std::vector<double> *src; const float **dst; };
 std::vector<DPiece> dpieces(const ProblemSetup &ps, DevTables &T)
 {
     const HostTables &t = ps.t;
-    return {{&ps.inv_jdeta, &T.inv_jdeta}, {&t.zx, &T.zx}, {&t.wx, &T.wx}, {&t.yy, &T.yy}, {&t.wy, &T.wy},
+    return {{&ps.inv_jdeta, &T.inv_jdeta}, {&ps.jdeta, &T.jdeta}, {&ps.dtn, &T.dtn}, {&t.zx, &T.zx}, {&t.wx, &T.wx}, {&t.yy, &T.yy}, {&t.wy, &T.wy},
             {&t.alpha, &T.alpha}, {&t.sbeta, &T.sbeta}, {&t.hz, &T.hz}, {&t.Yk, &T.Yk}, {&t.Wk, &T.Wk},
             {&t.He, &T.He}, {&ps.fwL, &T.fwL}, {&ps.fwR, &T.fwR}, {&ps.frest, &T.frest}, {&ps.vel, &T.d_vel},
             {&ps.vrow, &T.d_vrow}, {&ps.eqtab, &T.d_eqtab}};
@@ -78,7 +83,8 @@ std::vector<FPiece> fpieces(const ProblemSetup &ps, DevTables &T)
     const HostTables &t = ps.t;
     return {{&t.hz, &T.f_hz}, {&t.He, &T.f_He}, {&t.alpha, &T.f_alpha}, {&ps.isb, &T.f_isbeta},
             {&t.sbeta, &T.f_sbeta}, {&t.Yk, &T.f_Yk}, {&t.Wk, &T.f_Wk}, {&ps.invl, &T.f_inv_l},
-            {&ps.vel, &T.f_vel}, {&ps.inv_jdeta, &T.f_inv_jdeta}, {&ps.vrow, &T.f_vrow}, {&ps.eqtab, &T.f_eqtab}};
+            {&ps.vel, &T.f_vel}, {&ps.inv_jdeta, &T.f_inv_jdeta}, {&ps.vrow, &T.f_vrow}, {&ps.eqtab, &T.f_eqtab},
+            {&ps.dtn, &T.f_dtn}};
 }
 size_t pad_d(size_t n) { return (n + 31) / 32 * 32; }
 size_t pad_f(size_t n) { return (n + 63) / 64 * 64; }
@@ -95,7 +101,9 @@ bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std:
         err = "velocity set 2 Qx Qy = " + std::to_string(V) + " exceeds " + std::to_string(kMaxV);
         return false;
     }
-    make_grid(p.Nx, p.stretch_A, ps.x, ps.inv_jdeta, ps.deta, ps.min_jdeta);
+    make_grid(p.Nx, p.stretch_A, p.half_channel != 0, ps.x, ps.jdeta, ps.inv_jdeta, ps.deta, ps.min_jdeta);
+    ps.mrest = 0.0;
+    for (double j : ps.jdeta) ps.mrest += j;
 
     // table viscosity law (Eqs. mun, interp): segment exponents omega_n, and mu_n
     // divided by mu(T_ref = 1), the viscosity that defines delta
@@ -124,12 +132,19 @@ bool setup_problem(const lbc_params &p, int Nxe, int Nye, ProblemSetup &ps, std:
     }
 
     // time step: CFL on the smallest cell, and half the smallest relaxation time
-    // tau = (mu(T)/mu(T_ref)) / (n T delta sqrt(2)) at n = 1 (Eq. tau)
+    // tau = (mu(T)/mu(T_ref)) / (n T delta sqrt(2)) at n = 1 (Eq. tau); local
+    // steps take the CFL bound of each node
     double dt = p.dt > 0 ? p.dt : p.cfl * ps.min_jdeta / (t.zx.back() * p.p0);
+    double dt_coll = 1e300;
     if (p.dt <= 0 && p.delta > 0)
         for (double Tw : {1.0, p.T_left, p.T_right})
-            dt = std::min(dt, 0.5 * mu_of(Tw) / (Tw * p.delta * std::sqrt(2.0)));
+            dt_coll = std::min(dt_coll, 0.5 * mu_of(Tw) / (Tw * p.delta * std::sqrt(2.0)));
+    dt = std::min(dt, dt_coll);
     ps.dt = dt;
+    ps.dtn.assign(p.Nx, dt);
+    if (p.local_dt)
+        for (int s = 0; s < p.Nx; ++s)
+            ps.dtn[s] = std::min(p.cfl * ps.jdeta[s] / (t.zx.back() * p.p0), dt_coll);
 
     // wall Maxwellians (unit density), incoming unit fluxes, rest Maxwellian
     std::vector<double> gx(2 * p.Qx), gy(p.Qy);
@@ -258,6 +273,9 @@ void bind_tables(const ProblemSetup &ps, const lbc_params &p, const void *dev, D
     T.ntile = (p.Nx + kTile - 1) / kTile;
     T.law = p.mu_law;
     T.tab_n = (int)ps.tabT.size();
+    T.lts = p.local_dt;
+    T.half = p.half_channel;
+    T.mrest = ps.mrest;
     T.p0 = p.p0; T.dt = ps.dt; T.delta = p.delta; T.Pr = p.Pr; T.omega = p.omega;
     T.TL = p.T_left; T.TR = p.T_right; T.inL = ps.inL; T.inR = ps.inR;
     T.restOutL = ps.restOutL; T.restOutR = ps.restOutR;

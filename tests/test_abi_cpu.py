@@ -30,6 +30,9 @@ def test_exports_every_declared_symbol():
     (dict(Qx=0), "Qx"), (dict(Qy=65), "Qx and Qy"), (dict(Nx=4), "Nx"), (dict(delta=-1.0), "delta"),
     (dict(T_left=0.0), "temperatures"), (dict(stretch_A=1.0), "stretch_A"), (dict(Nexp_x=4), "Nexp_x"),
     (dict(Qy=2), "Nexp_y"), (dict(Pr=0.0), "Pr"), (dict(u_right=float("nan")), "velocities"),
+    (dict(local_dt=2), "local_dt"), (dict(local_dt=1, dt=1e-3), "automatic"), (dict(half_channel=3), "half_channel"),
+    (dict(half_channel=1, u_left=0.1, u_right=0.1), "symmetric walls"),
+    (dict(half_channel=1, T_left=0.9, T_right=1.1), "symmetric walls"),
 ])
 def test_create_rejects_bad_parameters(bad, msg):
     with pytest.raises(lbc.LbcError) as e:
