@@ -340,29 +340,31 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 }
 
 // ---- stage data of a set of nodes ----
-// orders per block of the tabulated recurrence (bounded by shared memory at Q = 64)
-template <typename R> struct OrderBlock { static constexpr int value = sizeof(R) == 4 ? 8 : 4; };
+constexpr int kEqLB = 16;   // orders per block of the projection: lanes = 2 signs x 16 orders
 
 // Shared scratch of node_equilibrium for up to `ncap` nodes. The first `red`
 // bytes are left to the stage kernel's warp partials, so that the equilibrium
-// tables can be copied into `tab` while those are being reduced.
+// tables can be copied into `tab` while those are being reduced. Each warp
+// works through its nodes one at a time in its own `wk` slice: projection
+// weights r^{+-} [2][K], coefficients c^{+-} [cstride], and a block of kEqLB
+// rows h_l(sqrt(T') Y_k) [kEqLB][kpad].
 template <typename R>
 struct EqScratch {
-    size_t red, tab, raw, shf, sc, rpm, bb, cb, H, total;
-    int cstride;
+    size_t red, tab, raw, shf, sc, bb, wk, wbytes, total;
+    int cstride, kpad;
     __host__ __device__ EqScratch(int K, int N, int Ny, int Qx, int Qy, int ntab, int ncap = kTile)
     {
-        cstride = 2 * (N + 1) + 1;   // odd stride: conflict-free rows per node
+        cstride = 2 * (N + 1);
+        kpad = K | 1;   // odd row stride: the lanes of a dot read conflict-free rows
         red = (size_t)kWarps * kNumRaw * kLanes * sizeof(R);
         tab = al16(red);
         raw = al16(tab + (size_t)EqTab(N, Ny, K, Qx, Qy, ntab).len * sizeof(R));
         shf = al16(raw + (size_t)ncap * kNumRaw * sizeof(R));
         sc = al16(shf + (size_t)2 * kLanes * sizeof(R));
-        rpm = al16(sc + (size_t)ncap * 8 * sizeof(R));
-        bb = al16(rpm + (size_t)ncap * 2 * K * sizeof(R));
-        cb = al16(bb + (size_t)ncap * (Ny + 1) * sizeof(R));
-        H = al16(cb + (size_t)ncap * cstride * sizeof(R));
-        total = H + (size_t)OrderBlock<R>::value * ncap * K * sizeof(R);
+        bb = al16(sc + (size_t)ncap * 8 * sizeof(R));
+        wk = al16(bb + (size_t)ncap * (Ny + 1) * sizeof(R));
+        wbytes = al16((size_t)(2 * K + cstride + kEqLB * kpad) * sizeof(R));
+        total = wk + kWarps * wbytes;
     }
     __host__ __device__ static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
 };
@@ -414,56 +416,36 @@ __device__ __forceinline__ void raw_to_moments_r(const R *r, R sx, R sy, R *m)
     m[9] = R(0.5) * hy + R(0.5) * (r[R_GY] - by * pzz);
 }
 
-// Combines the Dot2 states of lane groups (xor distance o) into each lane.
-template <typename R>
-__device__ __forceinline__ void dot_combine(Dot<R> &d, int o)
-{
-    const R so = __shfl_xor_sync(0xffffffffu, d.s, o), co = __shfl_xor_sync(0xffffffffu, d.c, o);
-    if constexpr (std::is_same<R, float>::value) {
-        R t, e;
-        two_sum(d.s, so, t, e);
-        d.s = t;
-        d.c = d.c + co + e;
-    } else {
-        d.s += so;
-    }
-}
-
 // Stage data of the nodes c = cfirst + i cstep (i < nn <= ncap) of tile `tile`
 // for buffer `buf` (block-wide, all threads). Input in `scratch` (EqScratch
-// for ncap nodes): the
-// equilibrium tables (EqTab), the raw moment sums of the deviation per node,
-// raw[i][m], and the shift of those sums per tile node, shf[0][c] = s_x,
-// shf[1][c] = s_y. Adds the rest state's share, turns the sums into moments,
-// and builds the discrete equilibrium factors of Eqs. gx, gy (algorithm: see
-// equilibrium_host). Writes eqm[buf] of the nodes and their columns of the
-// tile's eqg[buf] block; dm_a, dm_b (either may be NULL) receive each node's
-// mass deviation J_s deta (n_s - 1) (local steps, buffer 0).
-// Organised for latency: tables are read from shared memory, and every phase
-// spreads over all threads of the block (recurrences per (node, projection
-// node), dot products over 4 lanes per (node, order), factors per (node,
-// velocity)).
+// for ncap nodes): the equilibrium tables (EqTab), the raw moment sums of the
+// deviation per node, raw[i][m], and the shift of those sums per tile node,
+// shf[0][c] = s_x, shf[1][c] = s_y. Adds the rest state's share, turns the sums
+// into moments, and builds the discrete equilibrium factors of Eqs. gx, gy
+// (algorithm: see equilibrium_host). Writes eqm[buf] of the nodes and their
+// columns of the tile's eqg[buf] block; dm_a, dm_b (either may be NULL) receive
+// each node's mass deviation J_s deta (n_s - 1) (local steps, buffer 0).
+// Organised for instruction count and latency: a thread per node for the
+// moments and the g_y coefficients, then a warp per node for the rest (lanes
+// over projection nodes, then over (sign, order), then over factors), with
+// warp-level synchronisation only and the tables in shared memory.
 template <typename R>
 __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf, int tile, int cfirst, int cstep,
                                  int nn, int ncap, unsigned char *scratch, double *dm_a, double *dm_b)
 {
-    const int tid = threadIdx.x, c0 = tile * kTile;
-    const int N = T.Nxe, K = T.K, G = 2 * T.Qx + T.Qy, Ny = T.Nye;
-    const EqScratch<R> L(K, N, Ny, T.Qx, T.Qy, T.tab_n, ncap);
-    const EqTab E(N, Ny, K, T.Qx, T.Qy, T.tab_n);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, c0 = tile * kTile;
+    const int N = T.Nxe, K = T.K, G = 2 * T.Qx + T.Qy, Ny = T.Nye, Qx = T.Qx, Qy = T.Qy;
+    const EqScratch<R> L(K, N, Ny, Qx, Qy, T.tab_n, ncap);
+    const EqTab E(N, Ny, K, Qx, Qy, T.tab_n);
     const R *tab = reinterpret_cast<const R *>(scratch + L.tab);
     const R *raw = reinterpret_cast<const R *>(scratch + L.raw);   // [nn][kNumRaw]
     const R *shf = reinterpret_cast<const R *>(scratch + L.shf);   // [2][kLanes]
-    R *sc = reinterpret_cast<R *>(scratch + L.sc);      // [nn][8]: sT a a^2/2
-    R *rpm = reinterpret_cast<R *>(scratch + L.rpm);    // [nn][2][K]
+    R *sc = reinterpret_cast<R *>(scratch + L.sc);      // [nn][8]: sT a a^2/2 u'_y T'-1
     R *bb = reinterpret_cast<R *>(scratch + L.bb);      // [nn][Ny+1]   Hermite coefficients of g_y
-    R *cb = reinterpret_cast<R *>(scratch + L.cb);      // [nn][cstride] c^+_l, c^-_l
-    R *H = reinterpret_cast<R *>(scratch + L.H);        // [kLB][nn K]  h_l(sqrt(T') Y_k)
-    constexpr int kLB = OrderBlock<R>::value;
     R *eqm = static_cast<R *>(S.eqm[buf]);
     R *eqg = static_cast<R *>(S.eqg[buf]) + (size_t)tile * G * kLanes;
 
-    // moments, relaxation data and per-node scalars (thread per node)
+    // ---- moments, relaxation data, per-node scalars and the g_y coefficients (thread per node) ----
     if (tid < nn) {
         const int c = cfirst + tid * cstep, s = c0 + c;
         const bool live = s < T.Nx;
@@ -499,8 +481,8 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
                 if (lT[mid] <= Tc) lo = mid + 1;
                 else hi = mid;
             }
-            const int c = min(max(lo - 1, 0), T.tab_n - 2);
-            const R mu = tab[E.lawMu + c] * pow(Tc / lT[c], tab[E.lawW + c]);   // mu(T) / mu(T_ref)
+            const int cg = min(max(lo - 1, 0), T.tab_n - 2);
+            const R mu = tab[E.lawMu + cg] * pow(Tc / lT[cg], tab[E.lawW + cg]);   // mu(T) / mu(T_ref)
             nu = n * Tc / mu * Tabs<R>::sc(T, SC_NU);
             cS = (R(1) - tab[E.lawPr + max(lo - 1, 0)]) / (n * Tc * Tc);
         } else {
@@ -514,17 +496,12 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             e[10] = m[4]; e[11] = m[5]; e[12] = m[6]; e[13] = m[7]; e[14] = Tabs<R>::dtn(T)[s];
         }
         const R ip0 = Tabs<R>::sc(T, SC_IP0), Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
-        R *x = sc + tid * 8;   // sT a a^2/2 u'_y T'-1
-        x[0] = sT; x[1] = a; x[2] = R(0.5) * a * a; x[3] = uy * ip0; x[4] = Tp - R(1);
-    }
-    __syncthreads();
-    // g_y coefficients b_l = E[He_l(u' + sqrt(T') Y)] / l!: b_{l+1} = (u' b_l + (T'-1) b_{l-1}) / (l+1),
-    // by the last warp while the others run the g_x projection
-    if (tid >= kThreads - nn) {
-        const int i = tid - (kThreads - nn);
-        const R uq = sc[i * 8 + 3], tm1 = sc[i * 8 + 4];
+        R *x = sc + tid * 8;
+        x[0] = sT; x[1] = a; x[2] = R(0.5) * a * a;
+        // g_y coefficients b_l = E[He_l(u' + sqrt(T') Y)] / l!: b_{l+1} = (u' b_l + (T'-1) b_{l-1}) / (l+1)
+        const R uq = uy * ip0, tm1 = Tp - R(1);
         const R *invl = tab + E.invl;
-        R *b = bb + i * (Ny + 1);
+        R *b = bb + tid * (Ny + 1);
         R bm = R(1), bl = uq;
         b[0] = R(1);
         b[1] = uq;
@@ -535,83 +512,75 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             b[l + 1] = bn;
         }
     }
-    // weights r_k^{+-} = W_k exp(+-a Y_k - a^2/2) of every (node, projection node)
+    __syncthreads();
+
+    // ---- a warp per node: g_x by the stable Gauss-sum projection, then the factors ----
     const R *Yk = tab + E.Yk, *Wk = tab + E.Wk;
-    const int nk = nn * K;
-    for (int idx = tid; idx < nk; idx += kThreads) {
-        const int i = idx / K, k = idx - i * K;
-        const R *x = sc + i * 8;
-        const R Y = Yk[k], W = Wk[k];
-        rpm[(i * 2) * K + k] = W * exp(x[1] * Y - x[2]);
-        rpm[(i * 2 + 1) * K + k] = W * exp(-x[1] * Y - x[2]);
-    }
-    // projection coefficients c^{+-}_l = sum_k r_k^{+-} h_l(sqrt(T') Y_k), in blocks of kLB orders:
-    // recurrence state per (node, projection node) kept in registers across blocks
-    constexpr int kItems = (kTile * kMaxK + kThreads - 1) / kThreads;
-    const int nit = (nk + kThreads - 1) / kThreads;   // items in use: the rest is skipped, not computed
-    R zt[kItems], h[kItems], hp[kItems];
     const R *alpha = tab + E.alpha, *sbeta = tab + E.sbeta, *isbeta = tab + E.isbeta;
+    const R *hz = tab + E.hz, *He = tab + E.He;
     const R h0 = Tabs<R>::sc(T, SC_H0);
+    R *rp = reinterpret_cast<R *>(scratch + L.wk + warp * L.wbytes);   // [2][K] r^+, r^-
+    R *cw = rp + 2 * K;                                                // [2][N+1] c^+, c^-
+    R *Hw = cw + L.cstride;                                            // [kEqLB][kpad]
+    const int sgn = lane / kEqLB, lo = lane - sgn * kEqLB;             // the dot product of this lane
+    for (int i = warp; i < nn; i += kWarps) {
+        const R *x = sc + i * 8;
+        const R sT = x[0], a = x[1], a2 = x[2];
+        // weights r_k^{+-} = W_k exp(+-a Y_k - a^2/2) and recurrence arguments sqrt(T') Y_k
+        R zt[2], h[2], hp[2];
 #pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-        const int idx = tid + it * kThreads;
-        const int i = idx / K, k = idx - i * K;
-        zt[it] = R(0);
-        if (it < nit && idx < nk) zt[it] = sc[i * 8] * Yk[k];
-        h[it] = h0;
-        hp[it] = R(0);
-    }
-    for (int lb = 0; lb <= N; lb += kLB) {
-        const int le = min(N, lb + kLB - 1);
-        for (int l = lb; l <= le; ++l) {
-            const R al = alpha[l], sb = sbeta[l], isb1 = isbeta[l + 1];
+        for (int u = 0; u < 2; ++u) {   // K <= 46: projection nodes lane and lane + 32
+            const int k = lane + 32 * u;
+            zt[u] = R(0);
+            h[u] = h0;
+            hp[u] = R(0);
+            if (k < K) {
+                const R Y = Yk[k], W = Wk[k];
+                rp[k] = W * exp(a * Y - a2);
+                rp[K + k] = W * exp(-a * Y - a2);
+                zt[u] = sT * Y;
+            }
+        }
+        // c^{+-}_l = sum_k r_k^{+-} h_l(sqrt(T') Y_k), in blocks of kEqLB orders: lanes run the
+        // recurrence of h_l at their projection nodes, then lane (sign, l) takes one dot product
+        for (int lb = 0; lb <= N; lb += kEqLB) {
+            const int le = min(N, lb + kEqLB - 1);
+            for (int l = lb; l <= le; ++l) {
+                const R al = alpha[l], sb = sbeta[l], isb1 = isbeta[l + 1];
 #pragma unroll
-            for (int it = 0; it < kItems; ++it) {
-                if (it < nit) {
-                    const int idx = tid + it * kThreads;
-                    if (idx < nk) H[(l - lb) * nk + idx] = h[it];
-                    const R hn = ((zt[it] - al) * h[it] - sb * hp[it]) * isb1;
-                    hp[it] = h[it];
-                    h[it] = hn;
+                for (int u = 0; u < 2; ++u) {
+                    const int k = lane + 32 * u;
+                    if (k < K) Hw[(l - lb) * L.kpad + k] = h[u];
+                    const R hn = ((zt[u] - al) * h[u] - sb * hp[u]) * isb1;
+                    hp[u] = h[u];
+                    h[u] = hn;
                 }
             }
-        }
-        __syncthreads();
-        // 4 lanes per dot product (k strided by 4), partial states combined by shuffles
-        const int nl = le - lb + 1, items = nn * 2 * nl;
-        for (int base = 0; base < 4 * items; base += kThreads) {   // same trip count in every thread
-            const int i4 = base + tid, item = i4 >> 2, q = i4 & 3;
-            Dot<R> d;
-            int i = 0, sgn = 0, jl = 0;
-            if (item < items) {
-                i = item / (2 * nl);
-                const int rem = item - i * 2 * nl;
-                sgn = rem / nl;
-                jl = rem - sgn * nl;
-                const R *r = rpm + (i * 2 + sgn) * K, *hh = H + jl * nk + i * K;
-                for (int k = q; k < K; k += 4) d.add(r[k], hh[k]);
+            __syncwarp();
+            if (lb + lo <= le) {
+                const R *r = rp + sgn * K, *hh = Hw + lo * L.kpad;
+                Dot<R> d;
+                for (int k = 0; k < K; ++k) d.add(r[k], hh[k]);
+                cw[sgn * (N + 1) + lb + lo] = d.value();
             }
-            dot_combine(d, 1);
-            dot_combine(d, 2);
-            if (item < items && q == 0) cb[i * L.cstride + sgn * (N + 1) + lb + jl] = d.value();
+            __syncwarp();
         }
-        __syncthreads();
-    }
-    // factors: g_x/w at (node, a), g_y/w at (node, j)
-    const R *hz = tab + E.hz, *He = tab + E.He;
-    for (int idx = tid; idx < G * nn; idx += kThreads) {
-        const int ig = idx / nn, i = idx - ig * nn;
-        Dot<R> d;
-        if (ig < 2 * T.Qx) {
-            const int ii = ig < T.Qx ? ig : ig - T.Qx;
-            const R *cc = cb + i * L.cstride + (ig < T.Qx ? 0 : N + 1);
-            for (int l = 0; l <= N; ++l) d.add(hz[l * T.Qx + ii], cc[l]);
-        } else {
-            const int jj = ig - 2 * T.Qx;
-            const R *b = bb + i * (Ny + 1);
-            for (int l = 0; l <= Ny; ++l) d.add(He[l * T.Qy + jj], b[l]);
+        // factors: g_x/w at (node, a) = sum_l h_l(z_a) c_l^{sign a}, g_y/w at (node, j) = sum_l He_l(y_j) b_l
+        R *col = eqg + cfirst + i * cstep;
+        for (int ig = lane; ig < G; ig += 32) {
+            Dot<R> d;
+            if (ig < 2 * Qx) {
+                const int ii = ig < Qx ? ig : ig - Qx;
+                const R *cc = cw + (ig < Qx ? 0 : N + 1);
+                for (int l = 0; l <= N; ++l) d.add(hz[l * Qx + ii], cc[l]);
+            } else {
+                const int jj = ig - 2 * Qx;
+                const R *b = bb + i * (Ny + 1);
+                for (int l = 0; l <= Ny; ++l) d.add(He[l * Qy + jj], b[l]);
+            }
+            col[(size_t)ig * kLanes] = d.value();
         }
-        eqg[(size_t)ig * kLanes + cfirst + i * cstep] = d.value();
+        __syncwarp();   // the next node reuses this warp's slice
     }
 }
 
