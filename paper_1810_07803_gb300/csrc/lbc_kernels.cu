@@ -808,6 +808,9 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
 #pragma unroll
     for (int m = 0; m < kNumRaw; ++m) acc[m] = R(0);
     R res = R(0);
+    f2 pk[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) pk[m] = bc2(0.f);
     constexpr int NQ = kSubV / kWarps;      // rows per warp and slot: rows warp + kWarps q
     bool my_timeout = false;
 
@@ -911,21 +914,54 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
             mirror_fetch(sub + 1);
         }
         if constexpr (std::is_same<R, float>::value) {
-            // FP32: (phi, chi) as packed pairs, loaded and stored as one 64-bit access each
+            // FP32: (phi, chi) as packed pairs, loaded and stored as one 64-bit access each.
+            // Face c0 + lane of each row: rows v < Qx Qy have p_x > 0 and upwind from the
+            // left (nodes ck-3 .. ck+1), the others from the right (nodes ck+2 .. ck-2). A slot
+            // whose rows all share a side loads its stencils at fixed offsets.
             f2 fl[NQ], dd[NQ];
+            const int vq0 = vbeg + sub * kSubV, vq1 = min(vq0 + kSubV, vend) - 1;
+            const int vhalf = T.Qx * T.Qy;
+            const float *rowq = fin + (size_t)warp * 2 * kRowLen + 2 * (ck - 3);   // row warp, node ck - 3
+            if (vq1 < vhalf) {
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const float4 xa = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow);   // px py w fr
-                const bool pos = xa.x > 0.f;
-                const int base = pos ? ck - 3 : ck + 2, st = pos ? 1 : -1;   // upwind stencil order
-                const float *row = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen;
-                f2 v[5];
+                for (int q = 0; q < NQ; ++q) {
+                    const float *pp = rowq + (size_t)q * kWarps * 2 * kRowLen;
+                    f2 v[5];
 #pragma unroll
-                for (int i = 0; i < 5; ++i) v[i] = ld2(row + 2 * (base + i * st));
-                fl[q] = weno5_2(v[0], v[1], v[2], v[3], v[4]);   // face c0 + lane
-                dd[q] = pos ? v[3] : v[2];                        // the node itself
-                if (wall) {
+                    for (int i = 0; i < 5; ++i) v[i] = ld2(pp + 2 * i);
+                    fl[q] = weno5_2(v[0], v[1], v[2], v[3], v[4]);
+                    dd[q] = v[3];
+                }
+            } else if (vq0 >= vhalf) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float *pp = rowq + (size_t)q * kWarps * 2 * kRowLen + 2;
+                    f2 v[5];
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) v[i] = ld2(pp + 2 * i);
+                    fl[q] = weno5_2(v[4], v[3], v[2], v[1], v[0]);
+                    dd[q] = v[2];
+                }
+            } else {   // the slot holds both signs: upwind order per row
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float4 xa = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow);   // px py w fr
+                    const bool pos = xa.x > 0.f;
+                    const int base = pos ? ck - 3 : ck + 2, st = pos ? 1 : -1;
+                    const float *row = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen;
+                    f2 v[5];
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) v[i] = ld2(row + 2 * (base + i * st));
+                    fl[q] = weno5_2(v[0], v[1], v[2], v[3], v[4]);
+                    dd[q] = pos ? v[3] : v[2];   // the node itself
+                }
+            }
+            if (wall) {   // wall faces: the incoming population n_w f_w (Eq. diffuse)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float4 xa = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow);
                     const float4 xw = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow + 4);
+                    const bool pos = xa.x > 0.f;
                     if (needL && pos && s == 0) fl[q] = mk2(nwL * xw.x - xa.w, nwL * xw.y - xa.w);
                     if (needR && !pos && s == Nx) fl[q] = mk2(nwR * xw.z - xa.w, nwR * xw.w - xa.w);
                 }
@@ -961,20 +997,16 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                 }
                 if (active && ok[q]) {
                     st2(Fout_s + 2 * (size_t)Nxp * v, dn);
-                    float o0, o1;
-                    un2(dn, o0, o1);
-                    const float fw = w * o0, gw = w * o1;
-                    acc[R_S0] += fw;
-                    acc[R_SX] += xx * fw;
-                    acc[R_SY] += xy * fw;
-                    acc[R_SXX] += xx * xx * fw;
-                    acc[R_SXY] += xx * xy * fw;
-                    acc[R_SYY] += xy * xy * fw;
-                    acc[R_CZ] += gw;
-                    acc[R_R3X] += e2 * xx * fw;
-                    acc[R_R3Y] += e2 * xy * fw;
-                    acc[R_GX] += xx * gw;
-                    acc[R_GY] += xy * gw;
+                    const f2 fg = bc2(w) * dn;                 // (fw, gw)
+                    float fw, gw;
+                    un2(fg, fw, gw);
+                    const f2 pxy = mk2(xx, xy);
+                    pk[0] = pk[0] + fg;                        // (S0, CZ)
+                    pk[1] = fma2(pxy, bc2(fw), pk[1]);         // (SX, SY)
+                    pk[2] = fma2(pxy, bc2(gw), pk[2]);         // (GX, GY)
+                    pk[3] = fma2(pxy * pxy, bc2(fw), pk[3]);   // (SXX, SYY)
+                    pk[4] = fma2(bc2(e2) * pxy, bc2(fw), pk[4]);   // (R3X, R3Y)
+                    acc[R_SXY] = fmaf(xx * xy, fw, acc[R_SXY]);
                 }
             }
         } else {
@@ -1090,6 +1122,13 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     if (tid == 0) {   // the equilibrium tables, into the pipeline region that the loop no longer reads
         mbar_expect_tx(bar_tab, tab_bytes);
         bulk_load(scr + E.tab, Tabs<R>::eqtab(T), tab_bytes, bar_tab);
+    }
+    if constexpr (std::is_same<R, float>::value) {
+        un2(pk[0], acc[R_S0], acc[R_CZ]);
+        un2(pk[1], acc[R_SX], acc[R_SY]);
+        un2(pk[2], acc[R_GX], acc[R_GY]);
+        un2(pk[3], acc[R_SXX], acc[R_SYY]);
+        un2(pk[4], acc[R_R3X], acc[R_R3Y]);
     }
     R *s_red = reinterpret_cast<R *>(scr);   // [kWarps][kNumRaw][kLanes], below E.tab
 #pragma unroll
