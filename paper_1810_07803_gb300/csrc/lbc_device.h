@@ -16,8 +16,8 @@ constexpr int kRowLen = 40;        // TMA box width of a stage-input row (halo 3
 constexpr int kF0Len = 36;         // TMA box width of an RK base row (31 nodes, aligned start)
 constexpr int kWarps = 8;          // warps per CTA
 constexpr int kThreads = kWarps * 32;
-constexpr int kSubV = 16;          // velocities per pipeline stage (two per warp)
-constexpr int kPipe = 4;           // pipeline depth (stages in flight)
+constexpr int kSubV = 32;          // velocity rows per pipeline slot (four per warp)
+constexpr int kPipe = 2;           // pipeline slots (one computed while the other lands)
 constexpr int kEqM = 16;           // per-node stage data: n ux uy T qx qy 1/tau cS 1/(5T) 1/(J deta)
                                    // Pxx Pyy Pzz Pxy dt_s, 1 pad (64 B per FP32 node: 16-byte-aligned bulk copies)
 constexpr int kMassHdr = 32;       // doubles before the per-node mass deviations in DevState::mass

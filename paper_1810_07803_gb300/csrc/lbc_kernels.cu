@@ -1010,77 +1010,83 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                 }
             }
         } else {
-            R fl[NQ][2], dd[NQ][2];
+            // FP64: rows in pairs (q = qp, qp + 1), which bounds the live registers
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const R *x = s_vrow + kq[q] * kVRow;
-                const bool pos = x[VR_PX] > R(0);
-                const int base = pos ? ck - 3 : ck + 2, st = pos ? 1 : -1;   // upwind stencil order
-                const R *row = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen;
-                R v[5][2];
+            for (int qp = 0; qp < NQ; qp += 2) {
+                R fl[2][2], dd[2][2];
 #pragma unroll
-                for (int i = 0; i < 5; ++i) {
-                    const double2 t = *reinterpret_cast<const double2 *>(row + 2 * (base + i * st));
-                    v[i][0] = t.x;
-                    v[i][1] = t.y;
-                }
+                for (int qi = 0; qi < 2; ++qi) {
+                    const int q = qp + qi;
+                    const R *x = s_vrow + kq[q] * kVRow;
+                    const bool pos = x[VR_PX] > R(0);
+                    const int base = pos ? ck - 3 : ck + 2, st = pos ? 1 : -1;   // upwind stencil order
+                    const R *row = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen;
+                    R v[5][2];
 #pragma unroll
-                for (int fld = 0; fld < 2; ++fld) {
-                    // face c0 + lane (left of node c0 + lane)
-                    fl[q][fld] = weno5<R>(v[0][fld], v[1][fld], v[2][fld], v[3][fld], v[4][fld]);
-                    dd[q][fld] = pos ? v[3][fld] : v[2][fld];
-                    if (wall) {
-                        if (needL && pos && s == 0) fl[q][fld] = nwL * x[VR_FWL + fld] - x[VR_FR];
-                        if (needR && !pos && s == Nx) fl[q][fld] = nwR * x[VR_FWR + fld] - x[VR_FR];
+                    for (int i = 0; i < 5; ++i) {
+                        const double2 t = *reinterpret_cast<const double2 *>(row + 2 * (base + i * st));
+                        v[i][0] = t.x;
+                        v[i][1] = t.y;
+                    }
+#pragma unroll
+                    for (int fld = 0; fld < 2; ++fld) {
+                        // face c0 + lane (left of node c0 + lane)
+                        fl[qi][fld] = weno5<R>(v[0][fld], v[1][fld], v[2][fld], v[3][fld], v[4][fld]);
+                        dd[qi][fld] = pos ? v[3][fld] : v[2][fld];
+                        if (wall) {
+                            if (needL && pos && s == 0) fl[qi][fld] = nwL * x[VR_FWL + fld] - x[VR_FR];
+                            if (needR && !pos && s == Nx) fl[qi][fld] = nwR * x[VR_FWR + fld] - x[VR_FR];
+                        }
                     }
                 }
-            }
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const R *x = s_vrow + kq[q] * kVRow;
-                const int ga = row_bits(x[VR_GA]), gj = row_bits(x[VR_GJ]);
-                const int r = warp + kWarps * q, v = vbeg + kq[q];
-                const R px = x[VR_PX], py = x[VR_PY], w = x[VR_W], fr = x[VR_FR];
-                const R feq = n_c * s_g[ga + lane] * s_g[gj + lane];
-                const R xx = px - ux_c, xy = py - uy_c;
-                const R qxi = qx_c * xx + qy_c * xy;
-                const R x2 = (xx * xx + xy * xy) * i5T;
-                R fo[2];
-                const double2 d0 = stage > 0 ? *reinterpret_cast<const double2 *>(f0 + (size_t)r * 2 * kF0Len +
-                                                                                 2 * (lane + offf))
-                                             : make_double2(0.0, 0.0);
+                for (int qi = 0; qi < 2; ++qi) {
+                    const int q = qp + qi;
+                    const R *x = s_vrow + kq[q] * kVRow;
+                    const int ga = row_bits(x[VR_GA]), gj = row_bits(x[VR_GJ]);
+                    const int r = warp + kWarps * q, v = vbeg + kq[q];
+                    const R px = x[VR_PX], py = x[VR_PY], w = x[VR_W], fr = x[VR_FR];
+                    const R feq = n_c * s_g[ga + lane] * s_g[gj + lane];
+                    const R xx = px - ux_c, xy = py - uy_c;
+                    const R qxi = qx_c * xx + qy_c * xy;
+                    const R x2 = (xx * xx + xy * xy) * i5T;
+                    R fo[2];
+                    const double2 d0 = stage > 0 ? *reinterpret_cast<const double2 *>(f0 + (size_t)r * 2 * kF0Len +
+                                                                                     2 * (lane + offf))
+                                                 : make_double2(0.0, 0.0);
 #pragma unroll
-                for (int fld = 0; fld < 2; ++fld) {
-                    const R frt = __shfl_down_sync(0xffffffffu, fl[q][fld], 1);
-                    const R d = dd[q][fld];
-                    const R adv = -px * (frt - fl[q][fld]) * ijd;
-                    // Shakhov target minus the rest state
-                    const R tgt = fld ? T_c * feq * (R(1) + cS_c * (x2 - R(0.4)) * qxi) - fr
-                                      : feq * (R(1) + cS_c * (x2 - R(0.8)) * qxi) - fr;
-                    R dn = d + dt * (adv - nu_c * (d - tgt));
-                    if (stage > 0) {
-                        const R b0 = fld ? d0.y : d0.x;
-                        dn = ca * b0 + cb * dn;
-                        if (renorm) dn = fma(lam1r, dn + fr, dn);   // lambda (d + ft_rest) - ft_rest
-                        if (stage == 2 && active && ok[q]) res = fmax(res, w * fabs(dn - b0));
+                    for (int fld = 0; fld < 2; ++fld) {
+                        const R frt = __shfl_down_sync(0xffffffffu, fl[qi][fld], 1);
+                        const R d = dd[qi][fld];
+                        const R adv = -px * (frt - fl[qi][fld]) * ijd;
+                        // Shakhov target minus the rest state
+                        const R tgt = fld ? T_c * feq * (R(1) + cS_c * (x2 - R(0.4)) * qxi) - fr
+                                          : feq * (R(1) + cS_c * (x2 - R(0.8)) * qxi) - fr;
+                        R dn = d + dt * (adv - nu_c * (d - tgt));
+                        if (stage > 0) {
+                            const R b0 = fld ? d0.y : d0.x;
+                            dn = ca * b0 + cb * dn;
+                            if (renorm) dn = fma(lam1r, dn + fr, dn);   // lambda (d + ft_rest) - ft_rest
+                            if (stage == 2 && active && ok[q]) res = fmax(res, w * fabs(dn - b0));
+                        }
+                        fo[fld] = dn;
                     }
-                    fo[fld] = dn;
-                }
-                if (active && ok[q]) {
-                    *reinterpret_cast<double2 *>(Fout_s + 2 * (size_t)Nxp * v) = make_double2(fo[0], fo[1]);
-                    const R fw = w * fo[0], gw = w * fo[1];
-                    const R e2 = xx * xx + xy * xy;
-                    acc[R_S0] += fw;
-                    acc[R_SX] += xx * fw;
-                    acc[R_SY] += xy * fw;
-                    acc[R_SXX] += xx * xx * fw;
-                    acc[R_SXY] += xx * xy * fw;
-                    acc[R_SYY] += xy * xy * fw;
-                    acc[R_CZ] += gw;
-                    acc[R_R3X] += e2 * xx * fw;
-                    acc[R_R3Y] += e2 * xy * fw;
-                    acc[R_GX] += xx * gw;
-                    acc[R_GY] += xy * gw;
+                    if (active && ok[q]) {
+                        *reinterpret_cast<double2 *>(Fout_s + 2 * (size_t)Nxp * v) = make_double2(fo[0], fo[1]);
+                        const R fw = w * fo[0], gw = w * fo[1];
+                        const R e2 = xx * xx + xy * xy;
+                        acc[R_S0] += fw;
+                        acc[R_SX] += xx * fw;
+                        acc[R_SY] += xy * fw;
+                        acc[R_SXX] += xx * xx * fw;
+                        acc[R_SXY] += xx * xy * fw;
+                        acc[R_SYY] += xy * xy * fw;
+                        acc[R_CZ] += gw;
+                        acc[R_R3X] += e2 * xx * fw;
+                        acc[R_R3Y] += e2 * xy * fw;
+                        acc[R_GX] += xx * gw;
+                        acc[R_GY] += xy * gw;
+                    }
                 }
             }
         }
