@@ -96,9 +96,21 @@ typedef struct {
                                 1: local pseudo-time steps for steady states (below) */
     int half_channel;        /* 0: the full channel -1/2 < x < 1/2 with Nx nodes;
                                 1: the half channel 0 < x < 1/2 with Nx nodes (below) */
+    int compensated;         /* LBC_FP32_STATE only: 1 carries each state value's rounding
+                                remainder from step to step (below); 0: plain FP32 state */
 } lbc_params;
 
 /*
+ * Compensated FP32 state (compensated = 1, precision LBC_FP32_STATE; LBC_EINVAL
+ * otherwise). Each value of the state is held as an FP32 value d plus an FP32
+ * remainder c in one more state buffer: the third stage adds the step's
+ * increment Delta = f^{n+1} - f^n to d + c with the rounding error kept
+ * (TwoSum), so increments below half an ulp of d still move the state. Without
+ * it an FP32 iteration stalls at a steady state biased by about
+ * eps_32 |f| tau / dt (~1e-3 relative at delta = 0.1 on stretched grids). The
+ * stage arithmetic itself stays FP32. lbc_get_state returns d + c and
+ * lbc_set_state stores the FP64 input as d + c. lbc_step_noalloc rejects it.
+ *
  * Local pseudo-time steps (local_dt = 1; dt must be 0). Only the steady state
  * is meaningful: node s advances by dt_s = min(cfl * J_s deta / max|p_x|,
  * tau_min / 2), the automatic step below with the CFL bound taken at each node,

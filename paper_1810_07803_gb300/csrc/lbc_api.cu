@@ -259,7 +259,7 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     b->d_work = reinterpret_cast<int2 *>(tb + work_off);
     for (int i = 0; i < n; ++i) {
         bind_tables(setup[i], ps[i], tb + toff[i], b->inst[i].T);
-        b->ext = b->ext || ps[i].half_channel || ps[i].local_dt;
+        b->ext = b->ext || ps[i].half_channel || ps[i].local_dt || ps[i].compensated;
     }
 
     // ---- launch shape ----
@@ -421,8 +421,8 @@ lbc_status batch_get_state(lbc_batch *b, int i, double *state)
     if (!state) return fail(LBC_EINVAL, "NULL argument");
     const Inst &I = b->inst[i];
     const size_t bytes = 2 * (size_t)I.T.V * I.T.Nx * sizeof(double);
-    LBC_CUDA_TRY(b->fp32 ? launch_state_out<float>(I.S.F[0], b->d_io, I.T, b->stream)
-                         : launch_state_out<double>(I.S.F[0], b->d_io, I.T, b->stream));
+    LBC_CUDA_TRY(b->fp32 ? launch_state_out<float>(I.S.F[0], I.S.C, b->d_io, I.T, b->stream)
+                         : launch_state_out<double>(I.S.F[0], nullptr, b->d_io, I.T, b->stream));
     LBC_CUDA_TRY(cudaMemcpyAsync(state, b->d_io, bytes, cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
@@ -432,8 +432,9 @@ lbc_status batch_get_state(lbc_batch *b, int i, double *state)
 }
 
 // The host state goes to the device as it is (one copy); a kernel converts it
-// into the second RK buffer, which is free between steps, and checks it, so a
-// rejected state leaves the instance unchanged.
+// into the second RK buffer (and a compensated state's remainders into the third),
+// which are free between steps, and checks it, so a rejected state leaves the
+// instance unchanged.
 lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
 {
     lbc_status st = check_index(b, i);
@@ -443,8 +444,9 @@ lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
     const size_t bytes = 2 * (size_t)I.T.V * I.T.Nx * sizeof(double);
     LBC_CUDA_TRY(cudaMemcpyAsync(b->d_io, state, bytes, cudaMemcpyHostToDevice, b->stream));
     LBC_CUDA_TRY(cudaMemsetAsync(b->d_bad, 0, sizeof(int), b->stream));
-    LBC_CUDA_TRY(b->fp32 ? launch_state_in<float>(b->d_io, I.S.F[1], I.T, b->d_bad, b->stream)
-                         : launch_state_in<double>(b->d_io, I.S.F[1], I.T, b->d_bad, b->stream));
+    LBC_CUDA_TRY(b->fp32 ? launch_state_in<float>(b->d_io, I.S.F[1], I.S.C ? I.S.F[2] : nullptr, I.T, b->d_bad,
+                                                  b->stream)
+                         : launch_state_in<double>(b->d_io, I.S.F[1], nullptr, I.T, b->d_bad, b->stream));
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_bad, b->d_bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
@@ -456,6 +458,9 @@ lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
     const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
     LBC_CUDA_TRY(cudaMemcpyAsync(I.S.F[0], I.S.F[1], 2 * (size_t)I.T.V * I.T.Nxp * esz, cudaMemcpyDeviceToDevice,
                                  b->stream));
+    if (I.S.C)
+        LBC_CUDA_TRY(cudaMemcpyAsync(I.S.C, I.S.F[2], 2 * (size_t)I.T.V * I.T.Nxp * esz, cudaMemcpyDeviceToDevice,
+                                     b->stream));
     st = upload_ctl(b, i, 1);
     if (st == LBC_OK) st = rebuild_stage_data(b, i);
     if (st != LBC_OK) return st;
@@ -525,6 +530,8 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
         const DevTables &T = b->inst[i].T;
         const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
         cudaError_t e = cudaMemsetAsync(b->inst[i].S.F[0], 0, 2 * (size_t)T.V * T.Nxp * esz, b->stream);
+        if (e == cudaSuccess && b->inst[i].S.C)
+            e = cudaMemsetAsync(b->inst[i].S.C, 0, 2 * (size_t)T.V * T.Nxp * esz, b->stream);
         if (e != cudaSuccess) st2 = fail(LBC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
         if (st2 == LBC_OK) st2 = rebuild_stage_data(b, i);
     }

@@ -45,6 +45,7 @@ struct DevTables {
     int law, tab_n;                // viscosity law (LBC_MU_POWER / LBC_MU_TABLE), table entries
     int lts;                       // local pseudo-time steps with mass renormalisation (local_dt)
     int half;                      // half channel: symmetry plane at x = 0 instead of the left wall
+    int comp;                      // FP32 state with the rounding remainder of each value (DevState::C)
     double mrest;                  // sum_s J_s deta (the mass of the rest state n = 1)
     double p0, dt, delta, Pr, omega, TL, TR;
     double inL, inR;               // sum_{incoming} p_x w_v fw_v (signed) for a unit wall density
@@ -137,6 +138,7 @@ struct DevState {
     double *mom_out;       // [LBC_NMOM][Nxp] scratch for lbc_moments
     double *mass;          // local steps: [0] reference mass minus the rest mass; from kMassHdr on,
                            // [2][Nxp] J_s deta (n_s - 1) of buffer 0 after steps of parity 0 / 1
+    void *C;               // (R) compensated state: [V][Nxp][2] rounding remainder of buffer 0 (else NULL)
 };
 
 // TMA descriptors of the state buffers, viewed as 2-D [V rows][2 Nxp columns].
@@ -220,11 +222,12 @@ cudaError_t launch_tile_equilibrium(const DevTables &T, const DevState &S, int b
 template <typename R>
 cudaError_t launch_moments_from_stage_data(const DevTables &T, const DevState &S, cudaStream_t st);
 // FP64 [2][V][Nx] weight-divided state in device memory -> deviation rows of buffer `dst`
-// (sets *bad, if not NULL, when a value is not finite); and back.
+// and, if `carry` is not NULL, the rounding remainder of each value (sets *bad, if not
+// NULL, when a value is not finite); and back (adding the remainder when given).
 template <typename R>
-cudaError_t launch_state_in(const double *src, void *dst, const DevTables &T, int *bad, cudaStream_t st);
+cudaError_t launch_state_in(const double *src, void *dst, void *carry, const DevTables &T, int *bad, cudaStream_t st);
 template <typename R>
-cudaError_t launch_state_out(const void *src, double *dst, const DevTables &T, cudaStream_t st);
+cudaError_t launch_state_out(const void *src, const void *carry, double *dst, const DevTables &T, cudaStream_t st);
 cudaError_t launch_ctl_bump(Ctl *ctl, int n, long long k, cudaStream_t st);
 // last[k] = residual of instance slots[k]'s (k's if slots is NULL) last step taken (its stop
 // step - 1 if stopped, else base - 1), k < n
@@ -234,7 +237,7 @@ inline size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 // Device bytes of one instance's state (partials sized for the largest cluster, so
 // a launch shape can change without reallocating).
 struct StateSizes {
-    size_t f, eqm, eqg, part, resid, mom, mass, total;
+    size_t f, eqm, eqg, part, resid, mom, mass, carry, total;
     StateSizes(const DevTables &T, bool fp32)
     {
         const size_t esz = fp32 ? sizeof(float) : sizeof(double);
@@ -245,7 +248,8 @@ struct StateSizes {
         resid = kResidRing * sizeof(unsigned long long);
         mom = round256((size_t)LBC_NMOM * T.Nxp * sizeof(double));
         mass = round256((kMassHdr + 2 * (size_t)T.Nxp) * sizeof(double));
-        total = 3 * (f + eqm + eqg) + part + resid + mom + mass;
+        carry = T.comp ? f : 0;
+        total = 3 * (f + eqm + eqg) + part + resid + mom + mass + carry;
     }
     // Points the state arrays of S into `base` (total bytes); S.ctl is set by the caller.
     void carve(char *base, DevState &S) const
@@ -257,7 +261,8 @@ struct StateSizes {
         S.part = p; p += part;
         S.resid = reinterpret_cast<unsigned long long *>(p); p += resid;
         S.mom_out = reinterpret_cast<double *>(p); p += mom;
-        S.mass = reinterpret_cast<double *>(p);
+        S.mass = reinterpret_cast<double *>(p); p += mass;
+        S.C = carry ? p : nullptr;
     }
 };
 

@@ -775,6 +775,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     // local steps: this step's mass correction lambda - 1 = (M_ref - M(f^n)) / M(f^n), from the
     // mass deviations of f^n that the previous step (or the set-up) left for this step's parity
     const bool renorm = kExt && T.lts != 0 && stage == 2;
+    const bool comp = kExt && T.comp != 0 && stage == 2;   // compensated FP32 state (DevState::C)
     double lam1 = 0.0;
     if (renorm) {
         const double dM = block_mass_deviation(S.mass + kMassHdr + (size_t)(step & 1) * T.Nxp, T.Nx, s_misc);
@@ -987,12 +988,31 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                 f2 dn = fma2(bc2(dt), fma2(bc2(-nu_c), dd[q] - tgt, adv), dd[q]);
                 if (stage > 0) {
                     const f2 d0 = ld2(f0 + (size_t)r * 2 * kF0Len + 2 * (lane + offf));
-                    dn = fma2(bc2(ca), d0, bc2(cb) * dn);
-                    if (renorm) dn = fma2(bc2(lam1r), dn + bc2(fr), dn);   // lambda (d + ft_rest) - ft_rest
-                    if (stage == 2 && active && ok[q]) {
-                        float e0, e1;
-                        un2(dn - d0, e0, e1);
-                        res = fmaxf(res, w * fmaxf(fabsf(e0), fabsf(e1)));
+                    if (comp) {
+                        // the step's increment 2/3 (d2 + dt L(d2) - d0), added to d0 + c0 with its
+                        // rounding error kept (TwoSum of Knuth): increments below half an ulp of d0 count
+                        f2 inc = bc2(2.f / 3.f) * (dn - d0);
+                        if (renorm) inc = fma2(bc2(lam1r), d0 + inc + bc2(fr), inc);
+                        float *cp = static_cast<float *>(S.C) + 2 * ((size_t)Nxp * v + s);
+                        f2 cs = inc;
+                        if (active && ok[q]) cs = ld2(cp) + inc;
+                        const f2 sn = d0 + cs, bv = sn - d0;
+                        const f2 er = (d0 - (sn - bv)) + (cs - bv);
+                        dn = sn;
+                        if (active && ok[q]) {
+                            st2(cp, er);
+                            float e0, e1;
+                            un2(inc, e0, e1);
+                            res = fmaxf(res, w * fmaxf(fabsf(e0), fabsf(e1)));
+                        }
+                    } else {
+                        dn = fma2(bc2(ca), d0, bc2(cb) * dn);
+                        if (renorm) dn = fma2(bc2(lam1r), dn + bc2(fr), dn);   // lambda (d + ft_rest) - ft_rest
+                        if (stage == 2 && active && ok[q]) {
+                            float e0, e1;
+                            un2(dn - d0, e0, e1);
+                            res = fmaxf(res, w * fmaxf(fabsf(e0), fabsf(e1)));
+                        }
                     }
                 }
                 if (active && ok[q]) {
@@ -1293,7 +1313,8 @@ __global__ void moments_from_stage_data_kernel(const R *eqm, int Nx, int Nxp, do
 // Caller's weight-divided FP64 state [2][V][Nx] (in device memory) <-> deviation
 // rows [V][Nxp][2] in the state precision. state_in sets *bad if a value is not finite.
 template <typename R>
-__global__ void state_in_kernel(const double *src, R *dst, const double *frest, int V, int Nx, int Nxp, int *bad)
+__global__ void state_in_kernel(const double *src, R *dst, R *carry, const double *frest, int V, int Nx, int Nxp,
+                                int *bad)
 {
     const size_t n = 2 * (size_t)V * Nx;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -1301,18 +1322,23 @@ __global__ void state_in_kernel(const double *src, R *dst, const double *frest, 
         const int s = (int)(i - row * Nx);
         const double x = src[i];
         if (bad && !isfinite(x)) *bad = 1;
-        dst[2 * (v * Nxp + s) + fld] = R(x - frest[v]);
+        const double d = x - frest[v];
+        const R dr = R(d);
+        dst[2 * (v * Nxp + s) + fld] = dr;
+        if (carry) carry[2 * (v * Nxp + s) + fld] = R(d - (double)dr);
     }
 }
 
 template <typename R>
-__global__ void state_out_kernel(const R *src, double *dst, const double *frest, int V, int Nx, int Nxp)
+__global__ void state_out_kernel(const R *src, const R *carry, double *dst, const double *frest, int V, int Nx,
+                                 int Nxp)
 {
     const size_t n = 2 * (size_t)V * Nx;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t row = i / Nx, v = row % V, fld = row / V;
         const int s = (int)(i - row * Nx);
-        dst[i] = frest[v] + (double)src[2 * (v * Nxp + s) + fld];
+        const size_t k = 2 * (v * Nxp + s) + fld;
+        dst[i] = frest[v] + ((double)src[k] + (carry ? (double)carry[k] : 0.0));
     }
 }
 
@@ -1386,7 +1412,7 @@ cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStr
 {
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = cluster_config((unsigned)I.T.ntile, I.T.nchunk, smem, st, at);
-    if (I.T.half || I.T.lts) return cudaLaunchKernelEx(&cfg, stage_kernel<R, true>, I, stage, rel);
+    if (I.T.half || I.T.lts || I.T.comp) return cudaLaunchKernelEx(&cfg, stage_kernel<R, true>, I, stage, rel);
     return cudaLaunchKernelEx(&cfg, stage_kernel<R, false>, I, stage, rel);
 }
 
@@ -1456,18 +1482,20 @@ cudaError_t launch_moments_from_stage_data(const DevTables &T, const DevState &S
 }
 
 template <typename R>
-cudaError_t launch_state_in(const double *src, void *dst, const DevTables &T, int *bad, cudaStream_t st)
+cudaError_t launch_state_in(const double *src, void *dst, void *carry, const DevTables &T, int *bad, cudaStream_t st)
 {
     const int grid = (int)std::min<size_t>(4096, (2 * (size_t)T.V * T.Nx + 255) / 256);
-    state_in_kernel<R><<<grid, 256, 0, st>>>(src, static_cast<R *>(dst), T.frest, T.V, T.Nx, T.Nxp, bad);
+    state_in_kernel<R><<<grid, 256, 0, st>>>(src, static_cast<R *>(dst), static_cast<R *>(carry), T.frest, T.V,
+                                             T.Nx, T.Nxp, bad);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_state_out(const void *src, double *dst, const DevTables &T, cudaStream_t st)
+cudaError_t launch_state_out(const void *src, const void *carry, double *dst, const DevTables &T, cudaStream_t st)
 {
     const int grid = (int)std::min<size_t>(4096, (2 * (size_t)T.V * T.Nx + 255) / 256);
-    state_out_kernel<R><<<grid, 256, 0, st>>>(static_cast<const R *>(src), dst, T.frest, T.V, T.Nx, T.Nxp);
+    state_out_kernel<R><<<grid, 256, 0, st>>>(static_cast<const R *>(src), static_cast<const R *>(carry), dst,
+                                              T.frest, T.V, T.Nx, T.Nxp);
     return cudaGetLastError();
 }
 
@@ -1495,8 +1523,8 @@ cudaError_t launch_last_residuals(const Inst *insts, const int *slots, int n, do
     template cudaError_t stage_active_clusters<R>(size_t, int, bool, int *);                                          \
     template size_t equilibrium_smem_bytes<R>(int, int, int, int, int, int);                                         \
     template cudaError_t launch_moments_from_stage_data<R>(const DevTables &, const DevState &, cudaStream_t);  \
-    template cudaError_t launch_state_in<R>(const double *, void *, const DevTables &, int *, cudaStream_t);     \
-    template cudaError_t launch_state_out<R>(const void *, double *, const DevTables &, cudaStream_t);
+    template cudaError_t launch_state_in<R>(const double *, void *, void *, const DevTables &, int *, cudaStream_t); \
+    template cudaError_t launch_state_out<R>(const void *, const void *, double *, const DevTables &, cudaStream_t);
 LBC_INSTANTIATE(float)
 LBC_INSTANTIATE(double)
 

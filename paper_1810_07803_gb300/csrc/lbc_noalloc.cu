@@ -120,13 +120,13 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
     NA_TRY(cudaMemcpyAsync(scratch, ps.blob.data(), ps.blob.size(), cudaMemcpyHostToDevice, stream));
     // the array keeps the previous call's contents: clear everything that must start at zero
     NA_TRY(cudaMemsetAsync(static_cast<char *>(scratch) + table_bytes, 0, cv.off - table_bytes, stream));
-    NA_TRY(launch_state_in<R>(d_state, S.F[0], T, nullptr, stream));
+    NA_TRY(launch_state_in<R>(d_state, S.F[0], nullptr, T, nullptr, stream));
     NA_TRY(launch_moments_partial<R>(T, S, 0, stream));
     NA_TRY(launch_tile_equilibrium<R>(T, S, 0, stream));
     // the control block starts zeroed (the clear above): step 0, no early stop
     for (long k = 0; k < nsteps; ++k)
         for (int stage = 0; stage < 3; ++stage) NA_TRY(launch_stage<R>(I, smem, stage, (int)k, stream));
-    NA_TRY(launch_state_out<R>(S.F[0], d_state, T, stream));
+    NA_TRY(launch_state_out<R>(S.F[0], nullptr, d_state, T, stream));
     Ctl h_ctl;
     NA_TRY(cudaMemcpyAsync(&h_ctl, S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
     NA_TRY(cudaStreamSynchronize(stream));
@@ -153,6 +153,8 @@ extern "C" lbc_status lbc_step_noalloc(const lbc_params *params, double *d_state
     if (st != LBC_OK) return st;
     if (p.local_dt)   // the mass reference of local steps would not survive from one call to the next
         return fail_na(LBC_EINVAL, "local_dt is not available on the allocation-free path");
+    if (p.compensated)   // no room for the remainder buffer
+        return fail_na(LBC_EINVAL, "compensated is not available on the allocation-free path");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     return p.precision == LBC_FP32_STATE ? run_noalloc<float>(p, Nxe, Nye, d_state, nsteps, stream)
                                          : run_noalloc<double>(p, Nxe, Nye, d_state, nsteps, stream);

@@ -95,7 +95,7 @@ lbc_status rebuild_work(lbc_pool *P)
     P->nwork = (int)work.size();
     P->active = order;
     P->ext = false;
-    for (int s : order) P->ext = P->ext || P->inst[s].T.half || P->inst[s].T.lts;
+    for (int s : order) P->ext = P->ext || P->inst[s].T.half || P->inst[s].T.lts || P->inst[s].T.comp;
     // pageable sources: the copies are complete (staged) when cudaMemcpyAsync returns
     if (!work.empty())
         POOL_TRY(cudaMemcpyAsync(P->d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, P->stream));
@@ -391,8 +391,8 @@ lbc_status lbc_pool_get_state(lbc_pool *P, int s, double *state)
     if (st != LBC_OK) return st;
     if (!state) return fail(LBC_EINVAL, "NULL argument");
     const Inst &I = P->inst[s];
-    POOL_TRY(P->fp32 ? launch_state_out<float>(I.S.F[0], P->d_io, I.T, P->stream)
-                     : launch_state_out<double>(I.S.F[0], P->d_io, I.T, P->stream));
+    POOL_TRY(P->fp32 ? launch_state_out<float>(I.S.F[0], I.S.C, P->d_io, I.T, P->stream)
+                     : launch_state_out<double>(I.S.F[0], nullptr, P->d_io, I.T, P->stream));
     POOL_TRY(cudaMemcpyAsync(state, P->d_io, 2 * (size_t)I.T.V * I.T.Nx * sizeof(double), cudaMemcpyDeviceToHost,
                              P->stream));
     POOL_TRY(cudaStreamSynchronize(P->stream));

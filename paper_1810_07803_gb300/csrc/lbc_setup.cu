@@ -58,6 +58,9 @@ lbc_status validate(const lbc_params &p, int &Nxe, int &Nye)
     if (p.local_dt != 0 && p.local_dt != 1) return fail(LBC_EINVAL, "local_dt must be 0 or 1");
     if (p.local_dt && p.dt > 0.0) return fail(LBC_EINVAL, "local time steps are automatic: dt must be 0");
     if (p.half_channel != 0 && p.half_channel != 1) return fail(LBC_EINVAL, "half_channel must be 0 or 1");
+    if (p.compensated != 0 && p.compensated != 1) return fail(LBC_EINVAL, "compensated must be 0 or 1");
+    if (p.compensated && p.precision != LBC_FP32_STATE)
+        return fail(LBC_EINVAL, "compensated applies to the FP32 state only");
     if (p.half_channel && (p.T_left != p.T_right || p.u_left != -p.u_right))
         return fail(LBC_EINVAL, "the half channel needs symmetric walls: T_left = T_right, u_left = -u_right");
     if (p.precision != LBC_FP64 && p.precision != LBC_FP32_STATE) return fail(LBC_EINVAL, "unknown precision");
@@ -275,6 +278,7 @@ void bind_tables(const ProblemSetup &ps, const lbc_params &p, const void *dev, D
     T.tab_n = (int)ps.tabT.size();
     T.lts = p.local_dt;
     T.half = p.half_channel;
+    T.comp = p.compensated;
     T.mrest = ps.mrest;
     T.p0 = p.p0; T.dt = ps.dt; T.delta = p.delta; T.Pr = p.Pr; T.omega = p.omega;
     T.TL = p.T_left; T.TR = p.T_right; T.inL = ps.inL; T.inR = ps.inR;

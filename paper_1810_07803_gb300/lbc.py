@@ -38,12 +38,14 @@ class Params(C.Structure):
         ("Nx", C.c_int), ("stretch_A", C.c_double), ("Qx", C.c_int), ("Qy", C.c_int),
         ("Nexp_x", C.c_int), ("Nexp_y", C.c_int), ("p0", C.c_double), ("cfl", C.c_double),
         ("dt", C.c_double), ("precision", C.c_int), ("local_dt", C.c_int), ("half_channel", C.c_int),
+        ("compensated", C.c_int),
     ]
 
 
 DEFAULTS = dict(delta=1.0, u_left=0.0, u_right=0.0, T_left=1.0, T_right=1.0, Pr=2.0 / 3.0,
                 omega=0.5, Nx=64, stretch_A=0.0, Qx=4, Qy=4, Nexp_x=0, Nexp_y=0, p0=1.0,
-                cfl=0.5, dt=0.0, precision="fp64", local_dt=0, half_channel=0)
+                cfl=0.5, dt=0.0, precision="fp64", local_dt=0, half_channel=0,
+                compensated=0)
 
 
 MU_POWER, MU_TABLE = 0, 1
@@ -70,7 +72,7 @@ def make_params(d: dict) -> Params:
                  tab_mu=tabs[1], tab_Pr=tabs[2], tab_n=n, Nx=int(p["Nx"]), stretch_A=p["stretch_A"],
                  Qx=int(p["Qx"]), Qy=int(p["Qy"]), Nexp_x=int(p["Nexp_x"]), Nexp_y=int(p["Nexp_y"]),
                  p0=p["p0"], cfl=p["cfl"], dt=p["dt"], precision=int(prec), local_dt=int(p["local_dt"]),
-                 half_channel=int(p["half_channel"]))
+                 half_channel=int(p["half_channel"]), compensated=int(p["compensated"]))
     out._keep = keep
     return out
 

@@ -33,6 +33,7 @@ def test_exports_every_declared_symbol():
     (dict(local_dt=2), "local_dt"), (dict(local_dt=1, dt=1e-3), "automatic"), (dict(half_channel=3), "half_channel"),
     (dict(half_channel=1, u_left=0.1, u_right=0.1), "symmetric walls"),
     (dict(half_channel=1, T_left=0.9, T_right=1.1), "symmetric walls"),
+    (dict(compensated=2, precision="fp32"), "compensated"), (dict(compensated=1), "FP32 state only"),
 ])
 def test_create_rejects_bad_parameters(bad, msg):
     with pytest.raises(lbc.LbcError) as e:
