@@ -66,10 +66,11 @@ def small_solve(rng: np.random.Generator) -> dict:
                 stretch_A=math.sqrt(0.9), Qx=int(rng.integers(4, 9)), Qy=int(rng.integers(4, 9)))
 
 
-def make_trace(rate: float, duration: float, seed: int, draw=small_solve) -> list[Request]:
+def make_trace(rate: float, duration: float, seed: int, draw=small_solve, **extra) -> list[Request]:
+    """Requests of a Poisson trace; `extra` parameters (e.g. local_dt=1) go into every request."""
     times = poisson_arrivals(rate, duration, seed)
     rng = np.random.default_rng(seed + 1)
-    return [Request(k, float(t), draw(rng)) for k, t in enumerate(times)]
+    return [Request(k, float(t), dict(draw(rng), **extra)) for k, t in enumerate(times)]
 
 
 class Server:
@@ -168,6 +169,14 @@ def serve_sequential_fp64(requests: list[Request], residual: float = 1e-8, max_s
     return reqs
 
 
+def moment_error(m: np.ndarray, ref: np.ndarray) -> float:
+    """max over moments k of max_s |m_k - ref_k| / max(max_s |ref_k|, floor_k): floor 1 for
+    n, T and the pressures, 1e-2 for velocities, shear stress and heat flux."""
+    floors = np.array([1.0, 1e-2, 1e-2, 1.0, 1.0, 1.0, 1.0, 1e-2, 1e-2, 1e-2])
+    scale = np.maximum(np.max(np.abs(ref), axis=1), floors)
+    return float(np.max(np.max(np.abs(m - ref), axis=1) / scale))
+
+
 def summary(reqs: list[Request], label: str, rate: float, duration: float) -> dict:
     lat = np.array([r.latency for r in reqs])
     span = max(r.finished for r in reqs) if reqs else 0.0
@@ -187,20 +196,30 @@ def main():
     ap.add_argument("--cluster", type=int, default=4)
     ap.add_argument("--chunk", type=int, default=32)
     ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--local-dt", action="store_true", help="local pseudo-time steps in both servers")
+    ap.add_argument("--compensated", action="store_true", help="compensated FP32 state in the pool")
     ap.add_argument("--sequential-measure", type=int, default=3,
                     help="requests the FP64 sequential comparison solves and times (the rest are queued with "
                          "those service times)")
     args = ap.parse_args()
+    extra = dict(local_dt=1) if args.local_dt else {}
     for rate in (float(x) for x in args.rates.split(",")):
-        trace = make_trace(rate, args.duration, args.seed)
+        trace = make_trace(rate, args.duration, args.seed,
+                           **dict(extra, **(dict(compensated=1) if args.compensated else {})))
         srv = Server(cluster=args.cluster, residual=args.residual, chunk=args.chunk)
-        out = summary(srv.serve(trace), "pool-fp32", rate, args.duration)
+        served = srv.serve(trace)
+        out = summary(served, "pool-fp32", rate, args.duration)
         srv.close()
+        seq = make_trace(rate, args.duration, args.seed, **extra)
+        seq_out = serve_sequential_fp64(seq, args.residual, measure=args.sequential_measure)
+        # moment error of the pool's FP32 results against the FP64 solves of the same requests
+        errs = [moment_error(r.moments, q.moments) for r, q in zip(served, seq_out[:args.sequential_measure])]
+        out["moment_error_vs_fp64"] = max(errs) if errs else None
+        out["local_dt"], out["compensated"] = bool(args.local_dt), bool(args.compensated)
         print(json.dumps(out), flush=True)
-        seq = make_trace(rate, args.duration, args.seed)
-        out = summary(serve_sequential_fp64(seq, args.residual, measure=args.sequential_measure),
-                      "sequential-fp64", rate, args.duration)
+        out = summary(seq_out, "sequential-fp64", rate, args.duration)
         out["timing"] = f"{args.sequential_measure} solves measured, FIFO queue played with their service times"
+        out["local_dt"] = bool(args.local_dt)
         print(json.dumps(out), flush=True)
 
 
