@@ -227,6 +227,14 @@ lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, doubl
  *   LBC_ENOTCONV if any instance reached max_steps (the others' results hold).
  * lbc_batch_moments / get_state / set_state / info: as the single-solver calls,
  *   for instance i in [0, n).
+ * lbc_batch_set_states: states[i] (caller-owned host [2][V_i][Nx_i] float64, or
+ *   NULL to leave instance i as it is) for every instance in one call: all copies
+ *   and conversions are enqueued back to back and checked once; if any state
+ *   holds a NaN or Inf, no instance changes (LBC_EINVAL). Synchronises the
+ *   stream twice, where n calls of lbc_batch_set_state synchronise 2n times.
+ * lbc_batch_moments_all: the moments of every instance, the blocks
+ *   [LBC_NMOM][Nx_i] of instances 0 .. n-1 back to back in `out` (caller-owned,
+ *   sum_i LBC_NMOM Nx_i doubles); one synchronisation.
  * lbc_batch_shape: the launch shape (cluster size, work items, dynamic shared
  *   memory bytes of one stage CTA).
  * lbc_batch_autotune: for a batch whose instances have taken no step, times
@@ -242,6 +250,8 @@ lbc_status lbc_batch_run_to_steady(lbc_batch *b, double residual, long max_steps
 lbc_status lbc_batch_moments(lbc_batch *b, int i, double *out, double *x);
 lbc_status lbc_batch_get_state(lbc_batch *b, int i, double *state);
 lbc_status lbc_batch_set_state(lbc_batch *b, int i, const double *state);
+lbc_status lbc_batch_set_states(lbc_batch *b, const double *const *states);
+lbc_status lbc_batch_moments_all(lbc_batch *b, double *out);
 lbc_status lbc_batch_info(const lbc_batch *b, int i, int *Nx, int *V, double *dt, long *steps_taken);
 lbc_status lbc_batch_shape(const lbc_batch *b, int *cluster, int *nwork, size_t *smem_bytes);
 lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster);

@@ -469,6 +469,62 @@ lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
     return LBC_OK;
 }
 
+// Every given instance's state in one pass: copies and conversions back to back
+// through the staging buffer (reused in stream order), one check for all.
+lbc_status batch_set_states(lbc_batch *b, const double *const *states)
+{
+    if (!b || !states) return fail(LBC_EINVAL, "NULL argument");
+    LBC_CUDA_TRY(cudaMemsetAsync(b->d_bad, 0, sizeof(int), b->stream));
+    for (int i = 0; i < b->n; ++i) {
+        if (!states[i]) continue;
+        const Inst &I = b->inst[i];
+        const size_t bytes = 2 * (size_t)I.T.V * I.T.Nx * sizeof(double);
+        LBC_CUDA_TRY(cudaMemcpyAsync(b->d_io, states[i], bytes, cudaMemcpyHostToDevice, b->stream));
+        LBC_CUDA_TRY(b->fp32 ? launch_state_in<float>(b->d_io, I.S.F[1], I.S.C ? I.S.F[2] : nullptr, I.T, b->d_bad,
+                                                      b->stream)
+                             : launch_state_in<double>(b->d_io, I.S.F[1], nullptr, I.T, b->d_bad, b->stream));
+    }
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->h_bad, b->d_bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
+    LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (*b->h_bad) return fail(LBC_EINVAL, "a state holds a NaN or Inf; no instance changed");
+    bool any = false;
+    const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
+    for (int i = 0; i < b->n; ++i) {
+        if (states[i]) {
+            const Inst &I = b->inst[i];
+            const size_t bytes = 2 * (size_t)I.T.V * I.T.Nxp * esz;
+            b->h_ctl[i].nonfinite = 0;
+            LBC_CUDA_TRY(cudaMemcpyAsync(I.S.F[0], I.S.F[1], bytes, cudaMemcpyDeviceToDevice, b->stream));
+            if (I.S.C) LBC_CUDA_TRY(cudaMemcpyAsync(I.S.C, I.S.F[2], bytes, cudaMemcpyDeviceToDevice, b->stream));
+            lbc_status st = rebuild_stage_data(b, i);
+            if (st != LBC_OK) return st;
+        }
+        any = any || b->h_ctl[i].nonfinite;
+    }
+    lbc_status st = upload_ctl(b, 0, b->n);
+    if (st != LBC_OK) return st;
+    LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    b->poisoned = any;
+    return LBC_OK;
+}
+
+// The moments of every instance, back to back; one synchronisation.
+lbc_status batch_moments_all(lbc_batch *b, double *out)
+{
+    if (!b || !out) return fail(LBC_EINVAL, "NULL argument");
+    size_t off = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const Inst &I = b->inst[i];
+        LBC_CUDA_TRY(b->fp32 ? launch_moments_from_stage_data<float>(I.T, I.S, b->stream)
+                             : launch_moments_from_stage_data<double>(I.T, I.S, b->stream));
+        LBC_CUDA_TRY(cudaMemcpy2DAsync(out + off, I.T.Nx * sizeof(double), I.S.mom_out, I.T.Nxp * sizeof(double),
+                                       I.T.Nx * sizeof(double), LBC_NMOM, cudaMemcpyDeviceToHost, b->stream));
+        off += (size_t)LBC_NMOM * I.T.Nx;
+    }
+    return read_ctl(b);
+}
+
 // Times trial_steps steps per feasible cluster size (after one warm-up step) and
 // keeps the fastest; every instance starts and ends at the rest state.
 lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
@@ -575,6 +631,8 @@ lbc_status lbc_batch_run_to_steady(lbc_batch *b, double residual, long max_steps
 lbc_status lbc_batch_moments(lbc_batch *b, int i, double *out, double *x) { return batch_moments(b, i, out, x); }
 lbc_status lbc_batch_get_state(lbc_batch *b, int i, double *state) { return batch_get_state(b, i, state); }
 lbc_status lbc_batch_set_state(lbc_batch *b, int i, const double *state) { return batch_set_state(b, i, state); }
+lbc_status lbc_batch_set_states(lbc_batch *b, const double *const *states) { return batch_set_states(b, states); }
+lbc_status lbc_batch_moments_all(lbc_batch *b, double *out) { return batch_moments_all(b, out); }
 
 lbc_status lbc_batch_info(const lbc_batch *b, int i, int *Nx, int *V, double *dt, long *steps_taken)
 {

@@ -113,6 +113,8 @@ def lib():
         L.lbc_batch_moments.argtypes = [vp, C.c_int, dp, dp]
         L.lbc_batch_get_state.argtypes = [vp, C.c_int, dp]
         L.lbc_batch_set_state.argtypes = [vp, C.c_int, dp]
+        L.lbc_batch_set_states.argtypes = [vp, C.POINTER(dp)]
+        L.lbc_batch_moments_all.argtypes = [vp, dp]
         L.lbc_batch_info.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), dp, C.POINTER(C.c_long)]
         L.lbc_batch_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.lbc_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
@@ -348,6 +350,26 @@ class Batch:
     def set_state(self, i: int, f):
         ptr, keep = _state_ptr(f, self.V[i], self.Nx[i])
         _check(lib().lbc_batch_set_state(self._h, i, ptr))
+
+    def set_states(self, fs):
+        """Every instance's state in one call (lbc_batch_set_states); None leaves an instance as it is."""
+        ptrs, keep = (C.POINTER(C.c_double) * self.n)(), []
+        for i, f in enumerate(fs):
+            if f is not None:
+                p, k = _state_ptr(f, self.V[i], self.Nx[i])
+                ptrs[i] = p
+                keep.append(k)
+        _check(lib().lbc_batch_set_states(self._h, ptrs))
+
+    def moments_all(self):
+        """The moments of every instance (lbc_batch_moments_all), one [NMOM][Nx_i] array each."""
+        out = np.zeros(NMOM * sum(self.Nx))
+        _check(lib().lbc_batch_moments_all(self._h, _dptr(out)))
+        res, off = [], 0
+        for nx in self.Nx:
+            res.append(out[off:off + NMOM * nx].reshape(NMOM, nx))
+            off += NMOM * nx
+        return res
 
 
 class Pool:

@@ -157,3 +157,34 @@ def test_batch_rejects_mixed_precision_and_names_bad_instance():
     with pytest.raises(lbc.LbcError) as e:
         lbc.Batch([MIX[0], dict(MIX[1], Qx=0)])
     assert "instance 1" in str(e.value)
+
+
+def test_set_states_and_moments_all_match_the_single_calls():
+    """lbc_batch_set_states / lbc_batch_moments_all do what n single calls do; a
+    state with a NaN leaves every instance unchanged."""
+    ps = with_precision(MIX[:4], "fp32")
+    a, b = lbc.Batch(ps), lbc.Batch(ps)
+    fs = [workloads.perturbed_state(a.V[i], a.Nx[i], a.get_state(i), seed=30 + i) for i in range(len(ps))]
+    fs[2] = None                                   # instance 2 keeps its state
+    for i, f in enumerate(fs):
+        if f is not None:
+            a.set_state(i, f)
+    b.set_states(fs)
+    for i in range(len(ps)):
+        assert np.array_equal(a.get_state(i), b.get_state(i)), i
+    a.step(7)
+    b.step(7)
+    mall = b.moments_all()
+    for i in range(len(ps)):
+        assert np.array_equal(mall[i], b.moments(i)), i
+        assert np.array_equal(mall[i], a.moments(i)), i
+    before = [b.get_state(i) for i in range(len(ps))]
+    bad = [f.copy() if f is not None else None for f in fs]
+    bad[1][0, 3, 5] = np.nan
+    with pytest.raises(lbc.LbcError) as e:
+        b.set_states(bad)
+    assert e.value.status == lbc.EINVAL
+    for i in range(len(ps)):
+        assert np.array_equal(b.get_state(i), before[i]), i
+    a.close()
+    b.close()
