@@ -203,10 +203,20 @@ __device__ __forceinline__ void st2(float *p, f2 a) { *reinterpret_cast<unsigned
 __device__ __forceinline__ int row_bits(float x) { return __float_as_int(x); }
 __device__ __forceinline__ int row_bits(double x) { return (int)__double_as_longlong(x); }
 
+__device__ __forceinline__ f2 min2(f2 a, f2 b)
+{
+    float al, ah, bl, bh;
+    un2(a, al, ah);
+    un2(b, bl, bh);
+    return mk2(fminf(al, bl), fminf(ah, bh));
+}
+
 // WENO-5 (Jiang & Shu) on a packed pair, face between c and d, upwind cell c.
-// Nonlinear weights in product form, d_k prod_{m != k} E_m / sum, with the
-// E_m = (eps + beta_m)^2 first scaled by 1/max E_m (no overflow, two
-// reciprocals per pair instead of four per value).
+// The nonlinear weights d_k / (eps + beta_k)^2 in a form that FP32 holds: with
+// e_k = eps + beta_k scaled by 1/max e_m, as d_k prod_{m != k} e_m^2 over their
+// sum (two reciprocals per pair); where a warp meets e_m >= 1e12 (weight-divided
+// tails of hot-wall populations reach 1e10), whose squares would leave the FP32
+// range, as d_k (min e_m / e_k)^2 (the smoothest stencil keeps weight d_k).
 __device__ __forceinline__ f2 weno5_2(f2 a, f2 b, f2 c, f2 d, f2 e)
 {
     const f2 two = bc2(2.f), three = bc2(3.f), four = bc2(4.f), five = bc2(5.f);
@@ -220,14 +230,28 @@ __device__ __forceinline__ f2 weno5_2(f2 a, f2 b, f2 c, f2 d, f2 e)
     f2 e0 = fma2(k1312, t0 * t0, fma2(k025, t1 * t1, eps));
     f2 e1 = fma2(k1312, t2 * t2, fma2(k025, t3 * t3, eps));
     f2 e2 = fma2(k1312, t4 * t4, fma2(k025, t5 * t5, eps));
-    e0 = e0 * e0;
-    e1 = e1 * e1;
-    e2 = e2 * e2;
-    const f2 s = rcp2(max2(e0, max2(e1, e2)));
-    e0 = e0 * s;
-    e1 = e1 * s;
-    e2 = e2 * s;
-    const f2 a0 = bc2(0.1f) * (e1 * e2), a1 = bc2(0.6f) * (e0 * e2), a2 = bc2(0.3f) * (e0 * e1);
+    f2 a0, a1, a2;
+    const f2 mx = max2(e0, max2(e1, e2));
+    float ml, mh;
+    un2(mx, ml, mh);
+    if (__all_sync(0xffffffffu, fmaxf(ml, mh) < 1e12f)) {
+        const f2 s = rcp2(mx);
+        e0 = e0 * s;
+        e1 = e1 * s;
+        e2 = e2 * s;
+        e0 = e0 * e0;
+        e1 = e1 * e1;
+        e2 = e2 * e2;
+        a0 = bc2(0.1f) * (e1 * e2);
+        a1 = bc2(0.6f) * (e0 * e2);
+        a2 = bc2(0.3f) * (e0 * e1);
+    } else {
+        const f2 mn = min2(e0, min2(e1, e2));
+        const f2 r0 = mn * rcp2(e0), r1 = mn * rcp2(e1), r2 = mn * rcp2(e2);
+        a0 = bc2(0.1f) * (r0 * r0);
+        a1 = bc2(0.6f) * (r1 * r1);
+        a2 = bc2(0.3f) * (r2 * r2);
+    }
     const f2 num = fma2(a0, q0, fma2(a1, q1, a2 * q2));
     const f2 den = bc2(6.f) * (a0 + a1 + a2);
     return num * rcp2(den);
@@ -247,8 +271,20 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e)
     R e0 = eps + R(13.0 / 12.0) * t0 * t0 + R(0.25) * t1 * t1;
     R e1 = eps + R(13.0 / 12.0) * t2 * t2 + R(0.25) * t3 * t3;
     R e2 = eps + R(13.0 / 12.0) * t4 * t4 + R(0.25) * t5 * t5;
-    // nonlinear weights d_k / (eps + beta_k)^2 (each bounded by d_k / eps^2)
-    R a0 = R(0.1) * rcp<R>(e0 * e0), a1 = R(0.6) * rcp<R>(e1 * e1), a2 = R(0.3) * rcp<R>(e2 * e2);
+    R a0, a1, a2;
+    if constexpr (std::is_same<R, float>::value) {
+        // nonlinear weights as d_k (min e_m / e_k)^2: no square leaves the FP32 range
+        const R mn = fminf(e0, fminf(e1, e2));
+        const R r0 = mn * rcp<R>(e0), r1 = mn * rcp<R>(e1), r2 = mn * rcp<R>(e2);
+        a0 = R(0.1) * r0 * r0;
+        a1 = R(0.6) * r1 * r1;
+        a2 = R(0.3) * r2 * r2;
+    } else {
+        // nonlinear weights d_k / (eps + beta_k)^2 (each bounded by d_k / eps^2)
+        a0 = R(0.1) * rcp<R>(e0 * e0);
+        a1 = R(0.6) * rcp<R>(e1 * e1);
+        a2 = R(0.3) * rcp<R>(e2 * e2);
+    }
     return fdiv<R>(a0 * q0 + a1 * q1 + a2 * q2, R(6) * (a0 + a1 + a2));
 }
 
