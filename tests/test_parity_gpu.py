@@ -173,3 +173,19 @@ def test_full_size_c2_sampled(delta):
     e = moment_errors(s.moments(), o.moments())
     assert np.all(e < 1e-5), dict(zip(lbc.MOMENT_NAMES, e))
     s.close()
+
+
+def test_benchmark_launch_configuration_matches_oracle():
+    """The benchmark's exact configuration: the four delta solves of the single-large-solve
+    workload as one FP32 batch with the autotuned cluster size, 2 steps, each solve against
+    the oracle (1e-5), and the stage launch timed the way the benchmark times it."""
+    ps = [workloads.c2(d, precision="fp32") for d in workloads.C2_DELTAS]
+    b = lbc.Batch(ps)
+    b.autotune(2)
+    b.step_timed(2)
+    for i, p in enumerate(ps):
+        o = Oracle(p)
+        o.run(2)
+        e = moment_errors(b.moments(i), o.moments())
+        assert np.all(e < 1e-5), (p["delta"], dict(zip(lbc.MOMENT_NAMES, e)))
+    b.close()
