@@ -82,7 +82,7 @@ class Server:
     order deterministic for tests.
     """
 
-    def __init__(self, cluster: int = 4, precision: str = "fp32", budget_bytes: int = 16 << 30,
+    def __init__(self, cluster: int = 1, precision: str = "fp32", budget_bytes: int = 16 << 30,
                  residual: float = 1e-8, chunk: int = 32, max_steps: int = 200_000,
                  max_instances: int = 4096, pool=None):
         # `pool` replaces the device pool (same methods as lbc.Pool), e.g. to test the scheduling
@@ -193,7 +193,9 @@ def main():
     ap.add_argument("--rates", default="10,100,1000")
     ap.add_argument("--duration", type=float, default=10.0)
     ap.add_argument("--residual", type=float, default=1e-8)
-    ap.add_argument("--cluster", type=int, default=4)
+    ap.add_argument("--cluster", type=int, default=1,
+                    help="chunk CTAs per tile; 1 suits the small served requests (<= 256 velocities): more "
+                         "CTAs per tile add per-CTA overhead and measured lower solves/s")
     ap.add_argument("--chunk", type=int, default=32)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--local-dt", action="store_true", help="local pseudo-time steps in both servers")
