@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-steady", action="store_true", help="skip the steady-solves leg")
     ap.add_argument("--cluster", type=int, default=0,
                     help="chunk CTAs per tile of the batched launch (0: autotune; fix it to profile a shape)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
@@ -153,6 +154,40 @@ def cpu_baseline(seconds_target=12.0):
     dt = time.perf_counter() - t0
     return {"value": o.V * o.Nx * n / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": f"{n} RK-3 steps of the delta=1 solve (Nx=2048, 640 velocities), FP64, 1 thread"}
+
+
+def steady_leg(n=64, fp64_sample=2, residual=1e-8, seed=5):
+    """Steady solves/s: n small Couette solves (the serving workload's draw) as one FP32 batch
+    run to the residual, against the plain form, FP64 single solves one after the other, on the
+    first fp64_sample of them; both with local pseudo-time steps. Completion time of a batched
+    solve = batch time x its steps / the most steps (p50/p99 over the n)."""
+    import numpy as np
+    import torch
+    from paper_1810_07803_gb300 import lbc, serve
+    rng = np.random.default_rng(seed)
+    reqs = [dict(serve.small_solve(rng), local_dt=1) for _ in range(n)]
+    b = lbc.Batch([dict(r, precision="fp32") for r in reqs], cluster=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ks, _ = b.run_to_steady(residual, 200_000, raise_notconv=False)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    done = tb * np.asarray(ks, dtype=float) / max(ks)
+    err = 0.0
+    t64 = 0.0
+    for i in range(fp64_sample):
+        s = lbc.Solver(dict(reqs[i], precision="fp64"))
+        t0 = time.perf_counter()
+        s.run_to_steady(residual, 200_000)
+        t64 += time.perf_counter() - t0
+        err = max(err, serve.moment_error(b.moments(i), s.moments()))
+        s.close()
+    b.close()
+    return {"metric": "steady solves/s", "batched_fp32": n / tb, "plain_fp64": fp64_sample / t64,
+            "p50_s": float(np.percentile(done, 50)), "p99_s": float(np.percentile(done, 99)),
+            "moment_error_fp32_vs_fp64": err, "residual": residual,
+            "workload": f"{n} small Couette solves (Nx 32-160, Qx, Qy 4-8, delta 0.3-3; seed {seed}), local steps; "
+                        f"plain FP64 timed on {fp64_sample} of them"}
 
 
 def run_reference(args, rank):
@@ -298,6 +333,10 @@ def main():
         for s in s64:
             s.close()
 
+    steady = None
+    if not args.no_steady and args.precision == "fp32":
+        steady = steady_leg()
+
     peak, peak_kind = measured_hbm_peak()
     launches_per_step = 4   # one batched launch per RK stage (all solves) and the step-counter bump
     bpu = BYTES_PER_UPDATE_FP32 if args.precision == "fp32" else BYTES_PER_UPDATE_FP64
@@ -323,6 +362,8 @@ def main():
     }
     if fp64:
         line["fp64_plain"] = fp64
+    if steady:
+        line["steady"] = steady
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     batch.close()
