@@ -101,3 +101,14 @@ def test_create_rejects_bad_viscosity_tables(bad, msg):
         lbc.Solver(dict(mu_law="table", **bad))
     assert e.value.status == lbc.EINVAL
     assert msg in str(e.value)
+
+
+@pytest.mark.parametrize("opt,msg", [(dict(local_dt=1), "local_dt"), (dict(compensated=1, precision="fp32"), "compensated")])
+def test_noalloc_rejects_options_it_has_no_room_for(opt, msg):
+    """The allocation-free path refuses local steps (their reference mass would not survive from
+    one call to the next) and the compensated state (no remainder buffer), before any device
+    access: the state pointer below is never dereferenced."""
+    with pytest.raises(lbc.LbcError) as e:
+        lbc.step_noalloc(dict(Nx=16, Qx=4, Qy=4, **opt), 0x1000, 1)
+    assert e.value.status == lbc.EINVAL
+    assert msg in str(e.value)
