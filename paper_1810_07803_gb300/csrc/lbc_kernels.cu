@@ -9,7 +9,7 @@
 //      previous stage (or at set-up);
 //  (2) on a tile whose stencil reaches a wall, computes the wall density n_w
 //      from the outgoing WENO-5 wall flux (Eqs. diffuse, diffuse_nw);
-//  (3) streams the chunk's velocity rows through a TMA pipeline (kPipe stages
+//  (3) streams the chunk's velocity rows through a TMA pipeline (kPipe slots
 //      of kSubV rows, mbarrier completion): WENO-5 faces upwind by sign p_x,
 //      Shakhov target (Sec. II) with 1/tau of Eq. tau, TVD RK-3 combination,
 //      store, and the new stage's raw moments over the chunk's velocities;
@@ -19,6 +19,11 @@
 //      builds their next-stage data (moments, equilibrium factors by the
 //      stable Gauss-sum projection). On the last stage it also folds the
 //      residual max w |f^{n+1} - f^n|.
+// A second form of the kernels (kExt) adds what only some instances use: the
+// half channel's symmetry plane (ghosts from the opposite velocity), local
+// pseudo-time steps (each node's own step, the third stage's mass
+// renormalisation) and the compensated FP32 state (the third stage adds the
+// step's increment to d + c by TwoSum).
 // The state is the deviation d = ft - ft_rest from the weight-divided rest
 // Maxwellian (n = 1, u = 0, T = 1): WENO-5, the ghost extrapolation and the RK
 // combination are affine-invariant, so they act on d unchanged, and the FP32
