@@ -62,6 +62,12 @@ struct lbc_batch {
     bool poisoned = false;        // some instance holds a NaN/Inf
     cudaGraphExec_t graph = nullptr;
     bool ext = false;             // some instance uses the half channel or local steps
+    size_t io_elems = 0;          // doubles of the largest instance's host-layout state
+    // lbc_batch_set_states: a second staging buffer and a copy stream, so that the upload of
+    // one instance overlaps the conversion and stage data of the previous one (made at first use)
+    double *d_io2 = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
 };
 
 struct lbc_solver {
@@ -295,6 +301,7 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     const size_t ctl_off = sbytes, last_off = ctl_off + r256(n * sizeof(Ctl));
     const size_t io_off = last_off + r256(n * sizeof(double)), bad_off = io_off + r256(io_elems * sizeof(double));
     sbytes = bad_off + 256;
+    b->io_elems = io_elems;
     e = cudaMallocAsync(&b->state_block, sbytes, b->stream);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMallocAsync(state): ") + cudaGetErrorString(e));
@@ -469,20 +476,59 @@ lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
     return LBC_OK;
 }
 
-// Every given instance's state in one pass: copies and conversions back to back
-// through the staging buffer (reused in stream order), one check for all.
+// The second staging buffer, the copy stream and its events, made at the first
+// lbc_batch_set_states.
+lbc_status ensure_upload_pipeline(lbc_batch *b)
+{
+    if (b->copy_stream) return LBC_OK;
+    LBC_CUDA_TRY(cudaMallocAsync(&b->d_io2, b->io_elems * sizeof(double), b->stream));
+    LBC_CUDA_TRY(cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking));
+    LBC_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming));
+    for (int k = 0; k < 2; ++k) {
+        LBC_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_copied[k], cudaEventDisableTiming));
+        LBC_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_free[k], cudaEventDisableTiming));
+    }
+    return LBC_OK;
+}
+
+// Every given instance's state in one pass. Phase 1, per instance: the host copy on
+// the copy stream into one of two staging buffers, then on the batch's stream the
+// conversion into RK buffer 1 (a compensated state's remainders into buffer 2) and
+// the stage data of buffer 1 (free between steps), so the next instance's copy runs
+// under this instance's kernels. One check for all; only then phase 2 commits: the
+// buffer-1 state and stage data are copied to buffer 0 (local-step instances rebuild
+// buffer 0's stage data, which also holds their mass reference). A rejected set of
+// states changes nothing.
 lbc_status batch_set_states(lbc_batch *b, const double *const *states)
 {
     if (!b || !states) return fail(LBC_EINVAL, "NULL argument");
+    lbc_status st = ensure_upload_pipeline(b);
+    if (st != LBC_OK) return st;
     LBC_CUDA_TRY(cudaMemsetAsync(b->d_bad, 0, sizeof(int), b->stream));
+    LBC_CUDA_TRY(cudaEventRecord(b->ev_start, b->stream));   // earlier work on the staging buffers is done
+    LBC_CUDA_TRY(cudaStreamWaitEvent(b->copy_stream, b->ev_start, 0));
+    int k = 0;
     for (int i = 0; i < b->n; ++i) {
         if (!states[i]) continue;
         const Inst &I = b->inst[i];
+        const int slot = k & 1;
+        double *buf = slot ? b->d_io2 : b->d_io;
+        if (k >= 2) LBC_CUDA_TRY(cudaStreamWaitEvent(b->copy_stream, b->ev_free[slot], 0));
         const size_t bytes = 2 * (size_t)I.T.V * I.T.Nx * sizeof(double);
-        LBC_CUDA_TRY(cudaMemcpyAsync(b->d_io, states[i], bytes, cudaMemcpyHostToDevice, b->stream));
-        LBC_CUDA_TRY(b->fp32 ? launch_state_in<float>(b->d_io, I.S.F[1], I.S.C ? I.S.F[2] : nullptr, I.T, b->d_bad,
+        LBC_CUDA_TRY(cudaMemcpyAsync(buf, states[i], bytes, cudaMemcpyHostToDevice, b->copy_stream));
+        LBC_CUDA_TRY(cudaEventRecord(b->ev_copied[slot], b->copy_stream));
+        LBC_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev_copied[slot], 0));
+        LBC_CUDA_TRY(b->fp32 ? launch_state_in<float>(buf, I.S.F[1], I.S.C ? I.S.F[2] : nullptr, I.T, b->d_bad,
                                                       b->stream)
-                             : launch_state_in<double>(b->d_io, I.S.F[1], nullptr, I.T, b->d_bad, b->stream));
+                             : launch_state_in<double>(buf, I.S.F[1], nullptr, I.T, b->d_bad, b->stream));
+        LBC_CUDA_TRY(cudaEventRecord(b->ev_free[slot], b->stream));
+        if (!I.T.lts) {
+            LBC_CUDA_TRY(b->fp32 ? launch_moments_partial<float>(I.T, I.S, 1, b->stream)
+                                 : launch_moments_partial<double>(I.T, I.S, 1, b->stream));
+            LBC_CUDA_TRY(b->fp32 ? launch_tile_equilibrium<float>(I.T, I.S, 1, b->stream)
+                                 : launch_tile_equilibrium<double>(I.T, I.S, 1, b->stream));
+        }
+        ++k;
     }
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_bad, b->d_bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
@@ -497,12 +543,18 @@ lbc_status batch_set_states(lbc_batch *b, const double *const *states)
             b->h_ctl[i].nonfinite = 0;
             LBC_CUDA_TRY(cudaMemcpyAsync(I.S.F[0], I.S.F[1], bytes, cudaMemcpyDeviceToDevice, b->stream));
             if (I.S.C) LBC_CUDA_TRY(cudaMemcpyAsync(I.S.C, I.S.F[2], bytes, cudaMemcpyDeviceToDevice, b->stream));
-            lbc_status st = rebuild_stage_data(b, i);
-            if (st != LBC_OK) return st;
+            if (I.T.lts) {
+                st = rebuild_stage_data(b, i);
+                if (st != LBC_OK) return st;
+            } else {
+                const StateSizes z(I.T, b->fp32);
+                LBC_CUDA_TRY(cudaMemcpyAsync(I.S.eqm[0], I.S.eqm[1], z.eqm, cudaMemcpyDeviceToDevice, b->stream));
+                LBC_CUDA_TRY(cudaMemcpyAsync(I.S.eqg[0], I.S.eqg[1], z.eqg, cudaMemcpyDeviceToDevice, b->stream));
+            }
         }
         any = any || b->h_ctl[i].nonfinite;
     }
-    lbc_status st = upload_ctl(b, 0, b->n);
+    st = upload_ctl(b, 0, b->n);
     if (st != LBC_OK) return st;
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     b->poisoned = any;
@@ -700,6 +752,11 @@ void lbc_batch_destroy(lbc_batch *b)
 {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->copy_stream) cudaStreamSynchronize(b->copy_stream);
+    if (b->d_io2) cudaFreeAsync(b->d_io2, b->stream);
+    for (cudaEvent_t e : {b->ev_start, b->ev_copied[0], b->ev_copied[1], b->ev_free[0], b->ev_free[1]})
+        if (e) cudaEventDestroy(e);
+    if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
     if (b->state_block) cudaFreeAsync(b->state_block, b->stream);
     if (b->table_block) cudaFreeAsync(b->table_block, b->stream);
     if (b->h_ctl || b->h_last) cudaStreamSynchronize(b->stream);

@@ -188,3 +188,24 @@ def test_set_states_and_moments_all_match_the_single_calls():
         assert np.array_equal(b.get_state(i), before[i]), i
     a.close()
     b.close()
+
+
+def test_set_states_with_local_steps_and_compensated_instances():
+    """The batched upload builds most instances' stage data while later copies land;
+    local-step instances rebuild theirs (with the mass reference) after the check. Either
+    way the instances then step exactly as after single uploads."""
+    base = with_precision(MIX[:3], "fp32")
+    ps = [dict(base[0], local_dt=1, stretch_A=0.9), dict(base[1], compensated=1), base[2],
+          dict(base[0], compensated=1, local_dt=1, stretch_A=0.9)]
+    a, b = lbc.Batch(ps), lbc.Batch(ps)
+    fs = [workloads.perturbed_state(a.V[i], a.Nx[i], a.get_state(i), seed=50 + i) for i in range(len(ps))]
+    for i, f in enumerate(fs):
+        a.set_state(i, f)
+    b.set_states(fs)
+    a.step(9)
+    b.step(9)
+    for i in range(len(ps)):
+        assert np.array_equal(a.get_state(i), b.get_state(i)), i
+        assert np.array_equal(a.moments(i), b.moments(i)), i
+    a.close()
+    b.close()
