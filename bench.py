@@ -254,18 +254,24 @@ def time_steps(solvers, steps, warmup, flush):
 
 def time_batch(batch, steps, warmup, flush):
     """(ms per step, ms per stage launch) of a batch, L2 flushed between steps.
-    The step is timed with events around it on the current stream (the batch's
-    stream); the stage launches with events the library records around each."""
+    Steps go through the plain stepping call (lbc_batch_step), each timed with events
+    around it on the current stream (the batch's stream). A second pass of the same
+    number of steps times every stage launch with the events the library records
+    around each (lbc_batch_step_timed), for the roofline."""
     import torch
     batch.step(warmup)
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    stage_ms = 0.0
     for k in range(steps):
         flush.zero_()
         evs[k][0].record()
-        stage_ms += batch.step_timed(1)
+        batch.step(1)
         evs[k][1].record()
+    torch.cuda.synchronize()
+    stage_ms = 0.0
+    for k in range(steps):
+        flush.zero_()
+        stage_ms += batch.step_timed(1)
     torch.cuda.synchronize()
     return sum(a.elapsed_time(b) for a, b in evs) / steps, stage_ms / (3 * steps)
 
