@@ -86,7 +86,7 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
     st = choose_launch_shape(fp32, T);
     if (st != LBC_OK) return st;
     const size_t smem = stage_launch_smem(fp32, T);
-    const int V = T.V, Nx = T.Nx;
+    const int V = T.V;
 
     // ---- layout of the scratch array: tables, then the state ----
     Carve cv(scratch);
