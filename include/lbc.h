@@ -177,7 +177,8 @@ lbc_status lbc_moments(lbc_solver *s, double *out, double *x);
 lbc_status lbc_get_state(lbc_solver *s, double *state);
 lbc_status lbc_set_state(lbc_solver *s, const double *state);
 
-/* Sizes and constants of a created solver (any pointer may be NULL). */
+/* Sizes and constants of a created solver (any pointer may be NULL); dt is the
+ * global time step (with local_dt, the smallest node step). */
 lbc_status lbc_info(const lbc_solver *s, int *Nx, int *V, double *dt, long *steps_taken);
 
 /* Frees all device memory of the solver (stream-ordered). NULL is a no-op. */
