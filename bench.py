@@ -27,7 +27,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-velocity updates/s"
 FALLBACK_HBM_GBS = 6800.0
-BYTES_PER_UPDATE_FP32 = 64   # 16 state values per cell-velocity step
+BYTES_PER_UPDATE_FP32 = 64   # 16 state values per cell-velocity step: each stage reads its input (and, after
+                              # the first, the RK base) and writes its output, both fields: (2+3+3) x 2 values
 BYTES_PER_UPDATE_FP64 = 128
 
 
