@@ -128,13 +128,18 @@ class Server:
             vclock += 1.0
             t = now()
             for slot, r in list(active.items()):
+                # an instance that did not converge in this chunk took all of its steps, so
+                # its count is kept here; the pool is asked only about those that leave
+                if slot not in done:
+                    r.steps += self.chunk
+                    if r.steps < self.max_steps:
+                        continue
                 _, _, _, steps, res = self.pool.info(slot)
-                if slot in done or steps >= self.max_steps:
-                    r.finished, r.steps, r.residual = t, steps, res
-                    r.converged = slot in done
-                    r.moments = self.pool.moments(slot)
-                    self.pool.remove(slot)
-                    del active[slot]
+                r.finished, r.steps, r.residual = t, steps, res
+                r.converged = slot in done
+                r.moments = self.pool.moments(slot)
+                self.pool.remove(slot)
+                del active[slot]
         return reqs
 
 
