@@ -499,11 +499,22 @@ lbc_status ensure_upload_pipeline(lbc_batch *b)
 // buffer-1 state and stage data are copied to buffer 0 (local-step instances rebuild
 // buffer 0's stage data, which also holds their mass reference). A rejected set of
 // states changes nothing.
+lbc_status upload_states(lbc_batch *b, const double *const *states);
+
 lbc_status batch_set_states(lbc_batch *b, const double *const *states)
 {
     if (!b || !states) return fail(LBC_EINVAL, "NULL argument");
     lbc_status st = ensure_upload_pipeline(b);
     if (st != LBC_OK) return st;
+    st = upload_states(b, states);
+    // on any failure no copy from the caller's host arrays is left in flight
+    if (st != LBC_OK && b->copy_stream) cudaStreamSynchronize(b->copy_stream);
+    return st;
+}
+
+lbc_status upload_states(lbc_batch *b, const double *const *states)
+{
+    lbc_status st = LBC_OK;
     LBC_CUDA_TRY(cudaMemsetAsync(b->d_bad, 0, sizeof(int), b->stream));
     LBC_CUDA_TRY(cudaEventRecord(b->ev_start, b->stream));   // earlier work on the staging buffers is done
     LBC_CUDA_TRY(cudaStreamWaitEvent(b->copy_stream, b->ev_start, 0));
