@@ -82,3 +82,15 @@ def test_summary_percentiles():
     assert s["latency_p50_s"] == pytest.approx(50.5)
     assert s["latency_p99_s"] == pytest.approx(99.01)
     assert s["solves_per_s"] == pytest.approx(1.0)
+
+
+def test_request_stopped_at_the_step_cap():
+    """A request that does not converge leaves at max_steps, unconverged, with the pool's own
+    step count; the others are unaffected (the loop counts running requests' steps itself)."""
+    reqs = [serve.Request(0, 0.0, dict(rid=0, work=1000)), serve.Request(1, 0.0, dict(rid=1, work=64))]
+    pool = FakePool(capacity=2)
+    srv = serve.Server(residual=1e-8, chunk=32, max_steps=128, pool=pool)
+    out = {r.rid: r for r in srv.serve(reqs, clock="steps")}
+    assert not out[0].converged and out[0].steps == 128
+    assert out[1].converged and out[1].steps == 64
+    assert [rid for kind, rid in pool.log if kind == "remove"] == [1, 0]
