@@ -36,12 +36,14 @@ SQ2 = math.sqrt(2.0)
 
 
 def model(delta: float, Qx: int, Nx_exp: int, S: int, omega: float, Pr: float, Qy: int = 7,
-          Ny_exp: int = 6, precision: str = "fp64", half: bool = True, local: bool = True) -> dict:
+          Ny_exp: int = 6, precision: str = "fp64", half: bool = True, local: bool = True,
+          compensated: bool = False) -> dict:
     """HHLB(Nx_exp;Qx) x HLB(Ny_exp;Qy) on S nodes per half channel (A = 0.98, u_w = sqrt(2));
     half=False solves the full channel on 2 S nodes."""
     return dict(delta=delta, u_left=-SQ2, u_right=SQ2, T_left=1.0, T_right=1.0, Pr=Pr, omega=omega,
                 Nx=S if half else 2 * S, half_channel=int(half), local_dt=int(local), stretch_A=0.98, Qx=Qx,
-                Qy=Qy, Nexp_x=Nx_exp, Nexp_y=Ny_exp, precision=precision)
+                Qy=Qy, Nexp_x=Nx_exp, Nexp_y=Ny_exp, precision=precision,
+                compensated=int(compensated and precision == "fp32"))
 
 
 def production(delta: float, omega: float, Pr: float, **kw) -> dict:
@@ -72,11 +74,11 @@ def pi_number(moments: np.ndarray) -> tuple[float, float]:
 def convergence_study(deltas=(0.1, 1.0, 10.0), omega: float = 0.66, Pr: float = 2.0 / 3.0,
                       precision: str = "fp64", chunk: int = 20000, tol: float = 2e-7,
                       max_steps: int = 2_000_000, progress=None, half: bool = True,
-                      local: bool = True) -> list[dict]:
+                      local: bool = True, compensated: bool = False) -> list[dict]:
     """Steps all models together in chunks until every Pi changes by less than
     tol (relative) over a chunk, or max_steps; returns one row per delta."""
     ps = []
-    kw = dict(precision=precision, half=half, local=local)
+    kw = dict(precision=precision, half=half, local=local, compensated=compensated)
     for d in deltas:
         ps += [production(d, omega, Pr, **kw), reference(d, omega, Pr, **kw)]
     b = lbc.Batch(ps)
@@ -109,7 +111,8 @@ def convergence_study(deltas=(0.1, 1.0, 10.0), omega: float = 0.66, Pr: float = 
                     "relative_difference_extrapolated": rows[0]["extrapolated"] / rows[1]["extrapolated"] - 1.0,
                     "last_chunk_drift": [rows[0]["drift"], rows[1]["drift"]],
                     "Pxy_spread": [rows[0]["spread"], rows[1]["spread"]], "steps": steps,
-                    "precision": precision, "half_channel": half, "local_dt": local})
+                    "precision": precision, "compensated": compensated, "half_channel": half,
+                    "local_dt": local})
     b.close()
     return out
 
@@ -126,13 +129,14 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp32", "fp64"])
     ap.add_argument("--full-channel", action="store_true", help="solve -1/2 < x < 1/2 on 2 S nodes")
     ap.add_argument("--global-dt", action="store_true", help="one time step for every node")
+    ap.add_argument("--compensated", action="store_true", help="FP32 only: compensated state")
     ap.add_argument("--max-steps", type=int, default=2_000_000)
     ap.add_argument("--chunk", type=int, default=20000)
     args = ap.parse_args()
     rows = convergence_study(tuple(float(x) for x in args.deltas.split(",")), args.omega,
                              precision=args.precision, chunk=args.chunk, max_steps=args.max_steps,
                              progress=lambda k, pis: print(json.dumps({"steps": k, "Pi": pis}), flush=True),
-                             half=not args.full_channel, local=not args.global_dt)
+                             half=not args.full_channel, local=not args.global_dt, compensated=args.compensated)
     for row in rows:
         print(json.dumps(row), flush=True)
 
