@@ -270,7 +270,9 @@ void lbc_batch_destroy(lbc_batch *b);
  *
  * lbc_pool_create: cluster = chunk CTAs per tile for every instance, in
  *   [1, 16] (instances whose velocity set needs more rows per CTA than 256 or
- *   more shared memory than one CTA has are rejected); precision of every
+ *   more shared memory than one CTA has are rejected; for instances of at most
+ *   256 velocities, 1 gives the most solves per second under load, larger
+ *   clusters the lower latency at light load); precision of every
  *   instance; budget_bytes = device bytes the instances (tables and state, as
  *   lbc_pool_footprint) may use in total -- the pool adds a fixed part (slots,
  *   work list) and one staging buffer for state transfers of the largest
@@ -285,7 +287,8 @@ void lbc_batch_destroy(lbc_batch *b);
  * lbc_pool_remove: frees the slot (stream-ordered).
  * lbc_pool_run: advances every instance up to nsteps steps; an instance stops
  *   at its first step whose residual (as lbc_run_to_steady) is below
- *   `residual`. finished[] (caller-owned, max_instances entries, may be NULL)
+ *   `residual`, and one that does not converge takes exactly nsteps steps (a
+ *   caller may count those itself). finished[] (caller-owned, max_instances entries, may be NULL)
  *   receives the slots that converged and were not reported before,
  *   *nfinished their count; a reported instance left in the pool takes no
  *   further steps. Synchronises the stream.
