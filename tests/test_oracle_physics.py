@@ -106,3 +106,61 @@ def test_navier_stokes_limit():
     np.testing.assert_allclose(m[7][bulk], (-mu * dudx)[bulk], rtol=2e-4)
     # and Pi -> 1/delta (Eq. Pi with u_w -> the slip-free velocity jump) to O(1/delta)
     assert abs(-m[7][16] / (2 * uw) * delta * SQ2 - 1) < 0.05
+
+
+@pytest.mark.parametrize("delta,Q", [(1.0, 5), (10.0, 6)])
+def test_steady_momentum_flux_and_shear_stress_uniform(delta, Q):
+    """Steady state at finite delta (Sec. II, Eq. boltz_red): with a collision term
+    that conserves y-momentum (N >= 4), the y-momentum balance of the reduced
+    equation makes the p_y-momentum flux through every interface the same. The
+    interface fluxes are recovered from L = dphi/dt by the flux-form telescoping
+    G_{s+1/2} - G_{1/2} = -sum_{k <= s} J_k deta sum_v w_v p_y L_v,k; they are uniform
+    to the residual. The nodal P_xy is the same flux seen through the nodes: in the
+    central half of the channel (away from the walls' kinetic layers) it is uniform to
+    the WENO-5 truncation error, which falls at the scheme's order under refinement;
+    the mass flux n u_x vanishes to the same truncation."""
+    spreads = []
+    for Nx in (16, 32):
+        o = Oracle(dict(Nx=Nx, Qx=Q, Qy=Q, delta=delta, u_left=-0.1, u_right=0.1, omega=0.5))
+        k, r = o.run_to_steady(1e-12, 400000)
+        assert r < 1e-12
+        L, _ = o.rhs()
+        dmom = (o.w * o.py) @ L[0]                       # d/dt (n u_y) per node
+        G = np.cumsum(o.J * o.deta * dmom)               # G_{s+1/2} - G_{1/2}, up to sign
+        m = o.moments()
+        pxy = m[7]
+        assert np.max(np.abs(G)) < 1e-9 * abs(pxy.mean()) + 100 * r
+        bulk = slice(Nx // 4, 3 * Nx // 4)
+        spreads.append((pxy[bulk].max() - pxy[bulk].min()) / abs(pxy.mean()))
+        assert np.max(np.abs(m[0] * m[1])) < 1e-5 * 16 / Nx
+    # WENO-5 is fifth order on smooth profiles: at least a factor 2^4 per halving of the spacing
+    assert spreads[1] < spreads[0] / 16, spreads
+    assert spreads[1] < 1e-6, spreads
+
+
+def test_outgoing_ghosts_extrapolate_cubics_exactly():
+    """The outgoing ghost nodes beyond each wall extrapolate the last four nodes by the
+    cubic through them (reading R6 of the wall treatment; the paper's discrete form is
+    silent): on rows that are cubics in the node index, the advection of the outgoing
+    populations at the two nodes next to a wall equals that of the same cubic on a grid
+    where the ghost positions are real nodes. A lower-order extrapolation differs by a
+    multiple of the rows' third difference."""
+    Nx, ext, Q = 12, 4, 4
+    small = Oracle(dict(Nx=Nx, Qx=Q, Qy=Q, delta=0.0))
+    big = Oracle(dict(Nx=Nx + 2 * ext, Qx=Q, Qy=Q, delta=0.0))
+    rng = np.random.default_rng(7)
+    c = rng.uniform(-1, 1, size=(2, small.V, 4)) * np.array([1.0, 0.3, 0.05, 0.004])
+    s_big = np.arange(Nx + 2 * ext) - ext - (Nx - 1) / 2          # node index, centred
+    rows = np.einsum("fvk,ks->fvs", c, np.vstack([s_big ** k for k in range(4)])) + 2.0
+    big.set_state(rows)
+    small.set_state(rows[:, :, ext:ext + Nx].copy())
+    L_small, _ = small.rhs()
+    L_big, _ = big.rhs()
+    # uniform grids (J = 1): L deta is the flux difference, independent of the spacing
+    a = L_small * small.deta
+    b = L_big[:, :, ext:ext + Nx] * big.deta
+    right, left = small.px > 0, small.px < 0
+    scale = np.max(np.abs(b))
+    for nodes, rows_sel in (([Nx - 1, Nx - 2], right), ([0, 1], left)):
+        d = np.abs(a[:, rows_sel][:, :, nodes] - b[:, rows_sel][:, :, nodes])
+        assert np.max(d) < 1e-12 * scale, np.max(d) / scale
