@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-steady", action="store_true", help="skip the steady-solves leg")
+    ap.add_argument("--no-single", action="store_true", help="skip the single-solve leg")
     ap.add_argument("--cluster", type=int, default=0,
                     help="chunk CTAs per tile of the batched launch (0: autotune; fix it to profile a shape)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
@@ -48,11 +49,11 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(precision="fp32"):
+def workload_config():
     return {"workload": "single large solve: Nx=2048 tanh-stretched (spacing ratio 10), "
                         "HHLB(15;16)xHLB(19;20) = 640 velocities, delta in {0.1,1,10,100}, "
                         "u_w=+-0.1*sqrt(2kT/m), omega=0.66, Pr=2/3",
-            "solves_per_step": 4, "Nx": 2048, "velocities": 640, "state": precision,
+            "solves_per_step": 4, "Nx": 2048, "velocities": 640,
             "l2": "flushed between timed steps (256 MiB write)", "data": "synthetic"}
 
 
@@ -141,79 +142,121 @@ def profiled_traffic(precision: str):
         return None
 
 
-def cpu_baseline(seconds_target=12.0):
-    """The FP64 oracle as it stands, one host core, on a bounded sample: whole
-    RK-3 steps of the delta = 1 solve of the same workload."""
+def cpu_baseline(seconds_target=8.0):
+    """The FP64 oracle as it stands, on the host cores, on bounded samples of the same
+    workload: whole RK-3 steps of the delta = 1 solve, with the OpenMP build of the oracle
+    on every core (the reported value) and with the plain build on one core; and the small
+    configuration (Nx = 64, 8 x 4 velocities, FP64) run to r < 1e-10 on one core."""
     from oracle.oracle import Oracle
     from paper_1810_07803_gb300 import workloads
-    o = Oracle(workloads.c2(1.0, precision="fp64"))
-    t0 = time.perf_counter()
-    n = 0
-    while time.perf_counter() - t0 < seconds_target:
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    out = {}
+    for parallel in (True, False):
+        o = Oracle(workloads.c2(1.0, precision="fp64"), parallel=parallel)
         o.run(1)
-        n += 1
-    dt = time.perf_counter() - t0
-    return {"value": o.V * o.Nx * n / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{n} RK-3 steps of the delta=1 solve (Nx=2048, 640 velocities), FP64, 1 thread"}
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < seconds_target:
+            o.run(1)
+            n += 1
+        dt = time.perf_counter() - t0
+        out[parallel] = (o.V * o.Nx * n / dt, n)
+    o = Oracle(workloads.c1())
+    t0 = time.perf_counter()
+    k, r = o.run_to_steady(1e-10, 200000)
+    t1 = time.perf_counter() - t0
+    return {"value": out[True][0], "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{out[True][1]} RK-3 steps of the delta=1 solve (Nx=2048, 640 velocities), FP64, "
+                      f"OpenMP build of the oracle on {cores} threads",
+            "single_core": {"value": out[False][0], "unit": METRIC, "cores": 1,
+                            "sample": f"{out[False][1]} RK-3 steps of the same solve, plain build, 1 thread"},
+            "small_config_to_steady": {"steps": k, "residual": r, "seconds": t1, "solves_per_s": 1.0 / t1,
+                                       "cores": 1, "workload": "Nx=64 uniform, 8x4 velocities, delta=1, FP64, "
+                                                               "rest start to r < 1e-10"}}
 
 
-def steady_leg(n=64, fp64_sample=2, residual=1e-8, seed=5):
-    """Steady solves/s: n small Couette solves (the serving workload's draw) as one FP32 batch
-    run to the residual, against the plain form, FP64 single solves one after the other, on the
-    first fp64_sample of them; both with local pseudo-time steps. Completion time of a batched
-    solve = batch time x its steps / the most steps (p50/p99 over the n)."""
+def steady_leg(n=64, fp64_sample=8, residual=1e-8, seed=5):
+    """Steady solves/s: n small Couette solves (the serving workload's draw) as one batch
+    with the compensated FP32 state, run to the residual, against the plain form, FP64 single
+    solves one after the other, on the first fp64_sample of them; both with local
+    pseudo-time steps. Each arm's moments are compared with the limit: an FP64 batch of the
+    same solves run to r < 1e-12 (not timed). Completion time of a batched solve = batch
+    time x its steps / the most steps (p50/p99 over the n)."""
     import numpy as np
     import torch
     from paper_1810_07803_gb300 import lbc, serve
     rng = np.random.default_rng(seed)
     reqs = [dict(serve.small_solve(rng), local_dt=1) for _ in range(n)]
-    b = lbc.Batch([dict(r, precision="fp32") for r in reqs], cluster=1)
+    ref = lbc.Batch([dict(r, precision="fp64") for r in reqs], cluster=1)
+    ref.run_to_steady(1e-12, 2_000_000, raise_notconv=False)
+    limit = [ref.moments(i) for i in range(n)]
+    ref.close()
+    b = lbc.Batch([dict(r, precision="fp32", compensated=1) for r in reqs], cluster=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ks, _ = b.run_to_steady(residual, 200_000, raise_notconv=False)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     done = tb * np.asarray(ks, dtype=float) / max(ks)
-    err = 0.0
+    err32 = max(serve.moment_error(b.moments(i), limit[i]) for i in range(n))
+    b.close()
+    err64 = 0.0
     t64 = 0.0
     for i in range(fp64_sample):
         s = lbc.Solver(dict(reqs[i], precision="fp64"))
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.run_to_steady(residual, 200_000)
         t64 += time.perf_counter() - t0
-        err = max(err, serve.moment_error(b.moments(i), s.moments()))
+        err64 = max(err64, serve.moment_error(s.moments(), limit[i]))
         s.close()
-    b.close()
     return {"metric": "steady solves/s", "batched_fp32": n / tb, "plain_fp64": fp64_sample / t64,
             "p50_s": float(np.percentile(done, 50)), "p99_s": float(np.percentile(done, 99)),
-            "moment_error_fp32_vs_fp64": err, "residual": residual,
+            "moment_error_batched_fp32": err32, "moment_error_plain_fp64": err64, "residual": residual,
+            "reference": "each solve's FP64 steady state to r < 1e-12 (max over moments of the normalised error)",
             "workload": f"{n} small Couette solves (Nx 32-160, Qx, Qy 4-8, delta 0.3-3; seed {seed}), local steps; "
-                        f"plain FP64 timed on {fp64_sample} of them"}
+                        f"batched arm: compensated FP32 state; plain FP64 timed on {fp64_sample} of them"}
 
 
-def run_reference(args, rank):
+def run_reference(args, rank, budget_s=150.0):
+    """The FP64 oracle as it stands on every host core (its OpenMP build), on the same
+    workload and metric: a step is one RK-3 step of all four solves. If K steps of the
+    whole workload would exceed the time budget, each timed step is a bounded sample of
+    it (one solve, rotating) and the units follow the sample."""
     if rank != 0:
         return
     from oracle.oracle import Oracle
     from paper_1810_07803_gb300 import workloads
-    solves = [Oracle(workloads.c2(d, precision="fp64")) for d in workloads.C2_DELTAS]
-    for k in range(args.warmup):
-        solves[k % 4].run(1)
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    solves = [Oracle(workloads.c2(d, precision="fp64"), parallel=True) for d in workloads.C2_DELTAS]
+    t0 = time.perf_counter()
+    for o in solves:
+        o.run(1)
+    full_step = time.perf_counter() - t0
+    per_step = 1 if full_step * (args.steps + args.warmup) > budget_s else len(solves)
+    for k in range(max(0, args.warmup - 1)):
+        for j in range(per_step):
+            solves[(k * per_step + j) % 4].run(1)
     times = []
     for k in range(args.steps):
-        o = solves[k % 4]
         t0 = time.perf_counter()
-        o.run(1)
+        for j in range(per_step):
+            solves[(k * per_step + j) % 4].run(1)
         times.append(time.perf_counter() - t0)
-    per_step = sum(times) / len(times)
-    value = solves[0].V * solves[0].Nx / per_step
+    ms = sum(times) / len(times) * 1e3
+    value = per_step * solves[0].V * solves[0].Nx / (ms / 1e3)
+    sample = ("each step: one RK-3 step of all four solves" if per_step == 4 else
+              "each step: one RK-3 step of one of the four solves (rotating), the whole workload's step "
+              "exceeding the time budget")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(workload_config("fp64"), solves_per_step=1,
-                                                 sample="each step: one RK-3 step of one of the four solves"),
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} single-solve RK-3 steps, rotating over the four deltas"},
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed steps; {sample}; OpenMP build of the oracle, "
+                                       f"{cores} threads, FP64"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -340,6 +383,22 @@ def main():
         for s in s64:
             s.close()
 
+    # the single-solve path: one solve (delta = 1) through the single-instance stage kernel
+    single = None
+    if not args.no_single:
+        one = lbc.Batch([workloads.c2(1.0, precision=args.precision)])
+        one.autotune(3)
+        ms1, launch1 = time_batch(one, max(3, min(args.steps, 200)), args.warmup, flush)
+        units1 = V * Nx
+        peak1, _ = measured_hbm_peak()
+        ach1 = BYTES_PER_UPDATE_FP32 * units1 / 3 / (launch1 / 1e3) / 1e9 if args.precision == "fp32" else \
+            BYTES_PER_UPDATE_FP64 * units1 / 3 / (launch1 / 1e3) / 1e9
+        single = {"value": units1 * world / (ms1 / 1e3), "unit": METRIC, "ms_per_step": ms1, "launch_ms": launch1,
+                  "cluster": one.shape()[0], "kernel": "stage_kernel (single instance, descriptor as a parameter)",
+                  "roofline": {"bound": "hbm", "achieved": ach1, "peak": peak1, "unit": "GB/s", "frac": ach1 / peak1},
+                  "workload": "the delta=1 solve alone (Nx=2048, 640 velocities) through lbc_step's kernel"}
+        one.close()
+
     steady = None
     if not args.no_steady and args.precision == "fp32":
         steady = steady_leg()
@@ -353,8 +412,9 @@ def main():
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": dict(workload_config(args.precision), cluster=cluster,
-                       launch="one batched stage launch per RK stage for the four solves"),
+        "config": workload_config(),
+        "launch": {"cluster": cluster, "form": "one batched stage launch per RK stage for the four solves",
+                   "state": args.precision},
         "e2e": {"value": units * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "path": "per step: lbc_batch_set_states(pinned host f64, every solve) + lbc_batch_step(1) + "
@@ -367,6 +427,8 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
+    if single:
+        line["single"] = single
     if fp64:
         line["fp64_plain"] = fp64
     if steady:

@@ -313,12 +313,17 @@ void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
     int Nx = P->Nx, V = nvel(P), Qy = P->Qy;
     long fs = (long)V * Nx;
     double *fwl = malloc(sizeof(double) * V), *fwr = malloc(sizeof(double) * V);
-    double *ext = malloc(sizeof(double) * (Nx + 4));      /* ext[s+2] = cell s */
     double *face = malloc(sizeof(double) * (Nx + 1) * 2 * V); /* [field][v][Nx+1] */
     wall_maxwellians(P, fwl, fwr);
 
     /* 1) faces of outgoing populations, with cubically extrapolated ghosts
-     *    (in the uniform eta coordinate, Eq. stretch). */
+     *    (in the uniform eta coordinate, Eq. stretch). Rows are independent: the
+     *    OpenMP build of this file splits them over threads, each with its own
+     *    extended row ext[s+2] = cell s; without OpenMP the block runs once. */
+#pragma omp parallel
+    {
+    double *ext = malloc(sizeof(double) * (Nx + 4));
+#pragma omp for collapse(2) schedule(static)
     for (int fld = 0; fld < 2; ++fld)
         for (int v = 0; v < V; ++v) {
             const double *row = f + fld * fs + (long)v * Nx;
@@ -341,6 +346,9 @@ void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
             }
         }
 
+    free(ext);
+    }
+
     /* 2) n_w from zero mass flux through each wall (Eq. diffuse_nw), phi only. */
     double outL = 0, outR = 0, inL = 0, inR = 0;
     for (int v = 0; v < V; ++v) {
@@ -353,6 +361,10 @@ void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
     if (nw_out) { nw_out[0] = nwL; nw_out[1] = nwR; }
 
     /* 3) remaining faces; incoming ghosts and wall faces = n_w f_w (chi: T_w n_w f_w). */
+#pragma omp parallel
+    {
+    double *ext = malloc(sizeof(double) * (Nx + 4));
+#pragma omp for collapse(2) schedule(static)
     for (int fld = 0; fld < 2; ++fld)
         for (int v = 0; v < V; ++v) {
             const double *row = f + fld * fs + (long)v * Nx;
@@ -390,9 +402,15 @@ void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
             }
         }
 
+    free(ext);
+    }
+
     /* 4) L = -(p_x / (J deta)) (F_{s+1/2} - F_{s-1/2}) - (f - f_eq (1 + S)) / tau. */
+#pragma omp parallel
+    {
     double *tphi = malloc(sizeof(double) * V), *tchi = malloc(sizeof(double) * V);
     double m[M_COUNT];
+#pragma omp for schedule(static)
     for (int s = 0; s < Nx; ++s) {
         orc_cell_moments(P, f + s, f + fs + s, Nx, m);
         orc_target(P, m, tphi, tchi);
@@ -406,8 +424,10 @@ void orc_rhs(const orc_problem *P, const double *f, double *L, double *nw_out)
                     -px_of(P, v) * (F[s + 1] - F[s]) / (P->J[s] * P->deta) - nu * (fv - tgt);
             }
     }
+    free(tphi); free(tchi);
+    }
     (void)Qy;
-    free(tphi); free(tchi); free(fwl); free(fwr); free(ext); free(face);
+    free(fwl); free(fwr); free(face);
 }
 
 /* ---- TVD RK-3 (Shu & Osher) over a generic right-hand side --------------- */
@@ -418,10 +438,13 @@ void orc_ssprk3(long n, double *y, double dt, orc_rhs_fn rhs, void *ctx)
     double *y1 = malloc(sizeof(double) * n), *y2 = malloc(sizeof(double) * n);
     double *k = malloc(sizeof(double) * n);
     rhs(ctx, y, k);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) y1[i] = y[i] + dt * k[i];
     rhs(ctx, y1, k);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) y2[i] = 0.75 * y[i] + 0.25 * (y1[i] + dt * k[i]);
     rhs(ctx, y2, k);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) y[i] = y[i] / 3.0 + 2.0 / 3.0 * (y2[i] + dt * k[i]);
     free(y1); free(y2); free(k);
 }
@@ -481,6 +504,7 @@ long orc_run(const orc_problem *P, double *f, long nsteps, double *resid, double
             orc_ssprk3(n, f, P->dt, problem_rhs, (void *)P);
         }
         double r = 0;
+#pragma omp parallel for reduction(max : r) schedule(static)
         for (long i = 0; i < n; ++i) {
             int v = (int)((i / P->Nx) % nvel(P));
             double d = w_of(P, v) * fabs(f[i] - prev[i]);

@@ -20,6 +20,7 @@ from . import quadrature
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liblbc_oracle.so")
+LIB_OMP = os.path.join(HERE, "liblbc_oracle_omp.so")
 SRC = os.path.join(HERE, "lbc_oracle.c")
 
 DEFAULTS = dict(
@@ -31,13 +32,20 @@ WENO_EPS = 1e-6
 MOMENT_NAMES = ("n", "u_x", "u_y", "T", "P_xx", "P_yy", "P_zz", "P_xy", "q_x", "q_y")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no machine-specific flags)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", SRC, "-lm", "-o", tmp])
-        os.replace(tmp, LIB)
-    return LIB
+def build(force: bool = False, parallel: bool = False) -> str:
+    """Compile the oracle with gcc (-O3, no machine-specific flags, no fast-math).
+    parallel: the same source with OpenMP (independent rows and nodes of the
+    right-hand side over threads; used only to time the oracle on every host core).
+    Both are built by the default call; parallel=True returns the OpenMP one."""
+    out = LIB_OMP if parallel else LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        extra = ["-fopenmp"] if parallel else []
+        subprocess.check_call(["gcc", "-O3", "-std=gnu11", *extra, "-shared", "-fPIC", SRC, "-lm", "-o", tmp])
+        os.replace(tmp, out)
+    if not parallel:
+        build(force, parallel=True)
+    return out
 
 
 class _Problem(C.Structure):
@@ -55,14 +63,14 @@ class _Problem(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 RHS_FN = C.CFUNCTYPE(None, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double))
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def lib(parallel: bool = False):
+    """The oracle library; parallel=True: its OpenMP build (threads from OMP_NUM_THREADS)."""
+    if parallel not in _libs:
+        L = C.CDLL(build(parallel=parallel))
         dp = C.POINTER(C.c_double)
         L.orc_run.restype = C.c_long
         L.orc_run.argtypes = [C.c_void_p, dp, C.c_long, dp, C.c_double]
@@ -85,8 +93,8 @@ def lib():
         L.orc_ssprk3_nodal.argtypes = [C.c_long, C.c_int, dp, dp, RHS_FN, C.c_void_p]
         L.orc_total_mass.restype = C.c_double
         L.orc_total_mass.argtypes = [C.c_void_p, dp]
-        _lib = L
-    return _lib
+        _libs[parallel] = L
+    return _libs[parallel]
 
 
 def _ptr(a: np.ndarray):
@@ -144,9 +152,11 @@ def local_time_steps(p: dict, J: np.ndarray, deta: float, zmax: float, mu_ratio=
 
 
 class Oracle:
-    """One Couette problem on the CPU, in FP64."""
+    """One Couette problem on the CPU, in FP64. parallel=True steps it with the
+    OpenMP build of the same source (for timing on all host cores)."""
 
-    def __init__(self, params: dict):
+    def __init__(self, params: dict, parallel: bool = False):
+        self._parallel = bool(parallel)
         p = dict(DEFAULTS)
         p.update(params)
         self.p = p
@@ -220,7 +230,7 @@ class Oracle:
     def run(self, nsteps: int, stop_below: float = 0.0) -> np.ndarray:
         """Advance up to nsteps RK-3 steps; returns the per-step residuals."""
         res = np.zeros(max(nsteps, 1))
-        k = lib().orc_run(C.byref(self._pr), _ptr(self.f), nsteps, _ptr(res), stop_below)
+        k = lib(self._parallel).orc_run(C.byref(self._pr), _ptr(self.f), nsteps, _ptr(res), stop_below)
         self.steps += k
         return res[:k]
 

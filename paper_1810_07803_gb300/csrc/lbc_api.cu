@@ -60,6 +60,7 @@ struct lbc_batch {
     int *h_bad = nullptr;         // pinned
     bool steady_mode = false;     // the device control blocks hold run-to-steady settings
     bool poisoned = false;        // some instance holds a NaN/Inf
+    bool timed_out = false;       // a bounded device wait gave up: stepping is refused until set_state
     cudaGraphExec_t graph = nullptr;
     bool ext = false;             // some instance uses the half channel or local steps
     size_t io_elems = 0;          // doubles of the largest instance's host-layout state
@@ -121,9 +122,12 @@ lbc_status ensure_graph(lbc_batch *b)
 
 lbc_status run_steps(lbc_batch *b, long nsteps)
 {
+    if (b->timed_out) return fail(LBC_ETIMEOUT, "a bounded device wait gave up earlier; set a state to continue");
+    if (fault_injected("launch")) return fail(LBC_ECUDA, "stage launch: injected failure (LBC_FAULT=launch)");
     while (nsteps >= kGraphSteps) {
         lbc_status st = ensure_graph(b);
         if (st != LBC_OK) return st;
+        NvtxRange nvtx_range("graph launch (64 steps)");
         LBC_CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
         nsteps -= kGraphSteps;
     }
@@ -133,6 +137,8 @@ lbc_status run_steps(lbc_batch *b, long nsteps)
 
 lbc_status upload_ctl(lbc_batch *b, int first, int count)
 {
+    const int probe = fault_wait_polls();
+    for (int k = first; k < first + count; ++k) b->h_ctl[k].probe = probe;
     LBC_CUDA_TRY(cudaMemcpyAsync(b->d_ctl + first, b->h_ctl + first, count * sizeof(Ctl), cudaMemcpyHostToDevice,
                                  b->stream));
     return LBC_OK;
@@ -145,7 +151,10 @@ lbc_status read_ctl(lbc_batch *b)
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     bool any = false;
     for (int i = 0; i < b->n; ++i) {
-        if (b->h_ctl[i].timeout) return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
+        if (b->h_ctl[i].timeout) {
+            b->timed_out = true;
+            return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
+        }
         any = any || b->h_ctl[i].nonfinite;
     }
     if (any) {
@@ -255,7 +264,8 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     b->nwork = ntile_total;
     const size_t inst_off = tbytes, work_off = inst_off + r256(n * sizeof(Inst));
     tbytes = work_off + r256(b->nwork * sizeof(int2));
-    cudaError_t e = cudaMallocAsync(&b->table_block, tbytes, b->stream);
+    cudaError_t e = fault_injected("alloc") ? cudaErrorMemoryAllocation
+                                            : cudaMallocAsync(&b->table_block, tbytes, b->stream);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMallocAsync(tables): ") + cudaGetErrorString(e));
         return cleanup(e == cudaErrorMemoryAllocation ? LBC_ENOMEM : LBC_ECUDA);
@@ -434,7 +444,10 @@ lbc_status batch_get_state(lbc_batch *b, int i, double *state)
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     for (int k = 0; k < b->n; ++k)
-        if (b->h_ctl[k].timeout) return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
+        if (b->h_ctl[k].timeout) {
+            b->timed_out = true;
+            return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
+        }
     return LBC_OK;
 }
 
@@ -460,8 +473,12 @@ lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
     if (*b->h_bad) return fail(LBC_EINVAL, "state holds a NaN or Inf");
     // control blocks: keep the others' flags, clear this instance's
     b->h_ctl[i].nonfinite = 0;
-    bool any = false;
-    for (int k = 0; k < b->n; ++k) any = any || b->h_ctl[k].nonfinite;
+    b->h_ctl[i].timeout = 0;
+    bool any = false, late = false;
+    for (int k = 0; k < b->n; ++k) {
+        any = any || b->h_ctl[k].nonfinite;
+        late = late || b->h_ctl[k].timeout;
+    }
     const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
     LBC_CUDA_TRY(cudaMemcpyAsync(I.S.F[0], I.S.F[1], 2 * (size_t)I.T.V * I.T.Nxp * esz, cudaMemcpyDeviceToDevice,
                                  b->stream));
@@ -473,6 +490,7 @@ lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
     if (st != LBC_OK) return st;
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     b->poisoned = any;
+    b->timed_out = late;
     return LBC_OK;
 }
 
@@ -545,13 +563,14 @@ lbc_status upload_states(lbc_batch *b, const double *const *states)
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     if (*b->h_bad) return fail(LBC_EINVAL, "a state holds a NaN or Inf; no instance changed");
-    bool any = false;
+    bool any = false, late = false;
     const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
     for (int i = 0; i < b->n; ++i) {
         if (states[i]) {
             const Inst &I = b->inst[i];
             const size_t bytes = 2 * (size_t)I.T.V * I.T.Nxp * esz;
             b->h_ctl[i].nonfinite = 0;
+            b->h_ctl[i].timeout = 0;
             LBC_CUDA_TRY(cudaMemcpyAsync(I.S.F[0], I.S.F[1], bytes, cudaMemcpyDeviceToDevice, b->stream));
             if (I.S.C) LBC_CUDA_TRY(cudaMemcpyAsync(I.S.C, I.S.F[2], bytes, cudaMemcpyDeviceToDevice, b->stream));
             if (I.T.lts) {
@@ -564,11 +583,13 @@ lbc_status upload_states(lbc_batch *b, const double *const *states)
             }
         }
         any = any || b->h_ctl[i].nonfinite;
+        late = late || b->h_ctl[i].timeout;
     }
     st = upload_ctl(b, 0, b->n);
     if (st != LBC_OK) return st;
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     b->poisoned = any;
+    b->timed_out = late;
     return LBC_OK;
 }
 
@@ -671,11 +692,13 @@ extern "C" {
 
 lbc_status lbc_batch_create(const lbc_params *params, int n, int cluster, void *cuda_stream, lbc_batch **out)
 {
+    NvtxRange nvtx_range("lbc_batch_create");
     return batch_create(params, n, cluster, cuda_stream, out);
 }
 
 lbc_status lbc_batch_step(lbc_batch *b, long nsteps)
 {
+    NvtxRange nvtx_range("lbc_batch_step");
     if (!b || nsteps < 0) return fail(LBC_EINVAL, "bad batch or nsteps");
     if (b->poisoned) return fail(LBC_ENONFINITE, "a state is non-finite");
     lbc_status st = plain_mode(b);
@@ -688,13 +711,18 @@ lbc_status lbc_batch_step(lbc_batch *b, long nsteps)
 lbc_status lbc_batch_run_to_steady(lbc_batch *b, double residual, long max_steps, long *steps_done,
                                    double *final_residual)
 {
+    NvtxRange nvtx_range("lbc_batch_run_to_steady");
     return batch_run_to_steady(b, residual, max_steps, steps_done, final_residual);
 }
 
 lbc_status lbc_batch_moments(lbc_batch *b, int i, double *out, double *x) { return batch_moments(b, i, out, x); }
 lbc_status lbc_batch_get_state(lbc_batch *b, int i, double *state) { return batch_get_state(b, i, state); }
 lbc_status lbc_batch_set_state(lbc_batch *b, int i, const double *state) { return batch_set_state(b, i, state); }
-lbc_status lbc_batch_set_states(lbc_batch *b, const double *const *states) { return batch_set_states(b, states); }
+lbc_status lbc_batch_set_states(lbc_batch *b, const double *const *states)
+{
+    NvtxRange nvtx_range("lbc_batch_set_states");
+    return batch_set_states(b, states);
+}
 lbc_status lbc_batch_moments_all(lbc_batch *b, double *out) { return batch_moments_all(b, out); }
 
 lbc_status lbc_batch_info(const lbc_batch *b, int i, int *Nx, int *V, double *dt, long *steps_taken)
@@ -722,6 +750,7 @@ lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster) { ret
 
 lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms)
 {
+    NvtxRange nvtx_range("lbc_batch_step_timed");
     if (!b || nsteps < 0 || !stage_ms) return fail(LBC_EINVAL, "bad batch, nsteps or stage_ms");
     if (b->poisoned) return fail(LBC_ENONFINITE, "a state is non-finite");
     lbc_status st = plain_mode(b);
@@ -781,6 +810,7 @@ void lbc_batch_destroy(lbc_batch *b)
 
 lbc_status lbc_create(const lbc_params *params, void *cuda_stream, lbc_solver **out)
 {
+    NvtxRange nvtx_range("lbc_create");
     if (!params || !out) return fail(LBC_EINVAL, "params and out must not be NULL");
     lbc_solver *s = new (std::nothrow) lbc_solver();
     if (!s) return fail(LBC_ENOMEM, "host allocation failed");
@@ -795,6 +825,7 @@ lbc_status lbc_create(const lbc_params *params, void *cuda_stream, lbc_solver **
 
 lbc_status lbc_step(lbc_solver *s, long nsteps)
 {
+    NvtxRange nvtx_range("lbc_step");
     if (!s) return fail(LBC_EINVAL, "bad solver or nsteps");
     return lbc_batch_step(s->b, nsteps);
 }
@@ -802,6 +833,7 @@ lbc_status lbc_step(lbc_solver *s, long nsteps)
 lbc_status lbc_run_to_steady(lbc_solver *s, double residual, long max_steps, long *steps_done,
                              double *final_residual)
 {
+    NvtxRange nvtx_range("lbc_run_to_steady");
     if (!s) return fail(LBC_EINVAL, "bad solver, residual or max_steps");
     return batch_run_to_steady(s->b, residual, max_steps, steps_done, final_residual);
 }
@@ -820,6 +852,7 @@ lbc_status lbc_get_state(lbc_solver *s, double *state)
 
 lbc_status lbc_set_state(lbc_solver *s, const double *state)
 {
+    NvtxRange nvtx_range("lbc_set_state");
     if (!s) return fail(LBC_EINVAL, "NULL argument");
     return batch_set_state(s->b, 0, state);
 }

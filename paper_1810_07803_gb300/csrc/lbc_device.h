@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
@@ -122,7 +123,9 @@ struct Ctl {
     int stopped;           // set once a residual fell below stop_eps
     int nonfinite;         // set if a NaN/Inf was produced
     int timeout;           // set if a bounded wait on an mbarrier gave up
-    int pad;
+    int probe;             // test hook (LBC_FAULT=wait:N): > 0 makes every stage CTA wait at most this
+                           // many polls on an mbarrier that nothing arrives at, so the bounded-wait
+                           // path runs and reports; 0 in normal use
 };
 
 // Mutable device state; arrays marked (R) hold the state precision.
@@ -186,6 +189,13 @@ lbc_status choose_batch_shape(bool fp32, std::vector<DevTables> &Ts, int cluster
 size_t stage_launch_smem(bool fp32, const DevTables &T);
 // Errors and parameter checks shared by every entry point.
 lbc_status fail(lbc_status st, const std::string &msg);
+// Host-side fault injection for tests, from the LBC_FAULT environment variable (read at each
+// use, so a test can set and clear it): "alloc" (device allocations of create and pool
+// admission report failure without allocating), "launch" (stepping calls report a failed
+// stage launch without launching), "admit" (pool admission reports no room), "wait:N" (the
+// control blocks uploaded carry probe = N, see Ctl). Nothing here touches the device.
+bool fault_injected(const char *kind);
+int fault_wait_polls();
 const char *last_error();
 // Validates p (defaults already applied) and resolves the expansion orders.
 lbc_status validate(const lbc_params &p, int &Nxe, int &Nye);
@@ -232,6 +242,14 @@ cudaError_t launch_ctl_bump(Ctl *ctl, int n, long long k, cudaStream_t st);
 // last[k] = residual of instance slots[k]'s (k's if slots is NULL) last step taken (its stop
 // step - 1 if stopped, else base - 1), k < n
 cudaError_t launch_last_residuals(const Inst *insts, const int *slots, int n, double *last, cudaStream_t st);
+
+// NVTX range over a scope (header-only NVTX v3: a no-op unless a profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 inline size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 // Device bytes of one instance's state (partials sized for the largest cluster, so

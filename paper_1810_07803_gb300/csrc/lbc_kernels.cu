@@ -318,10 +318,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long limit = kSpinLimit)
 {
     const uint32_t a = smem_addr(bar);
-    for (long i = 0; i < kSpinLimit; ++i) {
+    for (long i = 0; i < limit; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -689,7 +689,7 @@ struct Layout {
     __host__ __device__ Layout(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster, int ntab)
     {
         size_t o = 0;
-        bar = o;  o = al(o + (kPipe + 2) * sizeof(uint64_t) + (kPipe + 1) * sizeof(uint32_t));
+        bar = o;  o = al(o + (kPipe + 2) * sizeof(uint64_t) + (2 * kPipe + 1) * sizeof(uint32_t));
         pipe = o;
         fin = o;
         f0 = fin + (size_t)kPipe * 2 * kSubV * kRowLen * sizeof(R);
@@ -727,6 +727,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     uint64_t *bar_data = bar + kPipe, *bar_tab = bar + kPipe + 1;
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(bar + kPipe + 2);   // [kPipe] warps done with a slot
     int *s_abort = reinterpret_cast<int *>(s_cnt + kPipe);              // a warp gave up waiting
+    uint32_t *s_fill = s_cnt + kPipe + 1;                               // [kPipe] copies issued per slot
     R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][kSubV][2 kRowLen]: (phi, chi) per node
     R *s_f0 = reinterpret_cast<R *>(smem + L.f0);         // [kPipe][kSubV][2 kF0Len]
     R *s_g = reinterpret_cast<R *>(smem + L.g);           // [2Qx + Qy][kLanes]
@@ -779,6 +780,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     // RK base (nodes xf ..), both fields; rows past V read as zeros
     auto issue = [&](int sub) {
         int p = sub % kPipe, v0 = vbeg + sub * kSubV;
+        s_fill[p] += 1;   // one issuer per slot at a time: a slot is refilled only once every warp released it
         mbar_expect_tx(&bar[p], tx_bytes);
         tma_load_2d(s_fin + (size_t)p * kSubV * 2 * kRowLen, in_map, 2 * x0, v0, &bar[p]);
         if (stage > 0) tma_load_2d(s_f0 + (size_t)p * kSubV * 2 * kF0Len, &M.f0, 2 * xf, v0, &bar[p]);
@@ -786,7 +788,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
 
     if (tid == 0) {
         for (int p = 0; p < kPipe + 2; ++p) mbar_init(&bar[p], 1);
-        for (int p = 0; p < kPipe; ++p) s_cnt[p] = 0;
+        for (int p = 0; p < kPipe; ++p) s_cnt[p] = s_fill[p] = 0;
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -823,6 +825,9 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
         lam1 = (S.mass[0] - dM) / (T.mrest + dM);
     }
     bool timed_out = __syncthreads_or(!mbar_wait(bar_data, 0));
+    // test hook: wait on the table barrier, which nothing has armed yet, so the wait gives up
+    const int probe = ctl->probe;
+    if (probe > 0) timed_out = __syncthreads_or(!mbar_wait(bar_tab, 0, probe)) || timed_out;
 
     const int s = c0 + lane;
     const bool active = lane < nloc;
@@ -1172,10 +1177,10 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
         // still takes part in the cluster barriers below, without touching data
         if (tid == 0) {
             atomicExch(&ctl->timeout, 1);
-            for (int p = 0; p < kPipe; ++p) {
-                mbar_wait(&bar[p], 0);
-                mbar_wait(&bar[p], 1);
-            }
+            // a slot has at most one copy outstanding (it is refilled only after every warp
+            // waited for its previous copy): wait for the last one issued to each slot
+            for (int p = 0; p < kPipe; ++p)
+                if (s_fill[p] > 0) mbar_wait(&bar[p], (s_fill[p] - 1) & 1);
             mbar_wait(bar_data, 0);
         }
         __syncthreads();

@@ -222,7 +222,7 @@ lbc_status lbc_pool_add(lbc_pool *P, const lbc_params *params, int *slot_out)
     const size_t tbytes = round256(ps.blob.size());
     const size_t io = 2 * (size_t)I.T.V * I.T.Nx;
     const size_t need = tbytes + z.total;
-    if (P->used + need > P->budget) return fail(LBC_ENOMEM, "pool budget exhausted");
+    if (P->used + need > P->budget || fault_injected("admit")) return fail(LBC_ENOMEM, "pool budget exhausted");
     if ((long)P->nwork + I.T.ntile > P->max_tiles) return fail(LBC_ENOMEM, "pool work list full");
     if (io > P->io_cap) {   // the state staging (outside the budget) grows to the largest instance seen
         if (P->d_io) POOL_TRY(cudaFreeAsync(P->d_io, P->stream));
@@ -231,7 +231,8 @@ lbc_status lbc_pool_add(lbc_pool *P, const lbc_params *params, int *slot_out)
         P->io_cap = io;
     }
     void *block = nullptr;
-    cudaError_t e = cudaMallocAsync(&block, tbytes + z.total, P->stream);
+    cudaError_t e = fault_injected("alloc") ? cudaErrorMemoryAllocation
+                                            : cudaMallocAsync(&block, tbytes + z.total, P->stream);
     if (e != cudaSuccess) return fail(LBC_ENOMEM, std::string("instance allocation: ") + cudaGetErrorString(e));
     bind_tables(ps, p, block, I.T);
     I.T.nchunk = P->cluster;
@@ -297,10 +298,13 @@ lbc_status lbc_pool_remove(lbc_pool *P, int s)
 
 lbc_status lbc_pool_run(lbc_pool *P, double residual, long nsteps, int *finished, int *nfinished)
 {
+    NvtxRange nvtx_range("lbc_pool_run");
     if (!P || !(residual > 0.0) || nsteps < 0) return fail(LBC_EINVAL, "bad pool, residual or nsteps");
     if (nfinished) *nfinished = 0;
     const int na = (int)P->active.size();
     if (na == 0 || nsteps == 0) return LBC_OK;
+    if (fault_injected("launch")) return fail(LBC_ECUDA, "stage launch: injected failure (LBC_FAULT=launch)");
+    const int probe = fault_wait_polls();
     size_t smem = 0;
     for (int s : P->active) {
         Ctl &c = P->h_ctl[s];
@@ -311,6 +315,7 @@ lbc_status lbc_pool_run(lbc_pool *P, double residual, long nsteps, int *finished
         c.stop_eps = residual;
         c.stop_step = 0;
         c.stopped = 0;
+        c.probe = probe;
         smem = std::max(smem, P->slot[s].smem);
     }
     POOL_TRY(cudaMemcpyAsync(P->d_ctl, P->h_ctl, P->cap * sizeof(Ctl), cudaMemcpyHostToDevice, P->stream));

@@ -3,6 +3,7 @@
 // time step), the device table image, TMA descriptors and launch shapes.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <string>
@@ -23,6 +24,20 @@ lbc_status fail(lbc_status st, const std::string &msg)
 {
     set_error(msg);
     return st;
+}
+
+bool fault_injected(const char *kind)
+{
+    const char *f = std::getenv("LBC_FAULT");
+    return f && std::strcmp(f, kind) == 0;
+}
+
+int fault_wait_polls()
+{
+    const char *f = std::getenv("LBC_FAULT");
+    if (!f || std::strncmp(f, "wait:", 5) != 0) return 0;
+    const long n = std::strtol(f + 5, nullptr, 10);
+    return n > 0 && n < (1L << 30) ? (int)n : 0;
 }
 
 lbc_status validate(const lbc_params &p, int &Nxe, int &Nye)

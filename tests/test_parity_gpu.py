@@ -164,28 +164,53 @@ def test_set_state_roundtrip_and_nonfinite_rejected():
     s.close()
 
 
+def perturbed(o, seed, amplitude=0.1):
+    """A seeded non-equilibrium state of problem o: every velocity row of the rest
+    state modulated by its own low Fourier modes in x, so that from the first step
+    every node has non-trivial n, u, T, q, the nonlinear WENO weights and the wall
+    fluxes are in play, and the moment sums cancel across velocities."""
+    return workloads.perturbed_state(o.V, o.Nx, o.f, seed=seed, amplitude=amplitude)
+
+
 @pytest.mark.parametrize("delta", workloads.C2_DELTAS)
-def test_full_size_c2_sampled(delta):
-    """Config 2 at full size (Nx = 2048, 32 x 20 velocities), FP32 state, in the
-    launch configuration the benchmark times: 2 steps against the oracle."""
+def test_full_size_c2_perturbed(delta):
+    """Config 2 at full size (Nx = 2048, 32 x 20 velocities), FP32 state, from a seeded
+    perturbed state: 3 steps against the oracle (1e-5)."""
     p = workloads.c2(delta)
-    s, o = run_pair(p, 2, precision="fp32")
+    o = Oracle(p)
+    s, o = run_pair(p, 3, precision="fp32", state=perturbed(o, seed=20 + int(10 * delta)))
     e = moment_errors(s.moments(), o.moments())
     assert np.all(e < 1e-5), dict(zip(lbc.MOMENT_NAMES, e))
     s.close()
 
 
+def test_full_size_c2_fp64_perturbed():
+    """Config 2 at full size in FP64 from a perturbed state: 3 steps, 1e-12."""
+    p = workloads.c2(1.0, precision="fp64")
+    o = Oracle(p)
+    s, o = run_pair(p, 3, precision="fp64", state=perturbed(o, seed=31))
+    e = moment_errors(s.moments(), o.moments())
+    assert np.all(e < 1e-12), dict(zip(lbc.MOMENT_NAMES, e))
+    assert weighted_state_error(s.get_state(), o.f, o.w) < 1e-12
+    s.close()
+
+
 def test_benchmark_launch_configuration_matches_oracle():
     """The benchmark's exact configuration: the four delta solves of the single-large-solve
-    workload as one FP32 batch with the autotuned cluster size, 2 steps, each solve against
-    the oracle (1e-5), and the stage launch timed the way the benchmark times it."""
+    workload as one FP32 batch with the autotuned cluster size, stepped the way the
+    benchmark steps them, from seeded perturbed states installed in one call; 3 steps,
+    each solve against the oracle (1e-5)."""
     ps = [workloads.c2(d, precision="fp32") for d in workloads.C2_DELTAS]
     b = lbc.Batch(ps)
     b.autotune(2)
-    b.step_timed(2)
-    for i, p in enumerate(ps):
-        o = Oracle(p)
-        o.run(2)
+    orcs = [Oracle(p) for p in ps]
+    states = [perturbed(o, seed=40 + i) for i, o in enumerate(orcs)]
+    b.set_states(states)
+    b.step(2)
+    b.step_timed(1)
+    for i, (p, o) in enumerate(zip(ps, orcs)):
+        o.set_state(states[i])
+        o.run(3)
         e = moment_errors(b.moments(i), o.moments())
         assert np.all(e < 1e-5), (p["delta"], dict(zip(lbc.MOMENT_NAMES, e)))
     b.close()

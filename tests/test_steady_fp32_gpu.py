@@ -1,0 +1,97 @@
+"""FP32 steady states against the FP64 oracle's steady state.
+
+The stated tolerance for reduced-precision runs is 1e-5 on every moment
+(normalised as in helpers.moment_errors). A steady state is the fixed point of
+the step, so each run is compared with the limit, not with another run that
+stopped at the same residual: the oracle runs to r < 1e-12, a GPU FP64 run to
+r < 1e-13, and the FP32 runs to r < 1e-10 or, where the FP32 evaluation of the
+right-hand side keeps the residual above that, for a fixed number of steps past
+the point where the state stops changing.
+
+The compensated FP32 state (each value carries its rounding remainder) is the
+form whose steady state meets the tolerance; the plain FP32 state stalls once
+the step's increments fall below half an ulp of the values, at a steady state
+biased by about eps_32 |f| tau / dt, and its error is measured and bounded here
+so that a regression shows.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_1810_07803_gb300 import build, lbc, workloads
+from tests.helpers import gpu_available, moment_errors
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "c1": workloads.c1(),
+    # stretched grid, unequal wall temperatures and speeds, local pseudo-time steps
+    "stretched_nonisothermal": dict(Nx=48, Qx=6, Qy=6, stretch_A=0.9, delta=2.0, u_left=-0.2, u_right=0.15,
+                                    T_left=0.7, T_right=1.4, omega=0.7, Pr=0.68, local_dt=1),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not gpu_available():
+        pytest.skip("no GPU")
+    build.build()
+
+
+_refs = {}
+
+
+def oracle_steady(name):
+    if name not in _refs:
+        o = Oracle(CASES[name])
+        k, r = o.run_to_steady(1e-12, 400000)
+        assert r < 1e-12
+        _refs[name] = (k, o.moments())
+    return _refs[name]
+
+
+def run_fp32(params, compensated, k_ref):
+    """FP32 run to r < 1e-10, or 3 k_ref steps if the residual stays above it."""
+    s = lbc.Solver(dict(params, precision="fp32", compensated=int(compensated)))
+    try:
+        s.run_to_steady(1e-10, 3 * k_ref)
+    except lbc.LbcError as e:
+        assert e.status == lbc.ENOTCONV
+    return s
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_steady_state_matches_oracle(name):
+    k, ref = oracle_steady(name)
+    s = lbc.Solver(dict(CASES[name], precision="fp64"))
+    s.run_to_steady(1e-13, 4 * k)
+    e = moment_errors(s.moments(), ref)
+    # the oracle stops at r < 1e-12: its distance from the limit is ~1e-12 / (1 - contraction)
+    assert np.all(e < 1e-9), dict(zip(lbc.MOMENT_NAMES, e))
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp32_compensated_steady_state_matches_oracle(name):
+    k, ref = oracle_steady(name)
+    s = run_fp32(CASES[name], True, k)
+    m = s.moments()
+    e = moment_errors(m, ref)
+    assert np.all(e < 1e-5), dict(zip(lbc.MOMENT_NAMES, e))
+    s64 = lbc.Solver(dict(CASES[name], precision="fp64"))
+    s64.run_to_steady(1e-13, 4 * k)
+    e64 = moment_errors(m, s64.moments())
+    assert np.all(e64 < 1e-5), dict(zip(lbc.MOMENT_NAMES, e64))
+    s.close()
+    s64.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp32_plain_steady_state_error_bounded(name):
+    """The plain FP32 state's stalled steady state: within 1e-3 of the limit (a bound
+    on the measured bias, not the reduced-precision tolerance)."""
+    k, ref = oracle_steady(name)
+    s = run_fp32(CASES[name], False, k)
+    e = moment_errors(s.moments(), ref)
+    assert np.all(e < 1e-3), dict(zip(lbc.MOMENT_NAMES, e))
+    s.close()

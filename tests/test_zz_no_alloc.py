@@ -61,3 +61,22 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
         lbc.step_noalloc(p, state.data_ptr(), 1)
     assert e.value.status == lbc.EINVAL
     assert "allocation-free path has" in str(e.value)
+
+
+def test_noalloc_call_allocates_no_device_memory():
+    """After a first call (which resolves the static array's address and sets kernel
+    attributes), a call leaves the device's free memory as it was: it allocates nothing."""
+    import torch
+    p = dict(PROBLEM, precision="fp32")
+    with lbc.Solver(p) as s:
+        f0 = s.get_state()
+    state = torch.tensor(f0, dtype=torch.float64, device="cuda")
+    lbc.step_noalloc(p, state.data_ptr(), 3)     # warm-up: first call on this device
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free0, _ = torch.cuda.mem_get_info()
+    lbc.step_noalloc(p, state.data_ptr(), 3)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    # a released pool block could only raise the free figure; an allocation would lower it
+    assert free1 >= free0, (free0, free1)
