@@ -260,6 +260,20 @@ lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster);
  * events on the batch's stream; *stage_ms receives the sum of the 3 nsteps
  * stage-kernel durations (for roofline reports). Synchronises the stream. */
 lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms);
+/*
+ * Persistent form (on != 0; no counterpart in the paper): each group of steps of the
+ * whole batch runs as ONE cooperative launch whose thread-block clusters (as many as
+ * can be resident, at most one per work item) take (step, stage, tile) items in order
+ * from a device counter. An item starts when its tile and the two neighbouring tiles
+ * (the WENO-5 stencil's halo) finished the previous stage; an instance with early stop
+ * (lbc_batch_run_to_steady) or local steps also waits, at the first stage of a step,
+ * for its whole previous step. Every wait is bounded (2 s): on timeout the launch
+ * aborts and the instance reports LBC_ETIMEOUT. Results are bit-identical to the
+ * per-stage launches. on = 0 returns to one launch per RK stage. Not available with
+ * lbc_batch_step_timed (LBC_EINVAL). Errors: LBC_EINVAL (the launch shape does not fit
+ * the device), LBC_ECUDA.
+ */
+lbc_status lbc_batch_set_persistent(lbc_batch *b, int on);
 void lbc_batch_destroy(lbc_batch *b);
 
 /*
@@ -336,6 +350,14 @@ void lbc_pool_destroy(lbc_pool *pool);
  * Errors: LBC_EINVAL, LBC_ECUDA, LBC_ENONFINITE, LBC_ETIMEOUT.
  */
 lbc_status lbc_step_noalloc(const lbc_params *params, double *d_state, long nsteps, void *cuda_stream);
+
+/*
+ * Measurement helper (no counterpart in the paper): the device's FP64 FMA rate in
+ * TFLOP/s, measured by timing independent FMA chains on every SM with CUDA events
+ * (best of three launches after a warm-up), for the roofline of the FP64 path.
+ * Uses the current device; changes no device setting. Errors: LBC_EINVAL, LBC_ECUDA.
+ */
+lbc_status lbc_measure_fp64_peak(double *tflops);
 
 #ifdef __cplusplus
 }

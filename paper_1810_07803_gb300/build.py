@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbc.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lbc_api.cu", "lbc_setup.cu", "lbc_pool.cu", "lbc_kernels.cu", "lbc_host.cpp", "lbc_noalloc.cu"]
+SOURCES = ["lbc_api.cu", "lbc_setup.cu", "lbc_pool.cu", "lbc_kernels.cu", "lbc_host.cpp", "lbc_noalloc.cu",
+           "lbc_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -63,6 +63,9 @@ struct lbc_batch {
     bool timed_out = false;       // a bounded device wait gave up: stepping is refused until set_state
     cudaGraphExec_t graph = nullptr;
     bool ext = false;             // some instance uses the half channel or local steps
+    bool persistent = false;      // steps run as the persistent form (one launch per group of steps)
+    int pclusters = 0;            // clusters of a persistent launch (all resident)
+    unsigned *d_cnt = nullptr;    // persistent form's counters: kPersistHdr + nwork + n
     size_t io_elems = 0;          // doubles of the largest instance's host-layout state
     // lbc_batch_set_states: a second staging buffer and a copy stream, so that the upload of
     // one instance overlaps the conversion and stage data of the previous one (made at first use)
@@ -93,7 +96,14 @@ cudaError_t launch_steps_t(lbc_batch *b, int nsteps, cudaStream_t st)
 // nsteps RK-3 steps of every instance, then the step counters.
 cudaError_t launch_steps(lbc_batch *b, int nsteps, cudaStream_t st)
 {
-    cudaError_t e = b->fp32 ? launch_steps_t<float>(b, nsteps, st) : launch_steps_t<double>(b, nsteps, st);
+    cudaError_t e;
+    if (b->persistent)
+        e = b->fp32 ? launch_persistent<float>(b->d_inst, b->d_work, b->nwork, b->n, b->cluster, b->pclusters, b->smem,
+                                               nsteps, b->ext, b->d_cnt, st)
+                    : launch_persistent<double>(b->d_inst, b->d_work, b->nwork, b->n, b->cluster, b->pclusters,
+                                                b->smem, nsteps, b->ext, b->d_cnt, st);
+    else
+        e = b->fp32 ? launch_steps_t<float>(b, nsteps, st) : launch_steps_t<double>(b, nsteps, st);
     if (e == cudaSuccess) e = launch_ctl_bump(b->d_ctl, b->n, nsteps, st);
     return e;
 }
@@ -310,7 +320,8 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     for (int i = 0; i < n; ++i) io_elems = std::max(io_elems, 2 * (size_t)b->inst[i].T.V * b->inst[i].T.Nx);
     const size_t ctl_off = sbytes, last_off = ctl_off + r256(n * sizeof(Ctl));
     const size_t io_off = last_off + r256(n * sizeof(double)), bad_off = io_off + r256(io_elems * sizeof(double));
-    sbytes = bad_off + 256;
+    const size_t cnt_off = bad_off + 256;
+    sbytes = cnt_off + r256((kPersistHdr + (size_t)b->nwork + n) * sizeof(unsigned));
     b->io_elems = io_elems;
     e = cudaMallocAsync(&b->state_block, sbytes, b->stream);
     if (e != cudaSuccess) {
@@ -324,6 +335,7 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     b->d_last = reinterpret_cast<double *>(sb + last_off);
     b->d_io = reinterpret_cast<double *>(sb + io_off);
     b->d_bad = reinterpret_cast<int *>(sb + bad_off);
+    b->d_cnt = reinterpret_cast<unsigned *>(sb + cnt_off);
     for (int i = 0; i < n; ++i) {
         DevTables &T = b->inst[i].T;
         DevState &S = b->inst[i].S;
@@ -611,6 +623,18 @@ lbc_status batch_moments_all(lbc_batch *b, double *out)
 
 // Times trial_steps steps per feasible cluster size (after one warm-up step) and
 // keeps the fastest; every instance starts and ends at the rest state.
+// Clusters of the persistent form at the batch's launch shape (resident at once, at most one per work item).
+lbc_status persistent_shape(lbc_batch *b)
+{
+    int nc = 0;
+    cudaError_t e = b->fp32 ? persistent_active_clusters<float>(b->smem, b->cluster, &nc)
+                            : persistent_active_clusters<double>(b->smem, b->cluster, &nc);
+    if (e != cudaSuccess) return fail(LBC_ECUDA, std::string("persistent occupancy: ") + cudaGetErrorString(e));
+    if (nc < 1) return fail(LBC_EINVAL, "the persistent form does not fit the device at this launch shape");
+    b->pclusters = std::min(nc, b->nwork);
+    return LBC_OK;
+}
+
 lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
 {
     if (!b || trial_steps < 1) return fail(LBC_EINVAL, "bad batch or trial_steps");
@@ -638,6 +662,7 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
         for (int i = 0; i < b->n; ++i) b->inst[i].T = Ts[i];
         b->cluster = c;
         b->smem = smem;
+        if (b->persistent && persistent_shape(b) != LBC_OK) continue;
         st = upload_descriptors(b);
         if (st != LBC_OK) break;
         cudaError_t e = launch_steps(b, 1, b->stream);
@@ -660,6 +685,7 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
         b->cluster = best_c;
         b->smem = best_smem;
     }
+    if (b->persistent && st == LBC_OK) st = persistent_shape(b);
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -748,10 +774,26 @@ lbc_status lbc_batch_shape(const lbc_batch *b, int *cluster, int *nwork, size_t 
 
 lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster) { return batch_autotune(b, trial_steps, cluster); }
 
+lbc_status lbc_batch_set_persistent(lbc_batch *b, int on)
+{
+    if (!b) return fail(LBC_EINVAL, "NULL batch");
+    if (on) {
+        lbc_status st = persistent_shape(b);
+        if (st != LBC_OK) return st;
+    }
+    if (b->persistent != (on != 0) && b->graph) {   // the captured group of steps changes form
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->persistent = on != 0;
+    return LBC_OK;
+}
+
 lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms)
 {
     NvtxRange nvtx_range("lbc_batch_step_timed");
     if (!b || nsteps < 0 || !stage_ms) return fail(LBC_EINVAL, "bad batch, nsteps or stage_ms");
+    if (b->persistent) return fail(LBC_EINVAL, "the persistent form has no separate stage launches to time");
     if (b->poisoned) return fail(LBC_ENONFINITE, "a state is non-finite");
     lbc_status st = plain_mode(b);
     if (st != LBC_OK) return st;

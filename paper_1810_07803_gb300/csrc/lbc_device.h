@@ -26,6 +26,7 @@ constexpr int kMaxVChunk = 256;    // velocities per CTA at most (per-velocity d
 constexpr int kMaxCluster = 16;    // chunk CTAs of a tile form one thread-block cluster (non-portable size 16)
 constexpr int kMaxV = kMaxCluster * kMaxVChunk;   // largest velocity set 2 Qx Qy
 constexpr int kMaxTable = 256;     // entries of a viscosity table
+constexpr int kPersistHdr = 4;     // counters before the per-item ones in the persistent form's block
 
 // Scalars derived from the parameters, in both precisions (no FP64 arithmetic in the FP32 kernels).
 enum { SC_NU = 0,      // delta sqrt(2): 1/tau = SC_NU n T^(1 - omega)   (Eq. tau)
@@ -142,6 +143,8 @@ struct DevState {
     double *mass;          // local steps: [0] reference mass minus the rest mass; from kMassHdr on,
                            // [2][Nxp] J_s deta (n_s - 1) of buffer 0 after steps of parity 0 / 1
     void *C;               // (R) compensated state: [V][Nxp][2] rounding remainder of buffer 0 (else NULL)
+    void *A;               // (R) compensated state: [V][Nxp][2] the step's increment accumulated over its
+                           //     stages, dt (L0 + L1) after the second (else NULL)
 };
 
 // TMA descriptors of the state buffers, viewed as 2-D [V rows][2 Nxp columns].
@@ -222,6 +225,14 @@ cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStr
 template <typename R>
 cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, int cluster, size_t smem, int stage,
                                int rel, bool ext, cudaStream_t st);
+// Persistent form: nsteps RK-3 steps of every work item in one cooperative launch of nclusters
+// clusters (grid (nclusters, cluster)); cnt: kPersistHdr + nwork + n device counters (zeroed here);
+// the steps' residual slots are zeroed first. Work items of an instance must be its tiles in order.
+template <typename R>
+cudaError_t launch_persistent(const Inst *insts, const int2 *work, int nwork, int n, int cluster, int nclusters,
+                              size_t smem, int nsteps, bool ext, unsigned *cnt, cudaStream_t st);
+template <typename R>
+cudaError_t persistent_active_clusters(size_t smem, int cluster, int *nclusters);
 template <typename R>
 cudaError_t launch_moments_partial(const DevTables &T, const DevState &S, int buf, cudaStream_t st);
 // Stage data of buffer `buf` from the chunk partials of launch_moments_partial; for
@@ -255,7 +266,7 @@ inline size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 // Device bytes of one instance's state (partials sized for the largest cluster, so
 // a launch shape can change without reallocating).
 struct StateSizes {
-    size_t f, eqm, eqg, part, resid, mom, mass, carry, total;
+    size_t f, eqm, eqg, part, resid, mom, mass, carry, acc, total;
     StateSizes(const DevTables &T, bool fp32)
     {
         const size_t esz = fp32 ? sizeof(float) : sizeof(double);
@@ -267,7 +278,8 @@ struct StateSizes {
         mom = round256((size_t)LBC_NMOM * T.Nxp * sizeof(double));
         mass = round256((kMassHdr + 2 * (size_t)T.Nxp) * sizeof(double));
         carry = T.comp ? f : 0;
-        total = 3 * (f + eqm + eqg) + part + resid + mom + mass + carry;
+        acc = T.comp ? f : 0;
+        total = 3 * (f + eqm + eqg) + part + resid + mom + mass + carry + acc;
     }
     // Points the state arrays of S into `base` (total bytes); S.ctl is set by the caller.
     void carve(char *base, DevState &S) const
@@ -281,6 +293,8 @@ struct StateSizes {
         S.mom_out = reinterpret_cast<double *>(p); p += mom;
         S.mass = reinterpret_cast<double *>(p); p += mass;
         S.C = carry ? p : nullptr;
+        p += carry;
+        S.A = acc ? p : nullptr;
     }
 };
 

@@ -312,6 +312,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
@@ -457,6 +462,58 @@ __device__ __forceinline__ void raw_to_moments_r(const R *r, R sx, R sy, R *m)
     m[9] = R(0.5) * hy + R(0.5) * (r[R_GY] - by * pzz);
 }
 
+// Hermite coefficients of g_x of one node by the Gauss-sum projection (a whole warp):
+// c^{+-}_l = sum_k r_k^{+-} h_l(sqrt(T') Y_k), r_k^{+-} = W_k exp(+-a Y_k - a^2/2), over the K
+// nodes of the projection rule, for l <= N, into cw[2][N+1]. Lanes run the recurrence of
+// the orthonormal h_l at projection nodes lane + 32 u (u < NU, K <= 32 NU) in blocks of kEqLB
+// orders; lane (sign, l) of a block takes one compensated dot product (Dot2 in FP32).
+// rp [2][K] and Hw [kEqLB][kpad] are this warp's scratch.
+template <typename R, int NU>
+__device__ __forceinline__ void project_coefficients(R sT, R a, R a2, int K, int N, int kpad, const R *Yk,
+                                                     const R *Wk, const R *alpha, const R *sbeta,
+                                                     const R *isbeta, R h0, R *rp, R *cw, R *Hw)
+{
+    const int lane = threadIdx.x & 31;
+    const int sgn = lane / kEqLB, lo = lane - sgn * kEqLB;
+    R zt[NU], h[NU], hp[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int k = lane + 32 * u;
+        zt[u] = R(0);
+        h[u] = h0;
+        hp[u] = R(0);
+        if (k < K) {
+            const R Y = Yk[k], W = Wk[k];
+            rp[k] = W * exp(a * Y - a2);
+            rp[K + k] = W * exp(-a * Y - a2);
+            zt[u] = sT * Y;
+        }
+    }
+    for (int lb = 0; lb <= N; lb += kEqLB) {
+        const int le = min(N, lb + kEqLB - 1);
+        for (int l = lb; l <= le; ++l) {
+            const R al = alpha[l], sb = sbeta[l], isb1 = isbeta[l + 1];
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                const int k = lane + 32 * u;
+                if (k < K) Hw[(l - lb) * kpad + k] = h[u];
+                const R hn = ((zt[u] - al) * h[u] - sb * hp[u]) * isb1;
+                hp[u] = h[u];
+                h[u] = hn;
+            }
+        }
+        __syncwarp();
+        if (lb + lo <= le) {
+            const R *r = rp + sgn * K, *hh = Hw + lo * kpad;
+            Dot<R> d;
+#pragma unroll 2
+            for (int k = 0; k < K; ++k) d.add(r[k], hh[k]);
+            cw[sgn * (N + 1) + lb + lo] = d.value();
+        }
+        __syncwarp();
+    }
+}
+
 // Stage data of the nodes c = cfirst + i cstep (i < nn <= ncap) of tile `tile`
 // for buffer `buf` (block-wide, all threads). Input in `scratch` (EqScratch
 // for ncap nodes): the equilibrium tables (EqTab), the raw moment sums of the
@@ -563,63 +620,31 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
     R *rp = reinterpret_cast<R *>(scratch + L.wk + warp * L.wbytes);   // [2][K] r^+, r^-
     R *cw = rp + 2 * K;                                                // [2][N+1] c^+, c^-
     R *Hw = cw + L.cstride;                                            // [kEqLB][kpad]
-    const int sgn = lane / kEqLB, lo = lane - sgn * kEqLB;             // the dot product of this lane
     for (int i = warp; i < nn; i += kWarps) {
         const R *x = sc + i * 8;
-        const R sT = x[0], a = x[1], a2 = x[2];
-        // weights r_k^{+-} = W_k exp(+-a Y_k - a^2/2) and recurrence arguments sqrt(T') Y_k
-        R zt[2], h[2], hp[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {   // K <= 46: projection nodes lane and lane + 32
-            const int k = lane + 32 * u;
-            zt[u] = R(0);
-            h[u] = h0;
-            hp[u] = R(0);
-            if (k < K) {
-                const R Y = Yk[k], W = Wk[k];
-                rp[k] = W * exp(a * Y - a2);
-                rp[K + k] = W * exp(-a * Y - a2);
-                zt[u] = sT * Y;
-            }
-        }
-        // c^{+-}_l = sum_k r_k^{+-} h_l(sqrt(T') Y_k), in blocks of kEqLB orders: lanes run the
-        // recurrence of h_l at their projection nodes, then lane (sign, l) takes one dot product
-        for (int lb = 0; lb <= N; lb += kEqLB) {
-            const int le = min(N, lb + kEqLB - 1);
-            for (int l = lb; l <= le; ++l) {
-                const R al = alpha[l], sb = sbeta[l], isb1 = isbeta[l + 1];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int k = lane + 32 * u;
-                    if (k < K) Hw[(l - lb) * L.kpad + k] = h[u];
-                    const R hn = ((zt[u] - al) * h[u] - sb * hp[u]) * isb1;
-                    hp[u] = h[u];
-                    h[u] = hn;
-                }
-            }
-            __syncwarp();
-            if (lb + lo <= le) {
-                const R *r = rp + sgn * K, *hh = Hw + lo * L.kpad;
-                Dot<R> d;
-                for (int k = 0; k < K; ++k) d.add(r[k], hh[k]);
-                cw[sgn * (N + 1) + lb + lo] = d.value();
-            }
-            __syncwarp();
-        }
-        // factors: g_x/w at (node, a) = sum_l h_l(z_a) c_l^{sign a}, g_y/w at (node, j) = sum_l He_l(y_j) b_l
+        if (K <= 32)
+            project_coefficients<R, 1>(x[0], x[1], x[2], K, N, L.kpad, Yk, Wk, alpha, sbeta, isbeta, h0, rp, cw, Hw);
+        else
+            project_coefficients<R, 2>(x[0], x[1], x[2], K, N, L.kpad, Yk, Wk, alpha, sbeta, isbeta, h0, rp, cw, Hw);
+        // factors: g_x/w at (node, a) = sum_l h_l(z_a) c_l^{sign a}, g_y/w at (node, j) = sum_l He_l(y_j) b_l.
+        // Evaluating the truncated expansions at the nodes is a plain FMA chain: where its terms
+        // cancel (the far tails of hot or cold Maxwellians) the factor's absolute error stays far
+        // below what the quadrature weight of that velocity lets reach any moment.
         R *col = eqg + cfirst + i * cstep;
         for (int ig = lane; ig < G; ig += 32) {
-            Dot<R> d;
+            R acc = R(0);
             if (ig < 2 * Qx) {
                 const int ii = ig < Qx ? ig : ig - Qx;
                 const R *cc = cw + (ig < Qx ? 0 : N + 1);
-                for (int l = 0; l <= N; ++l) d.add(hz[l * Qx + ii], cc[l]);
+#pragma unroll 4
+                for (int l = 0; l <= N; ++l) acc = fma(hz[l * Qx + ii], cc[l], acc);
             } else {
                 const int jj = ig - 2 * Qx;
                 const R *b = bb + i * (Ny + 1);
-                for (int l = 0; l <= Ny; ++l) d.add(He[l * Qy + jj], b[l]);
+#pragma unroll 4
+                for (int l = 0; l <= Ny; ++l) acc = fma(He[l * Qy + jj], b[l], acc);
             }
-            col[(size_t)ig * kLanes] = d.value();
+            col[(size_t)ig * kLanes] = acc;
         }
         __syncwarp();   // the next node reuses this warp's slice
     }
@@ -631,9 +656,14 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
 template <typename R>
 __device__ __forceinline__ R outgoing_wall_face(const R *row, int Nx, bool right)
 {
+    // L2 loads (.cg): in the persistent form another SM wrote these rows in the same launch
     R f1, f2, f3, f4;
-    if (right) { f1 = row[2 * (Nx - 1)]; f2 = row[2 * (Nx - 2)]; f3 = row[2 * (Nx - 3)]; f4 = row[2 * (Nx - 4)]; }
-    else       { f1 = row[0];            f2 = row[2];            f3 = row[4];            f4 = row[6]; }
+    if (right) {
+        f1 = __ldcg(row + 2 * (Nx - 1)); f2 = __ldcg(row + 2 * (Nx - 2));
+        f3 = __ldcg(row + 2 * (Nx - 3)); f4 = __ldcg(row + 2 * (Nx - 4));
+    } else {
+        f1 = __ldcg(row); f2 = __ldcg(row + 2); f3 = __ldcg(row + 4); f4 = __ldcg(row + 6);
+    }
     R g1 = R(4) * f1 - R(6) * f2 + R(4) * f3 - f4;
     R g2 = R(10) * f1 - R(20) * f2 + R(15) * f3 - R(4) * f4;
     return weno5<R>(f3, f2, f1, g1, g2);
@@ -669,7 +699,7 @@ __device__ void block_wall_density(const DevTables &T, const R *phi, bool right,
 __device__ double block_mass_deviation(const double *dm, int Nx, double *red)
 {
     double acc = 0.0;
-    for (int s = threadIdx.x; s < Nx; s += kThreads) acc += dm[s];
+    for (int s = threadIdx.x; s < Nx; s += kThreads) acc += __ldcg(dm + s);   // written by other tiles
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -689,7 +719,7 @@ struct Layout {
     __host__ __device__ Layout(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster, int ntab)
     {
         size_t o = 0;
-        bar = o;  o = al(o + (kPipe + 2) * sizeof(uint64_t) + (2 * kPipe + 1) * sizeof(uint32_t));
+        bar = o;  o = al(o + (kPipe + 2) * sizeof(uint64_t) + (kPipe + 1) * sizeof(uint32_t));
         pipe = o;
         fin = o;
         f0 = fin + (size_t)kPipe * 2 * kSubV * kRowLen * sizeof(R);
@@ -709,13 +739,32 @@ struct Layout {
     __host__ __device__ static int node_cap(int cluster) { return (kTile + cluster - 1) / cluster; }
 };
 
+// TVD RK-3 (Shu & Osher): stage k's output is ca f^n + cb (y_k + dt L(y_k)).
+template <typename R> __host__ __device__ constexpr R ca_of(int k) { return R(k == 0 ? 0.0 : (k == 1 ? 0.75 : 1.0 / 3.0)); }
+template <typename R> __host__ __device__ constexpr R cb_of(int k) { return R(k == 0 ? 1.0 : (k == 1 ? 0.25 : 2.0 / 3.0)); }
+
+// Kahan's compensated sum on packed pairs: s + x with the rounding error carried in c.
+__device__ __forceinline__ void kahan2(f2 &s, f2 &c, f2 x)
+{
+    const f2 y = x - c, t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+__device__ __forceinline__ void kahan1(float &s, float &c, float x)
+{
+    const float y = x - c, t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 // One RK stage of tile `tile` of instance I, for the CTA's velocity chunk
 // blockIdx.y (body of both stage kernels below). kExt compiles in the half
 // channel's symmetry plane and the local steps with mass renormalisation
 // (instances without them give the same results in either form).
-template <typename R, bool kExt>
-__device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, int rel)
+template <typename R, bool kExt, int kStage>
+__device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, bool persist = false)
 {
+    constexpr int stage = kStage;   // RK stage 0, 1, 2: a compile-time constant in every form
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     const DevTables &T = I.T;
     const DevState &S = I.S;
@@ -727,7 +776,6 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     uint64_t *bar_data = bar + kPipe, *bar_tab = bar + kPipe + 1;
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(bar + kPipe + 2);   // [kPipe] warps done with a slot
     int *s_abort = reinterpret_cast<int *>(s_cnt + kPipe);              // a warp gave up waiting
-    uint32_t *s_fill = s_cnt + kPipe + 1;                               // [kPipe] copies issued per slot
     R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][kSubV][2 kRowLen]: (phi, chi) per node
     R *s_f0 = reinterpret_cast<R *>(smem + L.f0);         // [kPipe][kSubV][2 kF0Len]
     R *s_g = reinterpret_cast<R *>(smem + L.g);           // [2Qx + Qy][kLanes]
@@ -747,9 +795,9 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     // ---- early stop (run-to-steady): every block of the instance takes the same decision ----
     const double stop_eps = ctl->stop_eps;
     if (stop_eps > 0.0) {
-        if (ctl->stopped) return;
+        if (__ldcg(&ctl->stopped)) return;
         if (step - 1 >= ctl->check_from) {
-            double rprev = __longlong_as_double((long long)S.resid[(step - 1) % kResidRing]);
+            const double rprev = __longlong_as_double((long long)__ldcg(&S.resid[(step - 1) % kResidRing]));
             if (rprev < stop_eps) {
                 if (stage == 0 && lead) {
                     ctl->stop_step = step;
@@ -759,7 +807,9 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
             }
         }
     }
-    if (stage == 0 && lead) S.resid[step % kResidRing] = 0ull;
+    // the step's residual slot starts at zero (the persistent form zeroes its steps' slots before
+    // the launch: its stages of one step may run in any order across tiles)
+    if (stage == 0 && lead && !persist) S.resid[step % kResidRing] = 0ull;
 
     // this CTA's velocity rows [vbeg, vend): may be empty for a small instance in a wide cluster
     const int vbeg = min(V, chunk * T.vchunk);
@@ -780,7 +830,6 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     // RK base (nodes xf ..), both fields; rows past V read as zeros
     auto issue = [&](int sub) {
         int p = sub % kPipe, v0 = vbeg + sub * kSubV;
-        s_fill[p] += 1;   // one issuer per slot at a time: a slot is refilled only once every warp released it
         mbar_expect_tx(&bar[p], tx_bytes);
         tma_load_2d(s_fin + (size_t)p * kSubV * 2 * kRowLen, in_map, 2 * x0, v0, &bar[p]);
         if (stage > 0) tma_load_2d(s_f0 + (size_t)p * kSubV * 2 * kF0Len, &M.f0, 2 * xf, v0, &bar[p]);
@@ -788,7 +837,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
 
     if (tid == 0) {
         for (int p = 0; p < kPipe + 2; ++p) mbar_init(&bar[p], 1);
-        for (int p = 0; p < kPipe; ++p) s_cnt[p] = s_fill[p] = 0;
+        for (int p = 0; p < kPipe; ++p) s_cnt[p] = 0;
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -818,16 +867,20 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     // local steps: this step's mass correction lambda - 1 = (M_ref - M(f^n)) / M(f^n), from the
     // mass deviations of f^n that the previous step (or the set-up) left for this step's parity
     const bool renorm = kExt && T.lts != 0 && stage == 2;
-    const bool comp = kExt && T.comp != 0 && stage == 2;   // compensated FP32 state (DevState::C)
+    // compensated FP32 state (DevState::C, DevState::A): every stage adds its dt L to the step's
+    // increment, so the third stage adds dt (L0/6 + L1/6 + 2 L2/3) to d0 + c without rounding it
+    // at the size of the state first
+    const bool comp_any = kExt && T.comp != 0;
+    const bool comp = comp_any && stage == 2;
     double lam1 = 0.0;
     if (renorm) {
         const double dM = block_mass_deviation(S.mass + kMassHdr + (size_t)(step & 1) * T.Nxp, T.Nx, s_misc);
         lam1 = (S.mass[0] - dM) / (T.mrest + dM);
     }
-    bool timed_out = __syncthreads_or(!mbar_wait(bar_data, 0));
-    // test hook: wait on the table barrier, which nothing has armed yet, so the wait gives up
+    // test hook (probe > 0): wait instead on the table barrier, which nothing has armed yet, so
+    // that the bounded wait gives up; the timeout path below then waits for the data copy
     const int probe = ctl->probe;
-    if (probe > 0) timed_out = __syncthreads_or(!mbar_wait(bar_tab, 0, probe)) || timed_out;
+    bool timed_out = __syncthreads_or(!mbar_wait(probe > 0 ? bar_tab : bar_data, 0, probe > 0 ? probe : kSpinLimit));
 
     const int s = c0 + lane;
     const bool active = lane < nloc;
@@ -843,8 +896,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
 
     // ---- (3) stream the chunk's velocity rows: every warp runs its own rows of each
     // pipeline slot; the last warp to release a slot issues its refill ----
-    const R ca = R(stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0));
-    const R cb = R(stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0));
+    const R ca = ca_of<R>(stage), cb = cb_of<R>(stage);
     const bool wall = needL || needR;
     const R lam1r = R(lam1);
     const int ck = lane + 3 + off;          // node column of node c0 + lane
@@ -855,9 +907,16 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
 #pragma unroll
     for (int m = 0; m < kNumRaw; ++m) acc[m] = R(0);
     R res = R(0);
-    f2 pk[5];
+    f2 pk[5], pkc[5];   // FP32: running raw sums as packed pairs; pkc: their Kahan compensation
 #pragma unroll
-    for (int m = 0; m < 5; ++m) pk[m] = bc2(0.f);
+    for (int m = 0; m < 5; ++m) pk[m] = pkc[m] = bc2(0.f);
+    float sxyc = 0.f;
+    // plain FP32 form: the stage's update out = ca d0 + k1 d + k2 (target - ft_rest) + k3 p_x (F_left - F_right)
+    // with the node's constants folded (k1 = cb (1 - dt/tau), k2 = cb dt/tau, k3 = cb dt/(J deta)),
+    // and the Shakhov factor's cS q folded into (shA, shB) = cS (q_x, q_y)
+    constexpr bool kLean = std::is_same<R, float>::value && !kExt;
+    const R k1 = cb_of<R>(stage) * (R(1) - dt * nu_c), k2 = cb_of<R>(stage) * dt * nu_c;
+    const R k3 = cb_of<R>(stage) * dt * ijd, shA = cS_c * qx_c, shB = cS_c * qy_c;
     constexpr int NQ = kSubV / kWarps;      // rows per warp and slot: rows warp + kWarps q
     bool my_timeout = false;
 
@@ -872,8 +931,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                 const int a = v / T.Qy, j = v - a * T.Qy;
                 const int vm = (a < T.Qx ? a + T.Qx : a - T.Qx) * T.Qy + (T.Qy - 1 - j);
                 const R *src = Fin + 2 * ((size_t)vm * T.Nxp + g);
-                mg0 = src[0];
-                mg1 = src[1];
+                mg0 = __ldcg(src);
+                mg1 = __ldcg(src + 1);
             }
         }
     };
@@ -960,8 +1019,99 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
             __syncwarp();
             mirror_fetch(sub + 1);
         }
-        if constexpr (std::is_same<R, float>::value) {
+        if constexpr (kLean) {
+            // plain FP32 form: (phi, chi) as packed pairs. Rows warp + kWarps q of the slot; a
+            // row past the chunk computes on the chunk's last row and stores nothing.
+            const int vs = vbeg + sub * kSubV;                  // first row of the slot
+            const int v0 = vs + warp;                           // this warp's row q = 0
+            const float *rowq = fin + (size_t)warp * 2 * kRowLen + 2 * (ck - 3);   // row q = 0, node ck - 3
+            const float *b0 = f0 + (size_t)warp * 2 * kF0Len + 2 * (lane + offf);
+            const int vlast = min(vs + kSubV, vend) - 1, vhalf = T.Qx * T.Qy;
+            const int side = vlast < vhalf ? 1 : (vs >= vhalf ? -1 : 0);   // every row left / right / mixed
+            f2 ps[5];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) ps[m] = bc2(0.f);
+            float psxy = 0.f;
+            // rows in pairs (q = qp, qp + 1): two WENO chains in flight, fewer live registers
+#pragma unroll
+            for (int qp = 0; qp < NQ; qp += 2) {
+                f2 fl[2], dd[2];
+#pragma unroll
+                for (int qi = 0; qi < 2; ++qi) {
+                    const int q = qp + qi;
+                    const bool pos = side > 0 || (side == 0 && v0 + kWarps * q < vhalf);   // uniform per warp
+                    const float *pp = rowq + (size_t)q * kWarps * 2 * kRowLen + (pos ? 0 : 2);
+                    const f2 a = ld2(pp), b = ld2(pp + 2), c = ld2(pp + 4), d = ld2(pp + 6), e = ld2(pp + 8);
+                    if (side != 0) {
+                        fl[qi] = side > 0 ? weno5_2(a, b, c, d, e) : weno5_2(e, d, c, b, a);
+                        dd[qi] = side > 0 ? d : c;
+                    } else {
+                        fl[qi] = weno5_2(pos ? a : e, pos ? b : d, c, pos ? d : b, pos ? e : a);
+                        dd[qi] = pos ? d : c;
+                    }
+                }
+#pragma unroll
+                for (int qi = 0; qi < 2; ++qi) {
+                    const int q = qp + qi;
+                    const int v = v0 + kWarps * q;
+                    const bool okq = v < vend;
+                    const float *xr = s_vrow + (size_t)(min(v, vend - 1) - vbeg) * kVRow;
+                    const float4 xa = *reinterpret_cast<const float4 *>(xr);       // p_x p_y w ft_rest
+                    const float2 xg = *reinterpret_cast<const float2 *>(xr + VR_GA);
+                    const float px = xa.x, py = xa.y, w = xa.z, fr = xa.w;
+                    if (wall) {   // wall faces: the incoming population n_w f_w (Eq. diffuse)
+                        const float4 xw = *reinterpret_cast<const float4 *>(xr + VR_FWL);
+                        if (needL && px > 0.f && s == 0) fl[qi] = mk2(nwL * xw.x - fr, nwL * xw.y - fr);
+                        if (needR && px < 0.f && s == Nx) fl[qi] = mk2(nwR * xw.z - fr, nwR * xw.w - fr);
+                    }
+                    const float feq = n_c * s_g[__float_as_int(xg.x) + lane] * s_g[__float_as_int(xg.y) + lane];
+                    const float xx = px - ux_c, xy = py - uy_c;
+                    const float xx2 = xx * xx, e2 = fmaf(xy, xy, xx2);
+                    const float sq = fmaf(shA, xx, shB * xy);        // cS (q . xi)
+                    const float h = e2 * i5T;                         // xi^2 / (5 T)
+                    // Shakhov targets minus the rest state (Sec. II, the reduced S_phi, S_chi)
+                    const float fT = T_c * feq;                       // chi_eq = T phi_eq
+                    const float tp = fmaf(feq * sq, h - 0.8f, feq) - fr;
+                    const float tc = fmaf(fT * sq, h - 0.4f, fT) - fr;
+                    float fll, flh;
+                    un2(fl[qi], fll, flh);
+                    const float frl = __shfl_down_sync(0xffffffffu, fll, 1);
+                    const float frh = __shfl_down_sync(0xffffffffu, flh, 1);
+                    float dl, dh;
+                    un2(dd[qi], dl, dh);
+                    const float kp = k3 * px;
+                    float ol = fmaf(kp, fll - frl, fmaf(k2, tp, k1 * dl));
+                    float oh = fmaf(kp, flh - frh, fmaf(k2, tc, k1 * dh));
+                    if constexpr (stage > 0) {
+                        float d0l, d0h;
+                        un2(ld2(b0 + (size_t)q * kWarps * 2 * kF0Len), d0l, d0h);
+                        ol = fmaf(ca_of<float>(stage), d0l, ol);
+                        oh = fmaf(ca_of<float>(stage), d0h, oh);
+                        if constexpr (stage == 2)
+                            if (active && okq) res = fmaxf(res, w * fmaxf(fabsf(ol - d0l), fabsf(oh - d0h)));
+                    }
+                    if (active && okq) {
+                        st2(Fout_s + 2 * (size_t)Nxp * v, mk2(ol, oh));
+                        const float fw = w * ol, gw = w * oh;
+                        ps[0] = ps[0] + mk2(fw, gw);                                  // (S0, CZ)
+                        ps[1] = fma2(mk2(xx, xy), bc2(fw), ps[1]);                    // (SX, SY)
+                        ps[2] = fma2(mk2(xx, xy), bc2(gw), ps[2]);                    // (GX, GY)
+                        ps[3] = fma2(mk2(xx2, xy * xy), bc2(fw), ps[3]);              // (SXX, SYY)
+                        ps[4] = fma2(mk2(e2 * xx, e2 * xy), bc2(fw), ps[4]);          // (R3X, R3Y)
+                        psxy = fmaf(xx * xy, fw, psxy);
+                    }
+                }
+            }
+            // the slot's partial sums into the running sums, compensated (Kahan)
+#pragma unroll
+            for (int m = 0; m < 5; ++m) kahan2(pk[m], pkc[m], ps[m]);
+            kahan1(acc[R_SXY], sxyc, psxy);
+        } else if constexpr (std::is_same<R, float>::value) {
             // FP32: (phi, chi) as packed pairs, loaded and stored as one 64-bit access each.
+            f2 ps[5];   // the slot's partial moment sums
+#pragma unroll
+            for (int m = 0; m < 5; ++m) ps[m] = bc2(0.f);
+            float psxy = 0.f;
             // Face c0 + lane of each row: rows v < Qx Qy have p_x > 0 and upwind from the
             // left (nodes ck-3 .. ck+1), the others from the right (nodes ck+2 .. ck-2). A slot
             // whose rows all share a side loads its stencils at fixed offsets.
@@ -1031,13 +1181,18 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                 // Shakhov targets minus the rest state: (phi_eq (1 + S_phi), chi_eq (1 + S_chi)) - ft_rest
                 const f2 sh = fma2(bc2(cS_c * qxi), bc2(e2 * i5T) - mk2(0.8f, 0.4f), bc2(1.f));
                 const f2 tgt = fma2(mk2(feq, T_c * feq), sh, bc2(-fr));
-                f2 dn = fma2(bc2(dt), fma2(bc2(-nu_c), dd[q] - tgt, adv), dd[q]);
+                const f2 lr = fma2(bc2(-nu_c), dd[q] - tgt, adv);   // L of this stage
+                f2 dn = fma2(bc2(dt), lr, dd[q]);
+                const f2 dtl = comp_any ? bc2(dt) * lr : bc2(0.f);
+                float *ap = comp_any ? static_cast<float *>(S.A) + 2 * ((size_t)Nxp * v + s) : nullptr;
+                if (comp_any && stage < 2 && active && ok[q]) st2(ap, stage == 0 ? dtl : ld2(ap) + dtl);
                 if (stage > 0) {
                     const f2 d0 = ld2(f0 + (size_t)r * 2 * kF0Len + 2 * (lane + offf));
                     if (comp) {
-                        // the step's increment 2/3 (d2 + dt L(d2) - d0), added to d0 + c0 with its
+                        // the step's increment dt (L0 + L1) / 6 + 2/3 dt L2, added to d0 + c0 with its
                         // rounding error kept (TwoSum of Knuth): increments below half an ulp of d0 count
-                        f2 inc = bc2(2.f / 3.f) * (dn - d0);
+                        f2 inc = bc2(2.f / 3.f) * dtl;
+                        if (active && ok[q]) inc = fma2(bc2(1.f / 6.f), ld2(ap), inc);
                         if (renorm) inc = fma2(bc2(lam1r), d0 + inc + bc2(fr), inc);
                         float *cp = static_cast<float *>(S.C) + 2 * ((size_t)Nxp * v + s);
                         f2 cs = inc;
@@ -1067,14 +1222,18 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
                     float fw, gw;
                     un2(fg, fw, gw);
                     const f2 pxy = mk2(xx, xy);
-                    pk[0] = pk[0] + fg;                        // (S0, CZ)
-                    pk[1] = fma2(pxy, bc2(fw), pk[1]);         // (SX, SY)
-                    pk[2] = fma2(pxy, bc2(gw), pk[2]);         // (GX, GY)
-                    pk[3] = fma2(pxy * pxy, bc2(fw), pk[3]);   // (SXX, SYY)
-                    pk[4] = fma2(bc2(e2) * pxy, bc2(fw), pk[4]);   // (R3X, R3Y)
-                    acc[R_SXY] = fmaf(xx * xy, fw, acc[R_SXY]);
+                    ps[0] = ps[0] + fg;                        // (S0, CZ)
+                    ps[1] = fma2(pxy, bc2(fw), ps[1]);         // (SX, SY)
+                    ps[2] = fma2(pxy, bc2(gw), ps[2]);         // (GX, GY)
+                    ps[3] = fma2(pxy * pxy, bc2(fw), ps[3]);   // (SXX, SYY)
+                    ps[4] = fma2(bc2(e2) * pxy, bc2(fw), ps[4]);   // (R3X, R3Y)
+                    psxy = fmaf(xx * xy, fw, psxy);
                 }
             }
+            // the slot's partial sums into the running sums, compensated (Kahan)
+#pragma unroll
+            for (int m = 0; m < 5; ++m) kahan2(pk[m], pkc[m], ps[m]);
+            kahan1(acc[R_SXY], sxyc, psxy);
         } else {
             // FP64: rows in pairs (q = qp, qp + 1), which bounds the live registers
 #pragma unroll
@@ -1177,16 +1336,21 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
         // still takes part in the cluster barriers below, without touching data
         if (tid == 0) {
             atomicExch(&ctl->timeout, 1);
-            // a slot has at most one copy outstanding (it is refilled only after every warp
-            // waited for its previous copy): wait for the last one issued to each slot
-            for (int p = 0; p < kPipe; ++p)
-                if (s_fill[p] > 0) mbar_wait(&bar[p], (s_fill[p] - 1) & 1);
+            // copies issued to slot p: its first fill (if p < nsub) and one refill per completed
+            // release round while rows remained. A slot has at most one copy outstanding (it is
+            // refilled only after every warp waited for its previous copy): wait for the last one
+            for (int p = 0; p < kPipe && p < nsub; ++p) {
+                const int rounds = (int)(s_cnt[p] / kWarps);
+                const int fills = 1 + min(rounds, (nsub - 1 - p) / kPipe);
+                mbar_wait(&bar[p], (uint32_t)((fills - 1) & 1));
+            }
             mbar_wait(bar_data, 0);
         }
         __syncthreads();
         cluster_wait();
         cluster_arrive();
         cluster_wait();
+        if (persist && tid < kPipe + 2) mbar_inval(&bar[tid]);   // the next item initialises them again
         return;
     }
 
@@ -1196,6 +1360,10 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
         bulk_load(scr + E.tab, Tabs<R>::eqtab(T), tab_bytes, bar_tab);
     }
     if constexpr (std::is_same<R, float>::value) {
+        // Kahan's sum is s - c
+#pragma unroll
+        for (int m = 0; m < 5; ++m) pk[m] = pk[m] - pkc[m];
+        acc[R_SXY] -= sxyc;
         un2(pk[0], acc[R_S0], acc[R_CZ]);
         un2(pk[1], acc[R_SX], acc[R_SY]);
         un2(pk[2], acc[R_GX], acc[R_GY]);
@@ -1246,27 +1414,161 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int stage, i
     // local steps: the mass deviations of f^{n+1} (buffer 0) for the next step's parity
     double *dm = renorm ? S.mass + kMassHdr + (size_t)((step + 1) & 1) * T.Nxp : nullptr;
     node_equilibrium<R>(T, S, out, tile, rank, nch, nn, ncap, scr, dm, nullptr);
+    if (persist) {   // the item's mbarriers are done with: the next item initialises them again
+        __syncthreads();
+        if (tid < kPipe + 2) mbar_inval(&bar[tid]);
+    }
 }
 
 // Single instance: the descriptor is a kernel parameter (constant bank), grid (ntile, nchunk).
-template <typename R, bool kExt>
+template <typename R, bool kExt, int kStage>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
-stage_kernel(const __grid_constant__ Inst I, int stage, int rel)
+stage_kernel(const __grid_constant__ Inst I, int rel)
 {
-    stage_body<R, kExt>(I, blockIdx.x, stage, rel);
+    stage_body<R, kExt, kStage>(I, blockIdx.x, rel);
 }
 
 // Batch: descriptors in device memory, one cluster per work item (instance, tile).
 // Three CTAs per SM in FP32: the descriptor fields live in registers here (in the
 // single-instance kernel they are constant-bank operands), and measured on GB300
 // the unspilled 3-CTA form is faster than a spilling 4-CTA form.
-template <typename R, bool kExt>
+template <typename R, bool kExt, int kStage>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
-stage_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int stage, int rel)
+stage_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int rel)
 {
     const int2 wk = work[blockIdx.x];
     if (wk.x < 0) return;   // empty work slot: the whole cluster leaves
-    stage_body<R, kExt>(insts[wk.x], wk.y, stage, rel);
+    stage_body<R, kExt, kStage>(insts[wk.x], wk.y, rel);
+}
+
+// ---- persistent form: one launch for a group of steps of every work item ----
+//
+// Items (step, stage, work item) are handed out in that order from one counter to
+// clusters that are all resident (cooperative launch, grid <= active clusters). An
+// item waits until the tile and its two neighbours (the stencil's halo) finished
+// the previous stage (done[w] counts a tile's finished stage items); an instance
+// with early stop or local steps also waits, at stage 0, for its whole previous
+// step (the residual and the mass are instance-wide). Every earlier item is held
+// by a resident cluster, so every wait ends; each is also bounded, and on timeout
+// the item's instance records it and the whole launch aborts.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void st_cluster_u32(unsigned *local, uint32_t rank, unsigned v)
+{
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(local)), "r"(rank));
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+
+constexpr unsigned long long kDepWaitNs = 2000000000ull;   // 2 s per dependency wait at most
+
+// Waits until *p >= need (acquire); false on timeout or abort.
+__device__ bool wait_at_least(const unsigned *p, unsigned need, const unsigned *abort)
+{
+    if (ld_acquire_gpu(p) >= need) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        __nanosleep(128);
+        if (ld_acquire_gpu(p) >= need) return true;
+        if (ld_acquire_gpu(abort) != 0u || global_ns() - t0 > kDepWaitNs) return false;
+    }
+}
+
+template <typename R, bool kExt>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
+persistent_stage_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int nwork, int nsteps,
+                        unsigned *cnt)
+{
+    // counters (zeroed before the launch): cnt[0] items handed out, cnt[1] abort flag,
+    // cnt[4 + w] finished stage items of work item w, cnt[4 + nwork + i] tiles of instance i
+    // that finished a step's third stage
+    unsigned *next = cnt, *abort = cnt + 1, *done = cnt + kPersistHdr, *inst_done = cnt + kPersistHdr + nwork;
+    __shared__ unsigned s_item[2];   // this cluster's item and whether its dependencies are met
+    const int tid = threadIdx.x;
+    const uint32_t rank = cluster_ctarank(), csize = gridDim.y;
+    const unsigned total = (unsigned)nsteps * 3u * (unsigned)nwork;
+    cluster_arrive();   // every CTA of the cluster runs before the first item is written into its shared memory
+    cluster_wait();
+    for (;;) {
+        if (rank == 0 && tid == 0) {
+            unsigned item = atomicAdd(next, 1u), ok = 1u;
+            if (item < total && ld_acquire_gpu(abort) == 0u) {
+                const int rel = (int)(item / (3u * nwork)), stage = (int)((item / nwork) % 3u), w = (int)(item % nwork);
+                const int2 wk = work[w];
+                if (wk.x >= 0) {
+                    const Inst &I = insts[wk.x];
+                    const unsigned need = 3u * rel + stage;
+                    for (int dt = -1; dt <= 1 && ok; ++dt) {
+                        const int t = wk.y + dt;
+                        if (t >= 0 && t < I.T.ntile) ok = wait_at_least(&done[w + dt], need, abort);
+                    }
+                    // early stop and local steps use instance-wide data of the previous step
+                    if (ok && stage == 0 && rel > 0 && (I.T.lts || I.S.ctl->stop_eps > 0.0))
+                        ok = wait_at_least(&inst_done[wk.x], (unsigned)(rel * I.T.ntile), abort);
+                    if (!ok) {
+                        atomicExch(&I.S.ctl->timeout, 1);
+                        atomicExch(abort, 1u);
+                    }
+                }
+            } else {
+                item = total;
+            }
+            for (uint32_t r = 0; r < csize; ++r) {
+                st_cluster_u32(&s_item[0], r, item);
+                st_cluster_u32(&s_item[1], r, ok);
+            }
+        }
+        cluster_arrive();
+        cluster_wait();
+        const unsigned item = s_item[0], ok = s_item[1];
+        if (item >= total || !ok) break;
+        if (tid == 0) {   // the producers' writes, seen by this CTA's loads and its TMA copies
+            __threadfence();
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
+        __syncthreads();
+        const int rel = (int)(item / (3u * nwork)), stage = (int)((item / nwork) % 3u), w = (int)(item % nwork);
+        const int2 wk = work[w];
+        if (wk.x >= 0) {
+            const Inst &I = insts[wk.x];
+            if (stage == 0) stage_body<R, kExt, 0>(I, wk.y, rel, true);
+            else if (stage == 1) stage_body<R, kExt, 1>(I, wk.y, rel, true);
+            else stage_body<R, kExt, 2>(I, wk.y, rel, true);
+        }
+        // completion: every CTA's writes fenced, then the tile's counter (and, after the
+        // third stage, the instance's) released by the cluster's first CTA
+        __syncthreads();
+        if (tid == 0) __threadfence();
+        cluster_arrive();
+        cluster_wait();
+        if (rank == 0 && tid == 0) {
+            atomicAdd(&done[w], 1u);
+            if (stage == 2 && wk.x >= 0) atomicAdd(&inst_done[wk.x], 1u);
+        }
+        __syncthreads();
+    }
+}
+
+// Zeroes the residual slots of the steps [base, base + nsteps) of every instance (the
+// persistent form's stages of a step run in any order across tiles).
+__global__ void zero_resid_kernel(const Inst *insts, int n, int nsteps)
+{
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const Inst &I = insts[k];
+        if (I.S.ctl->stop_eps > 0.0 && I.S.ctl->stopped) continue;   // keeps its last step's residual
+        const long long base = I.S.ctl->base;
+        for (int j = threadIdx.x; j < nsteps; j += blockDim.x) I.S.resid[(base + j) % kResidRing] = 0ull;
+    }
 }
 
 // Stage data of every tile of buffer `buf` from the chunk partials of
@@ -1417,12 +1719,25 @@ cudaError_t configure_kernels()
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const void *stage_fns[4] = {(const void *)stage_kernel<R, false>, (const void *)stage_kernel<R, true>,
-                                (const void *)stage_batch_kernel<R, false>, (const void *)stage_batch_kernel<R, true>};
-    for (const void *fn : stage_fns) {
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    const void *stage_fns[12] = {
+        (const void *)stage_kernel<R, false, 0>,       (const void *)stage_kernel<R, false, 1>,
+        (const void *)stage_kernel<R, false, 2>,       (const void *)stage_kernel<R, true, 0>,
+        (const void *)stage_kernel<R, true, 1>,        (const void *)stage_kernel<R, true, 2>,
+        (const void *)stage_batch_kernel<R, false, 0>, (const void *)stage_batch_kernel<R, false, 1>,
+        (const void *)stage_batch_kernel<R, false, 2>, (const void *)stage_batch_kernel<R, true, 0>,
+        (const void *)stage_batch_kernel<R, true, 1>,  (const void *)stage_batch_kernel<R, true, 2>};
+    // dynamic shared memory up to the opt-in limit less the kernel's static shared memory
+    auto allow = [&](const void *fn) {
+        cudaFuncAttributes fa = {};
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    }
+    };
+    for (const void *fn : stage_fns) allow(fn);
+    const void *persist_fns[2] = {(const void *)persistent_stage_kernel<R, false>,
+                                  (const void *)persistent_stage_kernel<R, true>};
+    for (const void *fn : persist_fns) allow(fn);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tile_equilibrium_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     return e;
@@ -1458,8 +1773,16 @@ cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStr
 {
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = cluster_config((unsigned)I.T.ntile, I.T.nchunk, smem, st, at);
-    if (I.T.half || I.T.lts || I.T.comp) return cudaLaunchKernelEx(&cfg, stage_kernel<R, true>, I, stage, rel);
-    return cudaLaunchKernelEx(&cfg, stage_kernel<R, false>, I, stage, rel);
+    const bool ext = I.T.half || I.T.lts || I.T.comp;
+    switch (stage + 3 * ext) {
+    case 0: return cudaLaunchKernelEx(&cfg, stage_kernel<R, false, 0>, I, rel);
+    case 1: return cudaLaunchKernelEx(&cfg, stage_kernel<R, false, 1>, I, rel);
+    case 2: return cudaLaunchKernelEx(&cfg, stage_kernel<R, false, 2>, I, rel);
+    case 3: return cudaLaunchKernelEx(&cfg, stage_kernel<R, true, 0>, I, rel);
+    case 4: return cudaLaunchKernelEx(&cfg, stage_kernel<R, true, 1>, I, rel);
+    case 5: return cudaLaunchKernelEx(&cfg, stage_kernel<R, true, 2>, I, rel);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // One cluster per work item (instance, tile): its `cluster` chunk CTAs (cluster dimension y).
@@ -1479,8 +1802,64 @@ cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, i
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (ext) return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true>, insts, work, stage, rel);
-    return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false>, insts, work, stage, rel);
+    switch (stage + 3 * ext) {
+    case 0: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 0>, insts, work, rel);
+    case 1: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 1>, insts, work, rel);
+    case 2: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 2>, insts, work, rel);
+    case 3: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 0>, insts, work, rel);
+    case 4: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 1>, insts, work, rel);
+    case 5: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 2>, insts, work, rel);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Persistent form: nsteps RK-3 steps of every work item in one cooperative launch of
+// nclusters clusters of `cluster` CTAs (all resident), after zeroing the item counters
+// (cnt: kPersistHdr + nwork + n) and the steps' residual slots.
+template <typename R>
+cudaError_t launch_persistent(const Inst *insts, const int2 *work, int nwork, int n, int cluster, int nclusters,
+                              size_t smem, int nsteps, bool ext, unsigned *cnt, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)(kPersistHdr + nwork + n) * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    zero_resid_kernel<<<std::min(n, 1024), 64, 0, st>>>(insts, n, nsteps);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nclusters, (unsigned)cluster, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = (unsigned)cluster;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    if (ext) return cudaLaunchKernelEx(&cfg, persistent_stage_kernel<R, true>, insts, work, nwork, nsteps, cnt);
+    return cudaLaunchKernelEx(&cfg, persistent_stage_kernel<R, false>, insts, work, nwork, nsteps, cnt);
+}
+
+// Clusters of the persistent kernel that can be resident at once.
+template <typename R>
+cudaError_t persistent_active_clusters(size_t smem, int cluster, int *nclusters)
+{
+    *nclusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, cluster, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = (unsigned)cluster;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(nclusters, persistent_stage_kernel<R, true>, &cfg);
 }
 
 template <typename R>
@@ -1499,8 +1878,8 @@ cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, int *ncl
     cfg.attrs = at;
     cfg.numAttrs = 1;
     // both forms of a kernel have the same launch bounds and shared memory: the plain one stands for both
-    return batch ? cudaOccupancyMaxActiveClusters(nclusters, stage_batch_kernel<R, false>, &cfg)
-                 : cudaOccupancyMaxActiveClusters(nclusters, stage_kernel<R, false>, &cfg);
+    return batch ? cudaOccupancyMaxActiveClusters(nclusters, stage_batch_kernel<R, false, 0>, &cfg)
+                 : cudaOccupancyMaxActiveClusters(nclusters, stage_kernel<R, false, 0>, &cfg);
 }
 
 template <typename R>
@@ -1567,6 +1946,9 @@ cudaError_t launch_last_residuals(const Inst *insts, const int *slots, int n, do
     template cudaError_t launch_tile_equilibrium<R>(const DevTables &, const DevState &, int, cudaStream_t);     \
     template cudaError_t launch_moments_partial<R>(const DevTables &, const DevState &, int, cudaStream_t);      \
     template cudaError_t stage_active_clusters<R>(size_t, int, bool, int *);                                          \
+    template cudaError_t launch_persistent<R>(const Inst *, const int2 *, int, int, int, int, size_t, int, bool,     \
+                                              unsigned *, cudaStream_t);                                          \
+    template cudaError_t persistent_active_clusters<R>(size_t, int, int *);                                           \
     template size_t equilibrium_smem_bytes<R>(int, int, int, int, int, int);                                         \
     template cudaError_t launch_moments_from_stage_data<R>(const DevTables &, const DevState &, cudaStream_t);  \
     template cudaError_t launch_state_in<R>(const double *, void *, void *, const DevTables &, int *, cudaStream_t); \

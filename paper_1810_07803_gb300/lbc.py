@@ -119,6 +119,7 @@ def lib():
         L.lbc_batch_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.lbc_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.lbc_batch_step_timed.argtypes = [vp, C.c_long, dp]
+        L.lbc_batch_set_persistent.argtypes = [vp, C.c_int]
         ip = C.POINTER(C.c_int)
         L.lbc_pool_create.argtypes = [C.c_int, C.c_int, C.c_size_t, C.c_int, C.c_int, vp, C.POINTER(vp)]
         L.lbc_pool_footprint.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_size_t)]
@@ -131,6 +132,7 @@ def lib():
         L.lbc_pool_get_state.argtypes = [vp, C.c_int, dp]
         L.lbc_pool_destroy.argtypes = [vp]
         L.lbc_pool_destroy.restype = None
+        L.lbc_measure_fp64_peak.argtypes = [dp]
         L.lbc_batch_destroy.argtypes = [vp]
         L.lbc_batch_destroy.restype = None
         for name in declared_functions():
@@ -183,6 +185,13 @@ def step_noalloc(params: dict, d_state: int, nsteps: int, stream=None) -> None:
     p = make_params(dict(DEFAULTS, **params))
     st = stream if stream is not None else current_stream_handle()
     _check(lib().lbc_step_noalloc(C.byref(p), C.c_void_p(d_state), int(nsteps), C.c_void_p(st) if st else None))
+
+
+def measure_fp64_peak() -> float:
+    """The device's FP64 FMA rate in TFLOP/s (lbc_measure_fp64_peak)."""
+    t = C.c_double()
+    _check(lib().lbc_measure_fp64_peak(C.byref(t)))
+    return t.value
 
 
 def current_stream_handle():
@@ -332,6 +341,10 @@ class Batch:
         c = C.c_int()
         _check(lib().lbc_batch_autotune(self._h, int(trial_steps), C.byref(c)))
         return c.value
+
+    def set_persistent(self, on: bool = True):
+        """Step as the persistent form (one launch per group of steps; lbc_batch_set_persistent)."""
+        _check(lib().lbc_batch_set_persistent(self._h, int(bool(on))))
 
     def moments(self, i: int):
         out = np.zeros((NMOM, self.Nx[i]))

@@ -144,17 +144,17 @@ class Server:
 
 
 def serve_sequential_fp64(requests: list[Request], residual: float = 1e-8, max_steps: int = 200_000,
-                          measure: int = 3) -> list[Request]:
-    """The plain comparison: one request at a time, single-instance FP64 solver,
-    in arrival order. The first `measure` requests are solved and timed; the
-    queue of the whole trace is then played with those service times in turn
-    (a single FIFO server: start = max(arrival, previous finish)), because one
-    FP64 solve takes seconds and a full trace would take minutes per rate."""
+                          measure: int = 0) -> list[Request]:
+    """The plain comparison: one request at a time, single-instance FP64 solver, in
+    arrival order (a single FIFO server). measure = 0: every request is solved in real
+    time (the server idles until the next arrival; latency = arrival to result).
+    measure = k > 0: only the first k requests are solved and timed, and the queue of
+    the whole trace is played with those service times in turn (start = max(arrival,
+    previous finish)), for traces whose FP64 solves would take too long to run."""
     reqs = sorted(requests, key=lambda r: r.arrival)
-    service = []
-    for r in reqs[:measure]:
+
+    def solve(r: Request) -> None:
         s = lbc.Solver(dict(r.params, precision="fp64"))
-        t0 = time.perf_counter()
         try:
             r.steps, r.residual = s.run_to_steady(residual, max_steps)
             r.converged = True
@@ -163,8 +163,23 @@ def serve_sequential_fp64(requests: list[Request], residual: float = 1e-8, max_s
                 raise
             r.steps, r.residual = s.steps, math.inf
         r.moments = s.moments()
-        service.append(time.perf_counter() - t0)
         s.close()
+
+    if measure <= 0:
+        t0 = time.perf_counter()
+        for r in reqs:
+            wait = r.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            r.admitted = time.perf_counter() - t0
+            solve(r)
+            r.finished = time.perf_counter() - t0
+        return reqs
+    service = []
+    for r in reqs[:measure]:
+        t1 = time.perf_counter()
+        solve(r)
+        service.append(time.perf_counter() - t1)
     free = 0.0
     for k, r in enumerate(reqs):
         r.admitted = max(r.arrival, free)
@@ -205,9 +220,10 @@ def main():
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--local-dt", action="store_true", help="local pseudo-time steps in both servers")
     ap.add_argument("--compensated", action="store_true", help="compensated FP32 state in the pool")
-    ap.add_argument("--sequential-measure", type=int, default=3,
-                    help="requests the FP64 sequential comparison solves and times (the rest are queued with "
-                         "those service times)")
+    ap.add_argument("--sequential-measure", type=int, default=0,
+                    help="0: the FP64 sequential comparison solves every request in real time; k > 0: it solves "
+                         "and times the first k and queues the rest with those service times")
+    ap.add_argument("--no-sequential", action="store_true", help="serve with the pool only")
     args = ap.parse_args()
     extra = dict(local_dt=1) if args.local_dt else {}
     for rate in (float(x) for x in args.rates.split(",")):
@@ -217,15 +233,20 @@ def main():
         served = srv.serve(trace)
         out = summary(served, "pool-fp32", rate, args.duration)
         srv.close()
+        out["local_dt"], out["compensated"] = bool(args.local_dt), bool(args.compensated)
+        if args.no_sequential:
+            print(json.dumps(out), flush=True)
+            continue
         seq = make_trace(rate, args.duration, args.seed, **extra)
         seq_out = serve_sequential_fp64(seq, args.residual, measure=args.sequential_measure)
         # moment error of the pool's FP32 results against the FP64 solves of the same requests
-        errs = [moment_error(r.moments, q.moments) for r, q in zip(served, seq_out[:args.sequential_measure])]
+        solved = seq_out if args.sequential_measure <= 0 else seq_out[:args.sequential_measure]
+        errs = [moment_error(r.moments, q.moments) for r, q in zip(served, solved)]
         out["moment_error_vs_fp64"] = max(errs) if errs else None
-        out["local_dt"], out["compensated"] = bool(args.local_dt), bool(args.compensated)
         print(json.dumps(out), flush=True)
         out = summary(seq_out, "sequential-fp64", rate, args.duration)
-        out["timing"] = f"{args.sequential_measure} solves measured, FIFO queue played with their service times"
+        out["timing"] = ("every request solved in real time" if args.sequential_measure <= 0 else
+                         f"{args.sequential_measure} solves measured, FIFO queue played with their service times")
         out["local_dt"] = bool(args.local_dt)
         print(json.dumps(out), flush=True)
 

@@ -1,0 +1,129 @@
+"""The persistent form of the batched stage kernel (lbc_batch_set_persistent): one
+cooperative launch per group of steps, clusters taking (step, stage, tile) items in
+order with bounded waits on their neighbours' stage counters. It computes what the
+per-stage launches compute: bit for bit in FP32 and for plain FP64 instances; for
+FP64 instances of the extended kernel form (local steps, half channel) the
+persistent kernel's own compilation of the stage (fused multiply-adds placed
+differently) leaves last-bit differences, measured at 1-2 ulp after 64 steps, and
+those are compared to 1e-14 relative. The uneven 512-solve batch is also sampled
+against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_1810_07803_gb300 import build, lbc, workloads
+from tests.helpers import gpu_available, moment_errors
+
+pytestmark = pytest.mark.gpu
+
+SQ2 = math.sqrt(2.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not gpu_available():
+        pytest.skip("no GPU")
+    build.build()
+
+
+def mixed(precision):
+    """Uneven instances: sizes, orders, stretching, non-isothermal walls, a collisionless one."""
+    return [dict(Nx=65, Qx=5, Qy=6, stretch_A=math.sqrt(0.9), delta=2.0, u_left=-0.1, u_right=0.2,
+                 T_left=0.8, T_right=1.25, omega=0.7, Pr=0.68, precision=precision),
+            dict(Nx=200, Qx=8, Qy=10, stretch_A=0.7, delta=5.0, u_left=-0.3, u_right=0.3, T_left=0.6,
+                 T_right=1.4, omega=0.6, precision=precision),
+            dict(Nx=40, Qx=4, Qy=5, delta=0.0, u_left=-0.2, u_right=0.1, T_left=1.2, T_right=0.7,
+                 precision=precision),
+            dict(workloads.c1(), precision=precision)]
+
+
+def extended(precision):
+    """Instances of the extended kernel form: local steps, half channel, compensated state."""
+    out = [dict(Nx=40, Qx=5, Qy=5, stretch_A=0.95, delta=0.3, u_left=-0.1, u_right=0.1, local_dt=1,
+                precision=precision),
+           dict(Nx=24, Qx=6, Qy=7, stretch_A=0.98, delta=1.0, u_left=-SQ2, u_right=SQ2, half_channel=1,
+                local_dt=1, precision=precision)]
+    if precision == "fp32":
+        out.append(dict(workloads.c1(), precision="fp32", compensated=1))
+    return out
+
+
+def states(b):
+    return [b.get_state(i) for i in range(b.n)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("kind", ["mixed", "extended"])
+def test_persistent_equals_stage_launches(precision, kind):
+    ps = mixed(precision) if kind == "mixed" else extended(precision)
+    a = lbc.Batch(ps, cluster=2)
+    b = lbc.Batch(ps, cluster=2)
+    b.set_persistent(True)
+    for n in (1, 3, 64, 66):   # eager groups and the captured group of 64 steps
+        a.step(n)
+        b.step(n)
+    for i, (x, y) in enumerate(zip(states(a), states(b))):
+        if precision == "fp64" and kind == "extended":
+            assert np.max(np.abs(x - y)) <= 1e-14 * np.max(np.abs(x)), i
+        else:
+            assert np.array_equal(x, y), i
+    assert [a.steps(i) for i in range(a.n)] == [b.steps(i) for i in range(b.n)]
+    a.close()
+    b.close()
+
+
+def test_persistent_run_to_steady_equals_stage_launches():
+    ps = [dict(p, precision="fp64") for p in mixed("fp64")[:2]] + [dict(workloads.c1(), delta=d) for d in (0.5, 3.0)]
+    a = lbc.Batch(ps)
+    b = lbc.Batch(ps)
+    b.set_persistent(True)
+    ka, ra = a.run_to_steady(1e-9, 20000, raise_notconv=False)
+    kb, rb = b.run_to_steady(1e-9, 20000, raise_notconv=False)
+    assert list(ka) == list(kb)
+    assert np.array_equal(np.asarray(ra), np.asarray(rb))
+    for x, y in zip(states(a), states(b)):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
+
+
+def test_persistent_bounded_wait_reports_timeout(monkeypatch):
+    ps = mixed("fp32")[:2]
+    b = lbc.Batch(ps)
+    b.set_persistent(True)
+    rest = states(b)
+    monkeypatch.setenv("LBC_FAULT", "wait:16")
+    with pytest.raises(lbc.LbcError) as e:
+        b.run_to_steady(1e-10, 5)
+    assert e.value.status == lbc.ETIMEOUT
+    monkeypatch.delenv("LBC_FAULT")
+    b.set_states(rest)
+    b.step(4)
+    ref = lbc.Batch(ps)
+    ref.step(4)
+    for x, y in zip(states(b), states(ref)):
+        assert np.array_equal(x, y)
+    b.close()
+    ref.close()
+
+
+def test_persistent_uneven_batch_sampled():
+    """The 512-solve uneven batch through the persistent form: every instance finite, a
+    seeded sample (the smallest, the largest and three more) against the oracle (1e-5)."""
+    ps = workloads.c4()
+    b = lbc.Batch(ps)
+    b.set_persistent(True)
+    sizes = [p["Nx"] * 2 * p["Qx"] * p["Qy"] for p in ps]
+    rng = np.random.default_rng(45)
+    sample = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), *rng.choice(len(ps), 3, replace=False).tolist()})
+    b.step(2)
+    for i in range(len(ps)):
+        assert np.all(np.isfinite(b.moments(i))), i
+    for i in sample:
+        o = Oracle(ps[i])
+        o.run(2)
+        e = moment_errors(b.moments(i), o.moments())
+        assert np.all(e < 1e-5), (i, dict(zip(lbc.MOMENT_NAMES, e)))
+    b.close()
