@@ -2,7 +2,7 @@
 """Benchmark: cell-velocity updates per second of the half-range LB Couette
 time step on the single-large-solve workload (Nx = 2048 stretched nodes,
 2Qx x Qy = 32 x 20 velocities, delta in {0.1, 1, 10, 100}: four solves per
-step, FP32 state with FP64 moment sums), one JSON line on stdout.
+step, FP32 state with compensated moment sums), one JSON line on stdout.
 
 A step is one TVD RK-3 step (three fused stage launches) of all four solves.
 Timing: W untimed warm-up steps, then K steps timed with CUDA events on the
@@ -183,14 +183,15 @@ def cpu_baseline(seconds_target=8.0):
                                                                "rest start to r < 1e-10"}}
 
 
-def steady_leg(n=64, fp64_sample=8, residual=1e-11, seed=5):
-    """Steady solves/s: n small Couette solves (the serving workload's draw) as one batch
-    with the compensated FP32 state, run to the residual (1e-11: these solves contract by
-    ~0.1 % per step, so a run stopped at r = 1e-8 is still ~1e-3 from its limit), against
-    the plain form, FP64 single
-    solves one after the other, on the first fp64_sample of them; both with local
-    pseudo-time steps. Each arm's moments are compared with the limit: an FP64 batch of the
-    same solves run to r < 1e-12 (not timed). Completion time of a batched solve = batch
+def steady_leg(n=64, fp64_sample=8, residual=1e-10, fp32_cap=100_000, seed=5):
+    """Steady solves/s at equal moment error: n small Couette solves (the serving workload's
+    draw) as one batch with the compensated FP32 state, against the plain form, FP64 single
+    solves one after the other, on the first fp64_sample of them; both with local pseudo-time
+    steps. Each arm's moments are compared with the limit (an FP64 batch of the same solves run
+    to r < 1e-12, not timed). These solves contract by ~0.1 % per step, so the FP64 arm needs
+    r < 1e-10 to come within 1e-5 of the limit; the FP32 evaluation of the right-hand side keeps
+    the FP32 residual above ~1e-9, so the FP32 arm stops at r < 1e-10 or after fp32_cap steps,
+    and its error against the limit is the measure. Completion time of a batched solve = batch
     time x its steps / the most steps (p50/p99 over the n)."""
     import numpy as np
     import torch
@@ -204,7 +205,7 @@ def steady_leg(n=64, fp64_sample=8, residual=1e-11, seed=5):
     b = lbc.Batch([dict(r, precision="fp32", compensated=1) for r in reqs], cluster=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ks, _ = b.run_to_steady(residual, 200_000, raise_notconv=False)
+    ks, _ = b.run_to_steady(residual, fp32_cap, raise_notconv=False)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     done = tb * np.asarray(ks, dtype=float) / max(ks)
@@ -216,13 +217,14 @@ def steady_leg(n=64, fp64_sample=8, residual=1e-11, seed=5):
         s = lbc.Solver(dict(reqs[i], precision="fp64"))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.run_to_steady(residual, 200_000)
+        s.run_to_steady(residual, 400_000)
         t64 += time.perf_counter() - t0
         err64 = max(err64, serve.moment_error(s.moments(), limit[i]))
         s.close()
     return {"metric": "steady solves/s", "batched_fp32": n / tb, "plain_fp64": fp64_sample / t64,
             "p50_s": float(np.percentile(done, 50)), "p99_s": float(np.percentile(done, 99)),
             "moment_error_batched_fp32": err32, "moment_error_plain_fp64": err64, "residual": residual,
+            "fp32_steps_cap": fp32_cap, "fp32_at_cap": int(sum(k >= fp32_cap for k in ks)),
             "reference": "each solve's FP64 steady state to r < 1e-12 (max over moments of the normalised error)",
             "workload": f"{n} small Couette solves (Nx 32-160, Qx, Qy 4-8, delta 0.3-3; seed {seed}), local steps; "
                         f"batched arm: compensated FP32 state; plain FP64 timed on {fp64_sample} of them"}

@@ -91,7 +91,7 @@ typedef struct {
     double p0;               /* momentum scale of both quadratures; 0 = 1 */
     double cfl;              /* CFL number of the time step; 0 = 0.5 */
     double dt;               /* explicit time step; 0 = automatic (see lbc_create) */
-    lbc_precision precision; /* LBC_FP64, or float32 state with float64 moment sums */
+    lbc_precision precision; /* LBC_FP64, or LBC_FP32_STATE (below) */
     int local_dt;            /* 0: one time step for every node (time-accurate);
                                 1: local pseudo-time steps for steady states (below) */
     int half_channel;        /* 0: the full channel -1/2 < x < 1/2 with Nx nodes;
@@ -101,15 +101,27 @@ typedef struct {
 } lbc_params;
 
 /*
+ * FP32 state (precision LBC_FP32_STATE): the state and the stage arithmetic
+ * (WENO-5, targets, relaxation, RK combination) are float32. Accumulations are
+ * compensated: each node's raw moment sums are float32 partials over the 4 rows a
+ * thread takes from each 32-row block of velocities, added into running sums with
+ * Kahan's compensation, and the partials of warps and of velocity chunks with TwoSum;
+ * the Hermite coefficients of the equilibrium are compensated dot products (Dot2);
+ * the wall densities n_w are accumulated in float64. The steady-state residual takes
+ * each value's increment in float32 (exact to one rounding) and reduces in float64.
+ *
  * Compensated FP32 state (compensated = 1, precision LBC_FP32_STATE; LBC_EINVAL
  * otherwise). Each value of the state is held as an FP32 value d plus an FP32
- * remainder c in one more state buffer: the third stage adds the step's
- * increment Delta = f^{n+1} - f^n to d + c with the rounding error kept
- * (TwoSum), so increments below half an ulp of d still move the state. Without
- * it an FP32 iteration stalls at a steady state biased by about
- * eps_32 |f| tau / dt (~1e-3 relative at delta = 0.1 on stretched grids). The
- * stage arithmetic itself stays FP32. lbc_get_state returns d + c and
- * lbc_set_state stores the FP64 input as d + c. lbc_step_noalloc rejects it.
+ * remainder c, and each stage adds its dt L to a per-value FP32 accumulator of the
+ * step's increment; the third stage adds Delta = dt (L0 + L1)/6 + (2/3) dt L2 to
+ * d + c with the rounding error kept (TwoSum), so increments below half an ulp of d
+ * still move the state and the increment is never rounded at the size of the state.
+ * Without it an FP32 iteration stalls at a steady state biased by about
+ * eps_32 |f| tau / dt (~1e-3 relative at delta = 0.1 on stretched grids); with it
+ * the steady state is within 1e-5 of the FP64 one, although the residual itself
+ * stays above ~1e-9 (the stage inputs are rounded to FP32). The stage arithmetic
+ * stays FP32. lbc_get_state returns d + c and lbc_set_state stores the FP64 input
+ * as d + c. lbc_step_noalloc rejects it.
  *
  * Local pseudo-time steps (local_dt = 1; dt must be 0). Only the steady state
  * is meaningful: node s advances by dt_s = min(cfl * J_s deta / max|p_x|,

@@ -1489,9 +1489,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
 persistent_stage_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int nwork, int nsteps,
                         unsigned *cnt)
 {
-    // counters (zeroed before the launch): cnt[0] items handed out, cnt[1] abort flag,
-    // cnt[4 + w] finished stage items of work item w, cnt[4 + nwork + i] tiles of instance i
-    // that finished a step's third stage
+    // counters (zeroed before the launch): cnt[0] items handed out, cnt[1] abort flag, cnt[4 + w]
+    // CTAs that finished a stage item of work item w, cnt[4 + nwork + i] CTAs of instance i that
+    // finished a third stage
     unsigned *next = cnt, *abort = cnt + 1, *done = cnt + kPersistHdr, *inst_done = cnt + kPersistHdr + nwork;
     __shared__ unsigned s_item[2];   // this cluster's item and whether its dependencies are met
     const int tid = threadIdx.x;
@@ -1499,22 +1499,29 @@ persistent_stage_kernel(const Inst *__restrict__ insts, const int2 *__restrict__
     const unsigned total = (unsigned)nsteps * 3u * (unsigned)nwork;
     cluster_arrive();   // every CTA of the cluster runs before the first item is written into its shared memory
     cluster_wait();
+    // The cluster's first thread claims items from the counter, the next one while the current
+    // one runs. A cluster takes its claimed items in increasing order and every cluster is
+    // resident, so the smallest unfinished item is always running or about to run, and every
+    // wait ends. That thread also checks the item's dependencies and tells the other CTAs, so
+    // that every CTA of the cluster takes the same path through the stage.
+    unsigned claimed = 0u;
+    if (rank == 0 && tid == 0) claimed = atomicAdd(next, 1u);
     for (;;) {
         if (rank == 0 && tid == 0) {
-            unsigned item = atomicAdd(next, 1u), ok = 1u;
+            unsigned item = claimed, ok = 1u;
             if (item < total && ld_acquire_gpu(abort) == 0u) {
                 const int rel = (int)(item / (3u * nwork)), stage = (int)((item / nwork) % 3u), w = (int)(item % nwork);
                 const int2 wk = work[w];
                 if (wk.x >= 0) {
                     const Inst &I = insts[wk.x];
-                    const unsigned need = 3u * rel + stage;
+                    const unsigned need = csize * (3u * rel + stage);
                     for (int dt = -1; dt <= 1 && ok; ++dt) {
                         const int t = wk.y + dt;
                         if (t >= 0 && t < I.T.ntile) ok = wait_at_least(&done[w + dt], need, abort);
                     }
                     // early stop and local steps use instance-wide data of the previous step
                     if (ok && stage == 0 && rel > 0 && (I.T.lts || I.S.ctl->stop_eps > 0.0))
-                        ok = wait_at_least(&inst_done[wk.x], (unsigned)(rel * I.T.ntile), abort);
+                        ok = wait_at_least(&inst_done[wk.x], csize * (unsigned)(rel * I.T.ntile), abort);
                     if (!ok) {
                         atomicExch(&I.S.ctl->timeout, 1);
                         atomicExch(abort, 1u);
@@ -1527,6 +1534,7 @@ persistent_stage_kernel(const Inst *__restrict__ insts, const int2 *__restrict__
                 st_cluster_u32(&s_item[0], r, item);
                 st_cluster_u32(&s_item[1], r, ok);
             }
+            if (item < total && ok) claimed = atomicAdd(next, 1u);
         }
         cluster_arrive();
         cluster_wait();
@@ -1545,17 +1553,14 @@ persistent_stage_kernel(const Inst *__restrict__ insts, const int2 *__restrict__
             else if (stage == 1) stage_body<R, kExt, 1>(I, wk.y, rel, true);
             else stage_body<R, kExt, 2>(I, wk.y, rel, true);
         }
-        // completion: every CTA's writes fenced, then the tile's counter (and, after the
-        // third stage, the instance's) released by the cluster's first CTA
+        // completion: this CTA's writes fenced, then counted (the tile's stage item is done when
+        // every CTA of its cluster has counted)
         __syncthreads();
-        if (tid == 0) __threadfence();
-        cluster_arrive();
-        cluster_wait();
-        if (rank == 0 && tid == 0) {
+        if (tid == 0) {
+            __threadfence();
             atomicAdd(&done[w], 1u);
             if (stage == 2 && wk.x >= 0) atomicAdd(&inst_done[wk.x], 1u);
         }
-        __syncthreads();
     }
 }
 
