@@ -217,14 +217,16 @@ __device__ __forceinline__ f2 min2(f2 a, f2 b)
 }
 
 // WENO-5 (Jiang & Shu) on a packed pair, face between c and d, upwind cell c.
-// The nonlinear weights d_k / (eps + beta_k)^2 in a form that FP32 holds: with
-// e_k = eps + beta_k scaled by 1/max e_m, as d_k prod_{m != k} e_m^2 over their
-// sum (two reciprocals per pair); where a warp meets e_m >= 1e12 (weight-divided
-// tails of hot-wall populations reach 1e10), whose squares would leave the FP32
-// range, as d_k (min e_m / e_k)^2 (the smoothest stencil keeps weight d_k).
+// The nonlinear weights d_k / (eps + beta_k)^2, normalised, written as
+// d_k (min_m e_m / e_k)^2 with e_k = eps + beta_k: the same weights in exact
+// arithmetic, and in FP32 range for any e_k (weight-divided tails of hot-wall
+// populations reach 1e10, so e_k reaches ~1e20 and e_k^2 would overflow): every
+// ratio is at most 1, the smoothest stencil's is exactly 1, so the normaliser is
+// at least min d_k = 0.1, and ratios that underflow belong to weights below FP32
+// resolution.
 __device__ __forceinline__ f2 weno5_2(f2 a, f2 b, f2 c, f2 d, f2 e)
 {
-    const f2 two = bc2(2.f), three = bc2(3.f), four = bc2(4.f), five = bc2(5.f);
+    const f2 two = bc2(2.f), three = bc2(3.f), five = bc2(5.f);
     const f2 q0 = fma2(bc2(11.f), c, fma2(bc2(-7.f), b, two * a));
     const f2 q1 = fma2(two, d, fma2(five, c, bc2(0.f) - b));
     const f2 q2 = fma2(five, d, two * c) - e;
@@ -232,33 +234,15 @@ __device__ __forceinline__ f2 weno5_2(f2 a, f2 b, f2 c, f2 d, f2 e)
     const f2 t2 = fma2(bc2(-2.f), c, b + d), t3 = b - d;
     const f2 t4 = fma2(bc2(-2.f), d, c + e), t5 = fma2(bc2(-4.f), d, fma2(three, c, e));
     const f2 k1312 = bc2(13.f / 12.f), k025 = bc2(0.25f), eps = bc2(1e-6f);
-    f2 e0 = fma2(k1312, t0 * t0, fma2(k025, t1 * t1, eps));
-    f2 e1 = fma2(k1312, t2 * t2, fma2(k025, t3 * t3, eps));
-    f2 e2 = fma2(k1312, t4 * t4, fma2(k025, t5 * t5, eps));
-    f2 a0, a1, a2;
-    const f2 mx = max2(e0, max2(e1, e2));
-    float ml, mh;
-    un2(mx, ml, mh);
-    if (__all_sync(0xffffffffu, fmaxf(ml, mh) < 1e12f)) {
-        const f2 s = rcp2(mx);
-        e0 = e0 * s;
-        e1 = e1 * s;
-        e2 = e2 * s;
-        e0 = e0 * e0;
-        e1 = e1 * e1;
-        e2 = e2 * e2;
-        a0 = bc2(0.1f) * (e1 * e2);
-        a1 = bc2(0.6f) * (e0 * e2);
-        a2 = bc2(0.3f) * (e0 * e1);
-    } else {
-        const f2 mn = min2(e0, min2(e1, e2));
-        const f2 r0 = mn * rcp2(e0), r1 = mn * rcp2(e1), r2 = mn * rcp2(e2);
-        a0 = bc2(0.1f) * (r0 * r0);
-        a1 = bc2(0.6f) * (r1 * r1);
-        a2 = bc2(0.3f) * (r2 * r2);
-    }
-    const f2 num = fma2(a0, q0, fma2(a1, q1, a2 * q2));
-    const f2 den = bc2(6.f) * (a0 + a1 + a2);
+    const f2 e0 = fma2(k1312, t0 * t0, fma2(k025, t1 * t1, eps));
+    const f2 e1 = fma2(k1312, t2 * t2, fma2(k025, t3 * t3, eps));
+    const f2 e2 = fma2(k1312, t4 * t4, fma2(k025, t5 * t5, eps));
+    const f2 mn = min2(e0, min2(e1, e2));
+    const f2 r0 = mn * rcp2(e0), r1 = mn * rcp2(e1), r2 = mn * rcp2(e2);
+    const f2 s0 = r0 * r0, s1 = r1 * r1, s2 = r2 * r2;
+    // sum_k d_k s_k q_k / (6 sum_k d_k s_k), d = (0.1, 0.6, 0.3)
+    const f2 num = fma2(bc2(0.1f) * s0, q0, fma2(bc2(0.6f) * s1, q1, bc2(0.3f) * s2 * q2));
+    const f2 den = fma2(bc2(0.6f), s0, fma2(bc2(3.6f), s1, bc2(1.8f) * s2));
     return num * rcp2(den);
 }
 
