@@ -28,7 +28,8 @@
  * Errors: every call returns an lbc_status; nothing throws across the ABI.
  * lbc_last_error() gives a thread-local message for the last failure. A failed
  * call leaves the solver unchanged, except LBC_ENONFINITE (the state held a
- * NaN or Inf), after which the solver refuses further steps.
+ * NaN or Inf), LBC_ETIMEOUT and LBC_EBOUNDS, after which the solver refuses
+ * further steps until a state is installed.
  *
  * Threads and streams: a solver may be used from one host thread at a time.
  * All device work is enqueued on the CUDA stream given at creation; calls
@@ -56,7 +57,8 @@ typedef enum {
     LBC_ECUDA = 3,       /* a CUDA runtime call failed */
     LBC_ENOTCONV = 4,    /* lbc_run_to_steady hit max_steps */
     LBC_ENONFINITE = 5,  /* NaN/Inf in the state; the solver is poisoned */
-    LBC_ETIMEOUT = 6     /* a bounded device wait gave up */
+    LBC_ETIMEOUT = 6,    /* a bounded device wait gave up */
+    LBC_EBOUNDS = 7      /* range-checked build only: a device index check failed (message names it) */
 } lbc_status;
 
 typedef enum { LBC_MU_POWER = 0, LBC_MU_TABLE = 1 } lbc_mu_law;
@@ -370,6 +372,20 @@ lbc_status lbc_step_noalloc(const lbc_params *params, double *d_state, long nste
  * Uses the current device; changes no device setting. Errors: LBC_EINVAL, LBC_ECUDA.
  */
 lbc_status lbc_measure_fp64_peak(double *tflops);
+
+/*
+ * Build variant (no counterpart in the paper): 1 if this library is the
+ * range-checked build (liblbc_checked.so, kernels compiled with LBC_CHECKED),
+ * else 0. In that build the stage, equilibrium and persistent kernels check
+ * their computed indices (TMA box alignment, bulk-copy extents, stencil and
+ * ghost columns, factor-table indices, state stores, symmetry partners,
+ * cluster exchange slots, persistent work neighbours) before each access; a
+ * failed check skips the access, records its site in the instance's control
+ * block, and the next call that reads the control blocks returns LBC_EBOUNDS
+ * naming the site; stepping is then refused until a state is installed.
+ * Never fails.
+ */
+int lbc_checked_build(void);
 
 #ifdef __cplusplus
 }

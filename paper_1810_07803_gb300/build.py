@@ -3,6 +3,11 @@
 Translation units compile in parallel, then link into one shared library next
 to this file. Host code uses no machine-specific flags, so the same command
 builds on x86_64 and aarch64 hosts.
+
+build(checked=True) makes the range-checked variant liblbc_checked.so: the
+kernels' translation unit compiled with LBC_CHECKED (every computed index
+checked before its access; a failed check skips the access and is reported as
+LBC_EBOUNDS), linked with the other objects of the normal build.
 """
 from __future__ import annotations
 
@@ -16,6 +21,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbc.so")
+LIB_CHECKED = os.path.join(HERE, "liblbc_checked.so")
+CHECKED_TU = "lbc_kernels.cu"   # the translation unit that holds the range checks
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["lbc_api.cu", "lbc_setup.cu", "lbc_pool.cu", "lbc_kernels.cu", "lbc_host.cpp", "lbc_noalloc.cu",
            "lbc_peak.cu"]
@@ -30,35 +37,56 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblbc.so")
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "lbc.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def _compile(cc: str, src: str, obj: str, extra: list[str], verbose: bool) -> str:
+    cmd = [cc, *FLAGS, *extra, *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.check_call(cmd)
+    return obj
+
+
+def _link(cc: str, lib: str, objs: list[str]) -> None:
+    tmp = lib + f".tmp{os.getpid()}"
+    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs])
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    if checked:
+        return build_checked(force, verbose)
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-
-    def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src + ".o")
-        cmd = [cc, *FLAGS, *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
-        if verbose:
-            print(" ".join(cmd))
-        subprocess.check_call(cmd)
-        return obj
-
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+        objs = list(ex.map(lambda f: _compile(cc, f, os.path.join(BUILD, f + ".o"), [], verbose), SOURCES))
+    _link(cc, LIB, objs)
     return LIB
 
 
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """liblbc_checked.so: the normal build's objects with the kernels recompiled under LBC_CHECKED."""
+    build(force, verbose)
+    if any(not os.path.exists(os.path.join(BUILD, f + ".o")) for f in SOURCES if f != CHECKED_TU):
+        build(True, verbose)   # the library exists but its objects do not
+    if not force and not _stale(LIB_CHECKED):
+        return LIB_CHECKED
+    cc = nvcc()
+    ck = _compile(cc, CHECKED_TU, os.path.join(BUILD, CHECKED_TU + ".checked.o"), ["-DLBC_CHECKED"], verbose)
+    objs = [ck if f == CHECKED_TU else os.path.join(BUILD, f + ".o") for f in SOURCES]
+    _link(cc, LIB_CHECKED, objs)
+    return LIB_CHECKED
+
+
 if __name__ == "__main__":
-    print(build(force=True, verbose=True))
+    import sys
+
+    print(build(force=True, verbose=True, checked="--checked" in sys.argv[1:]))

@@ -61,6 +61,7 @@ struct lbc_batch {
     bool steady_mode = false;     // the device control blocks hold run-to-steady settings
     bool poisoned = false;        // some instance holds a NaN/Inf
     bool timed_out = false;       // a bounded device wait gave up: stepping is refused until set_state
+    int bounds_site = 0;          // range-checked build: a device index check failed (refused the same way)
     cudaGraphExec_t graph = nullptr;
     bool ext = false;             // some instance uses the half channel or local steps
     bool persistent = false;      // steps run as the persistent form (one launch per group of steps)
@@ -132,6 +133,9 @@ lbc_status ensure_graph(lbc_batch *b)
 
 lbc_status run_steps(lbc_batch *b, long nsteps)
 {
+    if (b->bounds_site)
+        return fail(LBC_EBOUNDS, std::string("a device index check failed earlier (") + check_site_name(b->bounds_site) +
+                                     "); set a state to continue");
     if (b->timed_out) return fail(LBC_ETIMEOUT, "a bounded device wait gave up earlier; set a state to continue");
     if (fault_injected("launch")) return fail(LBC_ECUDA, "stage launch: injected failure (LBC_FAULT=launch)");
     while (nsteps >= kGraphSteps) {
@@ -147,8 +151,11 @@ lbc_status run_steps(lbc_batch *b, long nsteps)
 
 lbc_status upload_ctl(lbc_batch *b, int first, int count)
 {
-    const int probe = fault_wait_polls();
-    for (int k = first; k < first + count; ++k) b->h_ctl[k].probe = probe;
+    const int probe = fault_wait_polls(), site = fault_bounds_site();
+    for (int k = first; k < first + count; ++k) {
+        b->h_ctl[k].probe = probe;
+        if (site) b->h_ctl[k].bounds = site;
+    }
     LBC_CUDA_TRY(cudaMemcpyAsync(b->d_ctl + first, b->h_ctl + first, count * sizeof(Ctl), cudaMemcpyHostToDevice,
                                  b->stream));
     return LBC_OK;
@@ -161,6 +168,11 @@ lbc_status read_ctl(lbc_batch *b)
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     bool any = false;
     for (int i = 0; i < b->n; ++i) {
+        if (b->h_ctl[i].bounds) {
+            b->bounds_site = b->h_ctl[i].bounds;
+            return fail(LBC_EBOUNDS, "instance " + std::to_string(i) + ": device index check failed: " +
+                                         check_site_name(b->bounds_site));
+        }
         if (b->h_ctl[i].timeout) {
             b->timed_out = true;
             return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
@@ -455,11 +467,17 @@ lbc_status batch_get_state(lbc_batch *b, int i, double *state)
     LBC_CUDA_TRY(cudaMemcpyAsync(state, b->d_io, bytes, cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaMemcpyAsync(b->h_ctl, b->d_ctl, b->n * sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
-    for (int k = 0; k < b->n; ++k)
+    for (int k = 0; k < b->n; ++k) {
+        if (b->h_ctl[k].bounds) {
+            b->bounds_site = b->h_ctl[k].bounds;
+            return fail(LBC_EBOUNDS, "instance " + std::to_string(k) + ": device index check failed: " +
+                                         check_site_name(b->bounds_site));
+        }
         if (b->h_ctl[k].timeout) {
             b->timed_out = true;
             return fail(LBC_ETIMEOUT, "a bounded device wait gave up");
         }
+    }
     return LBC_OK;
 }
 
@@ -486,10 +504,13 @@ lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
     // control blocks: keep the others' flags, clear this instance's
     b->h_ctl[i].nonfinite = 0;
     b->h_ctl[i].timeout = 0;
+    b->h_ctl[i].bounds = 0;
     bool any = false, late = false;
+    int site = 0;
     for (int k = 0; k < b->n; ++k) {
         any = any || b->h_ctl[k].nonfinite;
         late = late || b->h_ctl[k].timeout;
+        if (!site) site = b->h_ctl[k].bounds;
     }
     const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
     LBC_CUDA_TRY(cudaMemcpyAsync(I.S.F[0], I.S.F[1], 2 * (size_t)I.T.V * I.T.Nxp * esz, cudaMemcpyDeviceToDevice,
@@ -503,6 +524,7 @@ lbc_status batch_set_state(lbc_batch *b, int i, const double *state)
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     b->poisoned = any;
     b->timed_out = late;
+    b->bounds_site = site;
     return LBC_OK;
 }
 
@@ -576,6 +598,7 @@ lbc_status upload_states(lbc_batch *b, const double *const *states)
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     if (*b->h_bad) return fail(LBC_EINVAL, "a state holds a NaN or Inf; no instance changed");
     bool any = false, late = false;
+    int site = 0;
     const size_t esz = b->fp32 ? sizeof(float) : sizeof(double);
     for (int i = 0; i < b->n; ++i) {
         if (states[i]) {
@@ -583,6 +606,7 @@ lbc_status upload_states(lbc_batch *b, const double *const *states)
             const size_t bytes = 2 * (size_t)I.T.V * I.T.Nxp * esz;
             b->h_ctl[i].nonfinite = 0;
             b->h_ctl[i].timeout = 0;
+            b->h_ctl[i].bounds = 0;
             LBC_CUDA_TRY(cudaMemcpyAsync(I.S.F[0], I.S.F[1], bytes, cudaMemcpyDeviceToDevice, b->stream));
             if (I.S.C) LBC_CUDA_TRY(cudaMemcpyAsync(I.S.C, I.S.F[2], bytes, cudaMemcpyDeviceToDevice, b->stream));
             if (I.T.lts) {
@@ -596,12 +620,14 @@ lbc_status upload_states(lbc_batch *b, const double *const *states)
         }
         any = any || b->h_ctl[i].nonfinite;
         late = late || b->h_ctl[i].timeout;
+        if (!site) site = b->h_ctl[i].bounds;
     }
     st = upload_ctl(b, 0, b->n);
     if (st != LBC_OK) return st;
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));
     b->poisoned = any;
     b->timed_out = late;
+    b->bounds_site = site;
     return LBC_OK;
 }
 

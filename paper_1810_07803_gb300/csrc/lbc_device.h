@@ -127,7 +127,34 @@ struct Ctl {
     int probe;             // test hook (LBC_FAULT=wait:N): > 0 makes every stage CTA wait at most this
                            // many polls on an mbarrier that nothing arrives at, so the bounded-wait
                            // path runs and reports; 0 in normal use
+    int bounds;            // range-checked build (LBC_CHECKED): the first failed index check's site
+    int pad;
 };
+
+// Range check of a computed index in the range-checked build (-DLBC_CHECKED): a failed check
+// records its site in the instance's control block and the access is skipped (no trap, no
+// fault); the host reports it. In the normal build the check is compiled away.
+enum CheckSite : int {
+    CK_NONE = 0,
+    CK_TMA_X,      // a TMA box's x coordinate off its 16-byte boundary
+    CK_BULK,       // a bulk copy outside its shared-memory region or its source array
+    CK_STENCIL,    // a stencil, ghost-node or RK-base column outside the staged row box
+    CK_GTAB,       // an equilibrium factor index outside the tile's factor table
+    CK_STORE,      // a state (or compensation) store outside [0, V) x [0, Nxp)
+    CK_MIRROR,     // a symmetry-plane partner row outside the state
+    CK_XCH,        // a cluster exchange slot outside the receiving CTA's region
+    CK_EQ,         // a node-stage write outside the stage data or the scratch capacity
+    CK_WORK,       // a persistent item's neighbour outside the work list or of another instance
+    CK_COUNT
+};
+const char *check_site_name(int site);   // host: the site's description
+bool checked_build();                     // host: whether the kernels carry the range checks
+
+#ifdef LBC_CHECKED
+#define LBC_CHECK(ctl, cond, site) ((cond) ? true : (atomicCAS(&(ctl)->bounds, 0, (site)), false))
+#else
+#define LBC_CHECK(ctl, cond, site) true
+#endif
 
 // Mutable device state; arrays marked (R) hold the state precision.
 struct DevState {
@@ -196,9 +223,12 @@ lbc_status fail(lbc_status st, const std::string &msg);
 // use, so a test can set and clear it): "alloc" (device allocations of create and pool
 // admission report failure without allocating), "launch" (stepping calls report a failed
 // stage launch without launching), "admit" (pool admission reports no room), "wait:N" (the
-// control blocks uploaded carry probe = N, see Ctl). Nothing here touches the device.
+// control blocks uploaded carry probe = N, see Ctl), "bounds:S" (the control blocks uploaded
+// carry the failed-check site S, as if a range check of the checked build had failed). Nothing
+// here touches the device.
 bool fault_injected(const char *kind);
 int fault_wait_polls();
+int fault_bounds_site();
 const char *last_error();
 // Validates p (defaults already applied) and resolves the expansion orders.
 lbc_status validate(const lbc_params &p, int &Nxe, int &Nye);

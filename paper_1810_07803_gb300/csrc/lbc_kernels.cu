@@ -195,6 +195,9 @@ __device__ __forceinline__ f2 max2(f2 a, f2 b)
     return mk2(fmaxf(al, bl), fmaxf(ah, bh));
 }
 
+// Brings the line of a global address into this SM's L1 (no data returned).
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.L1 [%0];" ::"l"(p)); }
+
 // One (phi, chi) pair of an interleaved row: a single 64-bit access.
 __device__ __forceinline__ f2 ld2(const float *p)
 {
@@ -475,6 +478,7 @@ __device__ __forceinline__ void project_coefficients(R sT, R a, R a2, int K, int
     }
     for (int lb = 0; lb <= N; lb += kEqLB) {
         const int le = min(N, lb + kEqLB - 1);
+#pragma unroll 4
         for (int l = lb; l <= le; ++l) {
             const R al = alpha[l], sb = sbeta[l], isb1 = isbeta[l + 1];
 #pragma unroll
@@ -490,7 +494,7 @@ __device__ __forceinline__ void project_coefficients(R sT, R a, R a2, int K, int
         if (lb + lo <= le) {
             const R *r = rp + sgn * K, *hh = Hw + lo * kpad;
             Dot<R> d;
-#pragma unroll 2
+#pragma unroll 4
             for (int k = 0; k < K; ++k) d.add(r[k], hh[k]);
             cw[sgn * (N + 1) + lb + lo] = d.value();
         }
@@ -508,9 +512,10 @@ __device__ __forceinline__ void project_coefficients(R sT, R a, R a2, int K, int
 // columns of the tile's eqg[buf] block; dm_a, dm_b (either may be NULL) receive
 // each node's mass deviation J_s deta (n_s - 1) (local steps, buffer 0).
 // Organised for instruction count and latency: a thread per node for the
-// moments and the g_y coefficients, then a warp per node for the rest (lanes
-// over projection nodes, then over (sign, order), then over factors), with
-// warp-level synchronisation only and the tables in shared memory.
+// moments and the g_y coefficients; the g_y factors over all threads, one
+// (node, j) each; then a warp per node for the projection and the g_x factors
+// (lanes over projection nodes, then over (sign, order), then over factors),
+// with warp-level synchronisation only and the tables in shared memory.
 template <typename R>
 __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf, int tile, int cfirst, int cstep,
                                  int nn, int ncap, unsigned char *scratch, double *dm_a, double *dm_b)
@@ -526,11 +531,20 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
     R *bb = reinterpret_cast<R *>(scratch + L.bb);      // [nn][Ny+1]   Hermite coefficients of g_y
     R *eqm = static_cast<R *>(S.eqm[buf]);
     R *eqg = static_cast<R *>(S.eqg[buf]) + (size_t)tile * G * kLanes;
+#ifdef LBC_CHECKED
+    if (!LBC_CHECK(S.ctl, nn <= ncap && tile >= 0 && tile < T.ntile, CK_EQ)) return;   // uniform over the CTA
+#endif
 
     // ---- moments, relaxation data, per-node scalars and the g_y coefficients (thread per node) ----
     if (tid < nn) {
         const int c = cfirst + tid * cstep, s = c0 + c;
         const bool live = s < T.Nx;
+        // per-node and per-instance data from global memory, loaded first so that their latency
+        // overlaps the moment arithmetic
+        const R ijd_s = live ? Tabs<R>::ijd(T)[s] : R(0), dtn_s = live ? Tabs<R>::dtn(T)[s] : R(0);
+        const double jd_s = live && (dm_a || dm_b) ? T.jdeta[s] : 0.0;
+        const R scNU = Tabs<R>::sc(T, SC_NU), ip0 = Tabs<R>::sc(T, SC_IP0);
+        const R scEXPO = Tabs<R>::sc(T, SC_EXPO), sc1MPR = Tabs<R>::sc(T, SC_1MPR);
         R m[10];
         if (live) {
             const R sx = shf[c], sy = shf[kLanes + c];
@@ -540,7 +554,7 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             for (int k = 0; k < kNumRaw; ++k) rr[k] += raw[tid * kNumRaw + k];
             raw_to_moments_r<R>(rr, sx, sy, m);
             if (dm_a || dm_b) {   // the deviation's own S0 is n_s - 1 (the rest state has n = 1)
-                const double dm = T.jdeta[s] * (double)raw[tid * kNumRaw + R_S0];
+                const double dm = jd_s * (double)raw[tid * kNumRaw + R_S0];
                 if (dm_a) dm_a[s] = dm;
                 if (dm_b) dm_b[s] = dm;
             }
@@ -565,19 +579,19 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             }
             const int cg = min(max(lo - 1, 0), T.tab_n - 2);
             const R mu = tab[E.lawMu + cg] * pow(Tc / lT[cg], tab[E.lawW + cg]);   // mu(T) / mu(T_ref)
-            nu = n * Tc / mu * Tabs<R>::sc(T, SC_NU);
+            nu = n * Tc / mu * scNU;
             cS = (R(1) - tab[E.lawPr + max(lo - 1, 0)]) / (n * Tc * Tc);
         } else {
-            nu = n * Tabs<R>::sc(T, SC_NU) * pow(Tc, Tabs<R>::sc(T, SC_EXPO));   // mu = T^omega (Eq. mu)
-            cS = Tabs<R>::sc(T, SC_1MPR) / (n * Tc * Tc);
+            nu = n * scNU * pow(Tc, scEXPO);   // mu = T^omega (Eq. mu)
+            cS = sc1MPR / (n * Tc * Tc);
         }
-        if (live) {
+        if (live && LBC_CHECK(S.ctl, s < T.Nxp, CK_EQ)) {
             R *e = eqm + (size_t)s * kEqM;
             e[0] = n; e[1] = ux; e[2] = uy; e[3] = Tc; e[4] = m[8]; e[5] = m[9];
-            e[6] = nu; e[7] = cS; e[8] = R(1) / (R(5) * Tc); e[9] = Tabs<R>::ijd(T)[s];
-            e[10] = m[4]; e[11] = m[5]; e[12] = m[6]; e[13] = m[7]; e[14] = Tabs<R>::dtn(T)[s];
+            e[6] = nu; e[7] = cS; e[8] = R(1) / (R(5) * Tc); e[9] = ijd_s;
+            e[10] = m[4]; e[11] = m[5]; e[12] = m[6]; e[13] = m[7]; e[14] = dtn_s;
         }
-        const R ip0 = Tabs<R>::sc(T, SC_IP0), Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
+        const R Tp = Tc * ip0 * ip0, sT = sqrt(Tp), a = ux * ip0 / sT;
         R *x = sc + tid * 8;
         x[0] = sT; x[1] = a; x[2] = R(0.5) * a * a;
         // g_y coefficients b_l = E[He_l(u' + sqrt(T') Y)] / l!: b_{l+1} = (u' b_l + (T'-1) b_{l-1}) / (l+1)
@@ -587,6 +601,7 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
         R bm = R(1), bl = uq;
         b[0] = R(1);
         b[1] = uq;
+#pragma unroll 4
         for (int l = 1; l < Ny; ++l) {
             const R bn = (uq * bl + tm1 * bm) * invl[l + 1];
             bm = bl;
@@ -596,10 +611,25 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
     }
     __syncthreads();
 
-    // ---- a warp per node: g_x by the stable Gauss-sum projection, then the factors ----
+    // factors: g_x/w at (node, a) = sum_l h_l(z_a) c_l^{sign a}, g_y/w at (node, j) = sum_l He_l(y_j) b_l.
+    // Evaluating the truncated expansions at the nodes is a plain FMA chain: where its terms
+    // cancel (the far tails of hot or cold Maxwellians) the factor's absolute error stays far
+    // below what the quadrature weight of that velocity lets reach any moment.
+    // ---- the g_y factors need only the b_l: every thread takes (node, j) pairs ----
+    const R *hz = tab + E.hz, *He = tab + E.He;
+    for (int idx = tid; idx < nn * Qy; idx += kThreads) {
+        const int jj = idx / nn, i = idx - jj * nn;   // consecutive threads: consecutive nodes
+        const R *b = bb + i * (Ny + 1);
+        R acc = R(0);
+#pragma unroll 4
+        for (int l = 0; l <= Ny; ++l) acc = fma(He[l * Qy + jj], b[l], acc);
+        if (LBC_CHECK(S.ctl, cfirst + i * cstep < kLanes, CK_EQ))
+            eqg[(size_t)(2 * Qx + jj) * kLanes + cfirst + i * cstep] = acc;
+    }
+
+    // ---- a warp per node: g_x by the stable Gauss-sum projection, then its factors ----
     const R *Yk = tab + E.Yk, *Wk = tab + E.Wk;
     const R *alpha = tab + E.alpha, *sbeta = tab + E.sbeta, *isbeta = tab + E.isbeta;
-    const R *hz = tab + E.hz, *He = tab + E.He;
     const R h0 = Tabs<R>::sc(T, SC_H0);
     R *rp = reinterpret_cast<R *>(scratch + L.wk + warp * L.wbytes);   // [2][K] r^+, r^-
     R *cw = rp + 2 * K;                                                // [2][N+1] c^+, c^-
@@ -610,25 +640,14 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
             project_coefficients<R, 1>(x[0], x[1], x[2], K, N, L.kpad, Yk, Wk, alpha, sbeta, isbeta, h0, rp, cw, Hw);
         else
             project_coefficients<R, 2>(x[0], x[1], x[2], K, N, L.kpad, Yk, Wk, alpha, sbeta, isbeta, h0, rp, cw, Hw);
-        // factors: g_x/w at (node, a) = sum_l h_l(z_a) c_l^{sign a}, g_y/w at (node, j) = sum_l He_l(y_j) b_l.
-        // Evaluating the truncated expansions at the nodes is a plain FMA chain: where its terms
-        // cancel (the far tails of hot or cold Maxwellians) the factor's absolute error stays far
-        // below what the quadrature weight of that velocity lets reach any moment.
         R *col = eqg + cfirst + i * cstep;
-        for (int ig = lane; ig < G; ig += 32) {
+        for (int ig = lane; ig < 2 * Qx; ig += 32) {   // g_x factors (sign, a)
+            const int ii = ig < Qx ? ig : ig - Qx;
+            const R *cc = cw + (ig < Qx ? 0 : N + 1);
             R acc = R(0);
-            if (ig < 2 * Qx) {
-                const int ii = ig < Qx ? ig : ig - Qx;
-                const R *cc = cw + (ig < Qx ? 0 : N + 1);
 #pragma unroll 4
-                for (int l = 0; l <= N; ++l) acc = fma(hz[l * Qx + ii], cc[l], acc);
-            } else {
-                const int jj = ig - 2 * Qx;
-                const R *b = bb + i * (Ny + 1);
-#pragma unroll 4
-                for (int l = 0; l <= Ny; ++l) acc = fma(He[l * Qy + jj], b[l], acc);
-            }
-            col[(size_t)ig * kLanes] = acc;
+            for (int l = 0; l <= N; ++l) acc = fma(hz[l * Qx + ii], cc[l], acc);
+            if (LBC_CHECK(S.ctl, cfirst + i * cstep < kLanes, CK_EQ)) col[(size_t)ig * kLanes] = acc;
         }
         __syncwarp();   // the next node reuses this warp's slice
     }
@@ -809,6 +828,25 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     const int ncap = Layout<R>::node_cap(T.nchunk);
     const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, T.tab_n, ncap);
     const uint32_t tab_bytes = (uint32_t)(EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy, T.tab_n).len * sizeof(R));
+#ifdef LBC_CHECKED
+    // the CTA's staged geometry, checked once: TMA boxes on 16-byte boundaries, bulk copies inside
+    // their shared-memory regions and source arrays, stencil and RK-base columns inside the staged
+    // rows, and the cluster exchange inside every CTA's region
+    const bool bad =
+        !LBC_CHECK(ctl, (2 * x0 * (int)sizeof(R)) % 16 == 0 && (2 * xf * (int)sizeof(R)) % 16 == 0, CK_TMA_X) ||
+        !LBC_CHECK(ctl,
+                   tile >= 0 && tile < T.ntile && nloc > 0 && c0 + nloc <= T.Nxp && vend - vbeg <= T.vchunk &&
+                       (size_t)G * kLanes * sizeof(R) <= L.eqm - L.g && (size_t)nloc * kEqM * sizeof(R) % 16 == 0,
+                   CK_BULK) ||
+        !LBC_CHECK(ctl, off >= 0 && kLanes + 4 + off < kRowLen && offf >= 0 && kLanes - 1 + offf < kF0Len,
+                   CK_STENCIL) ||
+        !LBC_CHECK(ctl,
+                   T.nchunk >= 1 && T.nchunk <= kMaxCluster &&
+                       T.nchunk * ((kTile + T.nchunk - 1) / T.nchunk) <= kTile + kMaxCluster,
+                   CK_XCH);
+#else
+    constexpr bool bad = false;
+#endif
 
     // rows v0 .. v0 + kSubV - 1 of the stage input (nodes x0 .. x0 + kRowLen - 1) and of the
     // RK base (nodes xf ..), both fields; rows past V read as zeros
@@ -828,6 +866,13 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     }
     __syncthreads();
     cluster_arrive_relaxed();   // this CTA runs: the others may write into its shared memory after their wait
+    if (bad) {   // range-checked build: give up before any copy, taking part in the cluster barriers
+        cluster_wait();
+        cluster_arrive();
+        cluster_wait();
+        if (persist && tid < kPipe + 2) mbar_inval(&bar[tid]);
+        return;
+    }
     if (tid == 0) {
         for (int sub = 0; sub < min(kPipe, nsub); ++sub) issue(sub);
         // ---- (1) the tile's stage data and the chunk's per-velocity rows, by bulk copies ----
@@ -911,9 +956,9 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     auto mirror_fetch = [&](int sub) {
         if (lane < 3 * NQ && sub < nsub) {
             const int q = lane / 3, g = lane - 3 * q, v = vbeg + sub * kSubV + warp + kWarps * q;
-            if (v < vend) {
-                const int a = v / T.Qy, j = v - a * T.Qy;
-                const int vm = (a < T.Qx ? a + T.Qx : a - T.Qx) * T.Qy + (T.Qy - 1 - j);
+            const int a = v / T.Qy, j = v - a * T.Qy;
+            const int vm = (a < T.Qx ? a + T.Qx : a - T.Qx) * T.Qy + (T.Qy - 1 - j);
+            if (v < vend && LBC_CHECK(ctl, vm >= 0 && vm < T.V && g < T.Nxp, CK_MIRROR)) {
                 const R *src = Fin + 2 * ((size_t)vm * T.Nxp + g);
                 mg0 = __ldcg(src);
                 mg1 = __ldcg(src + 1);
@@ -951,7 +996,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
                 const R *x = s_vrow + kqq * kVRow;
                 const bool pos = x[VR_PX] > R(0);
                 R *row = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen;
-                if (okq && side == 0 && needL) {          // nodes -1 (gi 0), -2 (gi 1)
+                if (okq && side == 0 && needL &&
+                    LBC_CHECK(ctl, -x0 - 2 >= 0 && -x0 + 3 < kRowLen, CK_STENCIL)) {   // nodes -1 (gi 0), -2 (gi 1)
                     R g0, g1;
                     if (pos) {
                         g0 = nwL * x[VR_FWL] - x[VR_FR];
@@ -966,7 +1012,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
                     R *gp = row + 2 * (-1 - gi - x0);
                     gp[0] = g0;
                     gp[1] = g1;
-                } else if (okq && side == 1 && needR) {   // nodes Nx (gi 0), Nx+1 (gi 1)
+                } else if (okq && side == 1 && needR &&
+                           LBC_CHECK(ctl, Nx - 4 - x0 >= 0 && Nx - 1 - x0 < kRowLen, CK_STENCIL)) {   // nodes Nx, Nx+1
                     R g0, g1;
                     if (!pos) {
                         g0 = nwR * x[VR_FWR] - x[VR_FR];
@@ -994,7 +1041,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
 #pragma unroll
                 for (int qq = 1; qq < NQ; ++qq)
                     if (q == qq) okq = ok[qq];
-                if (okq) {
+                if (okq && LBC_CHECK(ctl, -3 - x0 >= 0 && -1 - x0 < kRowLen, CK_STENCIL)) {
                     R *gp = fin + (size_t)(warp + kWarps * q) * 2 * kRowLen + 2 * (-1 - g - x0);   // node -1 - g
                     gp[0] = mg0;
                     gp[1] = mg1;
@@ -1011,80 +1058,111 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
             const float *rowq = fin + (size_t)warp * 2 * kRowLen + 2 * (ck - 3);   // row q = 0, node ck - 3
             const float *b0 = f0 + (size_t)warp * 2 * kF0Len + 2 * (lane + offf);
             const int vlast = min(vs + kSubV, vend) - 1, vhalf = T.Qx * T.Qy;
-            const int side = vlast < vhalf ? 1 : (vs >= vhalf ? -1 : 0);   // every row left / right / mixed
             f2 ps[5];
 #pragma unroll
             for (int m = 0; m < 5; ++m) ps[m] = bc2(0.f);
             float psxy = 0.f;
-            // rows in pairs (q = qp, qp + 1): two WENO chains in flight, fewer live registers
+            // The slot's rows, compiled for where they lie. Rows v < Qx Qy have p_x > 0 and upwind
+            // from the left, the others from the right: a slot whose rows all lie in one half
+            // (kSide 1 or -1, all slots but one per velocity set) takes its stencils at fixed
+            // offsets with no per-row choice; the slot across the halves (kSide 0) chooses per
+            // row. kFull: every row of the slot is inside the chunk (all but a chunk's last slot);
+            // kInner: the tile's stencils reach no wall (all but the channel's end tiles).
+            auto rows = [&](auto side_c, auto full_c, auto inner_c) {
+                constexpr int kSide = decltype(side_c)::value;
+                constexpr bool kFull = decltype(full_c)::value, kInner = decltype(inner_c)::value;
+                // rows in pairs (q = qp, qp + 1): two WENO chains in flight, fewer live registers
 #pragma unroll
-            for (int qp = 0; qp < NQ; qp += 2) {
-                f2 fl[2], dd[2];
+                for (int qp = 0; qp < NQ; qp += 2) {
+                    f2 fl[2], dd[2];
 #pragma unroll
-                for (int qi = 0; qi < 2; ++qi) {
-                    const int q = qp + qi;
-                    const bool pos = side > 0 || (side == 0 && v0 + kWarps * q < vhalf);   // uniform per warp
-                    const float *pp = rowq + (size_t)q * kWarps * 2 * kRowLen + (pos ? 0 : 2);
-                    const f2 a = ld2(pp), b = ld2(pp + 2), c = ld2(pp + 4), d = ld2(pp + 6), e = ld2(pp + 8);
-                    if (side != 0) {
-                        fl[qi] = side > 0 ? weno5_2(a, b, c, d, e) : weno5_2(e, d, c, b, a);
-                        dd[qi] = side > 0 ? d : c;
-                    } else {
-                        fl[qi] = weno5_2(pos ? a : e, pos ? b : d, c, pos ? d : b, pos ? e : a);
-                        dd[qi] = pos ? d : c;
+                    for (int qi = 0; qi < 2; ++qi) {
+                        const int q = qp + qi;
+                        const bool pos = kSide > 0 || (kSide == 0 && v0 + kWarps * q < vhalf);   // uniform per warp
+                        const float *pp = rowq + (size_t)q * kWarps * 2 * kRowLen + (pos ? 0 : 2);
+                        const f2 a = ld2(pp), b = ld2(pp + 2), c = ld2(pp + 4), d = ld2(pp + 6), e = ld2(pp + 8);
+                        if constexpr (kSide > 0) {
+                            fl[qi] = weno5_2(a, b, c, d, e);
+                            dd[qi] = d;
+                        } else if constexpr (kSide < 0) {
+                            fl[qi] = weno5_2(e, d, c, b, a);
+                            dd[qi] = c;
+                        } else {
+                            fl[qi] = weno5_2(pos ? a : e, pos ? b : d, c, pos ? d : b, pos ? e : a);
+                            dd[qi] = pos ? d : c;
+                        }
+                    }
+#pragma unroll
+                    for (int qi = 0; qi < 2; ++qi) {
+                        const int q = qp + qi;
+                        const int v = v0 + kWarps * q;
+                        const bool okq = kFull || v < vend;
+                        const float *xr = s_vrow + (size_t)((kFull ? v : min(v, vend - 1)) - vbeg) * kVRow;
+                        const float4 xa = *reinterpret_cast<const float4 *>(xr);       // p_x p_y w ft_rest
+                        const float2 xg = *reinterpret_cast<const float2 *>(xr + VR_GA);
+                        const float px = xa.x, py = xa.y, w = xa.z, fr = xa.w;
+                        if (!kInner && wall) {   // wall faces: the incoming population n_w f_w (Eq. diffuse)
+                            const float4 xw = *reinterpret_cast<const float4 *>(xr + VR_FWL);
+                            if (needL && px > 0.f && s == 0) fl[qi] = mk2(nwL * xw.x - fr, nwL * xw.y - fr);
+                            if (needR && px < 0.f && s == Nx) fl[qi] = mk2(nwR * xw.z - fr, nwR * xw.w - fr);
+                        }
+                        int ga = __float_as_int(xg.x), gj = __float_as_int(xg.y);
+                        if (!LBC_CHECK(ctl, ga >= 0 && gj >= 0 && ga + kLanes <= G * kLanes && gj + kLanes <= G * kLanes,
+                                       CK_GTAB))
+                            ga = gj = 0;
+                        const float feq = n_c * s_g[ga + lane] * s_g[gj + lane];
+                        const float xx = px - ux_c, xy = py - uy_c;
+                        const float xx2 = xx * xx, e2 = fmaf(xy, xy, xx2);
+                        const float sq = fmaf(shA, xx, shB * xy);        // cS (q . xi)
+                        const float h = e2 * i5T;                         // xi^2 / (5 T)
+                        // Shakhov targets minus the rest state (Sec. II, the reduced S_phi, S_chi)
+                        const float fT = T_c * feq;                       // chi_eq = T phi_eq
+                        const float tp = fmaf(feq * sq, h - 0.8f, feq) - fr;
+                        const float tc = fmaf(fT * sq, h - 0.4f, fT) - fr;
+                        float fll, flh;
+                        un2(fl[qi], fll, flh);
+                        const float frl = __shfl_down_sync(0xffffffffu, fll, 1);
+                        const float frh = __shfl_down_sync(0xffffffffu, flh, 1);
+                        float dl, dh;
+                        un2(dd[qi], dl, dh);
+                        const float kp = k3 * px;
+                        float ol = fmaf(kp, fll - frl, fmaf(k2, tp, k1 * dl));
+                        float oh = fmaf(kp, flh - frh, fmaf(k2, tc, k1 * dh));
+                        if constexpr (stage > 0) {
+                            float d0l, d0h;
+                            un2(ld2(b0 + (size_t)q * kWarps * 2 * kF0Len), d0l, d0h);
+                            ol = fmaf(ca_of<float>(stage), d0l, ol);
+                            oh = fmaf(ca_of<float>(stage), d0h, oh);
+                            if constexpr (stage == 2)
+                                if (active && okq) res = fmaxf(res, w * fmaxf(fabsf(ol - d0l), fabsf(oh - d0h)));
+                        }
+                        if (active && okq && LBC_CHECK(ctl, v < T.V && s < Nxp, CK_STORE)) {
+                            st2(Fout_s + 2 * (size_t)Nxp * v, mk2(ol, oh));
+                            const float fw = w * ol, gw = w * oh;
+                            ps[0] = ps[0] + mk2(fw, gw);                                  // (S0, CZ)
+                            ps[1] = fma2(mk2(xx, xy), bc2(fw), ps[1]);                    // (SX, SY)
+                            ps[2] = fma2(mk2(xx, xy), bc2(gw), ps[2]);                    // (GX, GY)
+                            ps[3] = fma2(mk2(xx2, xy * xy), bc2(fw), ps[3]);              // (SXX, SYY)
+                            ps[4] = fma2(mk2(e2 * xx, e2 * xy), bc2(fw), ps[4]);          // (R3X, R3Y)
+                            psxy = fmaf(xx * xy, fw, psxy);
+                        }
                     }
                 }
-#pragma unroll
-                for (int qi = 0; qi < 2; ++qi) {
-                    const int q = qp + qi;
-                    const int v = v0 + kWarps * q;
-                    const bool okq = v < vend;
-                    const float *xr = s_vrow + (size_t)(min(v, vend - 1) - vbeg) * kVRow;
-                    const float4 xa = *reinterpret_cast<const float4 *>(xr);       // p_x p_y w ft_rest
-                    const float2 xg = *reinterpret_cast<const float2 *>(xr + VR_GA);
-                    const float px = xa.x, py = xa.y, w = xa.z, fr = xa.w;
-                    if (wall) {   // wall faces: the incoming population n_w f_w (Eq. diffuse)
-                        const float4 xw = *reinterpret_cast<const float4 *>(xr + VR_FWL);
-                        if (needL && px > 0.f && s == 0) fl[qi] = mk2(nwL * xw.x - fr, nwL * xw.y - fr);
-                        if (needR && px < 0.f && s == Nx) fl[qi] = mk2(nwR * xw.z - fr, nwR * xw.w - fr);
-                    }
-                    const float feq = n_c * s_g[__float_as_int(xg.x) + lane] * s_g[__float_as_int(xg.y) + lane];
-                    const float xx = px - ux_c, xy = py - uy_c;
-                    const float xx2 = xx * xx, e2 = fmaf(xy, xy, xx2);
-                    const float sq = fmaf(shA, xx, shB * xy);        // cS (q . xi)
-                    const float h = e2 * i5T;                         // xi^2 / (5 T)
-                    // Shakhov targets minus the rest state (Sec. II, the reduced S_phi, S_chi)
-                    const float fT = T_c * feq;                       // chi_eq = T phi_eq
-                    const float tp = fmaf(feq * sq, h - 0.8f, feq) - fr;
-                    const float tc = fmaf(fT * sq, h - 0.4f, fT) - fr;
-                    float fll, flh;
-                    un2(fl[qi], fll, flh);
-                    const float frl = __shfl_down_sync(0xffffffffu, fll, 1);
-                    const float frh = __shfl_down_sync(0xffffffffu, flh, 1);
-                    float dl, dh;
-                    un2(dd[qi], dl, dh);
-                    const float kp = k3 * px;
-                    float ol = fmaf(kp, fll - frl, fmaf(k2, tp, k1 * dl));
-                    float oh = fmaf(kp, flh - frh, fmaf(k2, tc, k1 * dh));
-                    if constexpr (stage > 0) {
-                        float d0l, d0h;
-                        un2(ld2(b0 + (size_t)q * kWarps * 2 * kF0Len), d0l, d0h);
-                        ol = fmaf(ca_of<float>(stage), d0l, ol);
-                        oh = fmaf(ca_of<float>(stage), d0h, oh);
-                        if constexpr (stage == 2)
-                            if (active && okq) res = fmaxf(res, w * fmaxf(fabsf(ol - d0l), fabsf(oh - d0h)));
-                    }
-                    if (active && okq) {
-                        st2(Fout_s + 2 * (size_t)Nxp * v, mk2(ol, oh));
-                        const float fw = w * ol, gw = w * oh;
-                        ps[0] = ps[0] + mk2(fw, gw);                                  // (S0, CZ)
-                        ps[1] = fma2(mk2(xx, xy), bc2(fw), ps[1]);                    // (SX, SY)
-                        ps[2] = fma2(mk2(xx, xy), bc2(gw), ps[2]);                    // (GX, GY)
-                        ps[3] = fma2(mk2(xx2, xy * xy), bc2(fw), ps[3]);              // (SXX, SYY)
-                        ps[4] = fma2(mk2(e2 * xx, e2 * xy), bc2(fw), ps[4]);          // (R3X, R3Y)
-                        psxy = fmaf(xx * xy, fw, psxy);
-                    }
-                }
+            };
+            using Pos = std::integral_constant<int, 1>;
+            using Neg = std::integral_constant<int, -1>;
+            using Mix = std::integral_constant<int, 0>;
+            using Yes = std::true_type;
+            using No = std::false_type;
+            const bool full = vs + kSubV <= vend;
+            if (vlast < vhalf) {
+                if (full && !wall) rows(Pos(), Yes(), Yes());
+                else rows(Pos(), No(), No());
+            } else if (vs >= vhalf) {
+                if (full && !wall) rows(Neg(), Yes(), Yes());
+                else rows(Neg(), No(), No());
+            } else {
+                rows(Mix(), No(), No());
             }
             // the slot's partial sums into the running sums, compensated (Kahan)
 #pragma unroll
@@ -1151,7 +1229,10 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
             for (int q = 0; q < NQ; ++q) {
                 const float4 xa = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow);   // px py w fr
                 const float4 xg = *reinterpret_cast<const float4 *>(s_vrow + kq[q] * kVRow + 8);
-                const int ga = __float_as_int(xg.x), gj = __float_as_int(xg.y);
+                int ga = __float_as_int(xg.x), gj = __float_as_int(xg.y);
+                if (!LBC_CHECK(ctl, ga >= 0 && gj >= 0 && ga + kLanes <= G * kLanes && gj + kLanes <= G * kLanes,
+                               CK_GTAB))
+                    ga = gj = 0;
                 const int r = warp + kWarps * q, v = vbeg + kq[q];
                 const float px = xa.x, py = xa.y, w = xa.z, fr = xa.w;
                 const float feq = n_c * s_g[ga + lane] * s_g[gj + lane];
@@ -1167,24 +1248,26 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
                 const f2 tgt = fma2(mk2(feq, T_c * feq), sh, bc2(-fr));
                 const f2 lr = fma2(bc2(-nu_c), dd[q] - tgt, adv);   // L of this stage
                 f2 dn = fma2(bc2(dt), lr, dd[q]);
+                // the node's own state (and compensation) entries: stored only inside the arrays
+                const bool okw = active && ok[q] && LBC_CHECK(ctl, v >= 0 && v < T.V && s < Nxp, CK_STORE);
                 const f2 dtl = comp_any ? bc2(dt) * lr : bc2(0.f);
                 float *ap = comp_any ? static_cast<float *>(S.A) + 2 * ((size_t)Nxp * v + s) : nullptr;
-                if (comp_any && stage < 2 && active && ok[q]) st2(ap, stage == 0 ? dtl : ld2(ap) + dtl);
+                if (comp_any && stage < 2 && okw) st2(ap, stage == 0 ? dtl : ld2(ap) + dtl);
                 if (stage > 0) {
                     const f2 d0 = ld2(f0 + (size_t)r * 2 * kF0Len + 2 * (lane + offf));
                     if (comp) {
                         // the step's increment dt (L0 + L1) / 6 + 2/3 dt L2, added to d0 + c0 with its
                         // rounding error kept (TwoSum of Knuth): increments below half an ulp of d0 count
                         f2 inc = bc2(2.f / 3.f) * dtl;
-                        if (active && ok[q]) inc = fma2(bc2(1.f / 6.f), ld2(ap), inc);
+                        if (okw) inc = fma2(bc2(1.f / 6.f), ld2(ap), inc);
                         if (renorm) inc = fma2(bc2(lam1r), d0 + inc + bc2(fr), inc);
                         float *cp = static_cast<float *>(S.C) + 2 * ((size_t)Nxp * v + s);
                         f2 cs = inc;
-                        if (active && ok[q]) cs = ld2(cp) + inc;
+                        if (okw) cs = ld2(cp) + inc;
                         const f2 sn = d0 + cs, bv = sn - d0;
                         const f2 er = (d0 - (sn - bv)) + (cs - bv);
                         dn = sn;
-                        if (active && ok[q]) {
+                        if (okw) {
                             st2(cp, er);
                             float e0, e1;
                             un2(inc, e0, e1);
@@ -1193,14 +1276,14 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
                     } else {
                         dn = fma2(bc2(ca), d0, bc2(cb) * dn);
                         if (renorm) dn = fma2(bc2(lam1r), dn + bc2(fr), dn);   // lambda (d + ft_rest) - ft_rest
-                        if (stage == 2 && active && ok[q]) {
+                        if (stage == 2 && okw) {
                             float e0, e1;
                             un2(dn - d0, e0, e1);
                             res = fmaxf(res, w * fmaxf(fabsf(e0), fabsf(e1)));
                         }
                     }
                 }
-                if (active && ok[q]) {
+                if (okw) {
                     st2(Fout_s + 2 * (size_t)Nxp * v, dn);
                     const f2 fg = bc2(w) * dn;                 // (fw, gw)
                     float fw, gw;
@@ -1252,7 +1335,10 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
                 for (int qi = 0; qi < 2; ++qi) {
                     const int q = qp + qi;
                     const R *x = s_vrow + kq[q] * kVRow;
-                    const int ga = row_bits(x[VR_GA]), gj = row_bits(x[VR_GJ]);
+                    int ga = row_bits(x[VR_GA]), gj = row_bits(x[VR_GJ]);
+                    if (!LBC_CHECK(ctl, ga >= 0 && gj >= 0 && ga + kLanes <= G * kLanes && gj + kLanes <= G * kLanes,
+                                   CK_GTAB))
+                        ga = gj = 0;
                     const int r = warp + kWarps * q, v = vbeg + kq[q];
                     const R px = x[VR_PX], py = x[VR_PY], w = x[VR_W], fr = x[VR_FR];
                     const R feq = n_c * s_g[ga + lane] * s_g[gj + lane];
@@ -1280,7 +1366,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
                         }
                         fo[fld] = dn;
                     }
-                    if (active && ok[q]) {
+                    if (active && ok[q] && LBC_CHECK(ctl, v >= 0 && v < T.V && s < Nxp, CK_STORE)) {
                         *reinterpret_cast<double2 *>(Fout_s + 2 * (size_t)Nxp * v) = make_double2(fo[0], fo[1]);
                         const R fw = w * fo[0], gw = w * fo[1];
                         const R e2 = xx * xx + xy * xy;
@@ -1315,6 +1401,14 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     const int nn = (kTile - rank + nch - 1) / nch;          // nodes rank, rank + nch, ... of the tile
     const int nnmax = (kTile + nch - 1) / nch;
     unsigned char *scr = smem + L.pipe;                     // EqScratch
+    if (!timed_out && tid < nn) {   // the equilibrium step's per-node data, towards L1 during the exchange
+        const int sp = c0 + rank + tid * nch;
+        if (sp < T.Nx) {
+            prefetch_l1(Tabs<R>::ijd(T) + sp);
+            prefetch_l1(Tabs<R>::dtn(T) + sp);
+            if (renorm) prefetch_l1(T.jdeta + sp);
+        }
+    }
     if (timed_out) {
         // give up: record it and let in-flight copies land (bounded); the CTA
         // still takes part in the cluster barriers below, without touching data
@@ -1370,7 +1464,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
         CSum<R> t;
         for (int w2 = 0; w2 < kWarps; ++w2) t.add(s_red[(w2 * kNumRaw + m) * kLanes + c]);
         const int owner = c % nch, i = c / nch;
-        st_cluster(&s_xch[((size_t)rank * nnmax + i) * kNumRaw + m], (uint32_t)owner, t.value());
+        if (LBC_CHECK(ctl, owner < nch && rank * nnmax + i < kTile + kMaxCluster, CK_XCH))
+            st_cluster(&s_xch[((size_t)rank * nnmax + i) * kNumRaw + m], (uint32_t)owner, t.value());
     }
     cluster_arrive();
     cluster_wait();   // every chunk's partials of this CTA's nodes are in s_xch
@@ -1501,7 +1596,12 @@ persistent_stage_kernel(const Inst *__restrict__ insts, const int2 *__restrict__
                     const unsigned need = csize * (3u * rel + stage);
                     for (int dt = -1; dt <= 1 && ok; ++dt) {
                         const int t = wk.y + dt;
-                        if (t >= 0 && t < I.T.ntile) ok = wait_at_least(&done[w + dt], need, abort);
+                        // the tile's neighbours are the adjacent work items of the same instance
+                        if (t >= 0 && t < I.T.ntile &&
+                            LBC_CHECK(I.S.ctl,
+                                      w + dt >= 0 && w + dt < nwork && work[w + dt].x == wk.x && work[w + dt].y == t,
+                                      CK_WORK))
+                            ok = wait_at_least(&done[w + dt], need, abort);
                     }
                     // early stop and local steps use instance-wide data of the previous step
                     if (ok && stage == 0 && rel > 0 && (I.T.lts || I.S.ctl->stop_eps > 0.0))
@@ -1911,6 +2011,31 @@ cudaError_t launch_state_out(const void *src, const void *carry, double *dst, co
     state_out_kernel<R><<<grid, 256, 0, st>>>(static_cast<const R *>(src), static_cast<const R *>(carry), dst,
                                               T.frest, T.V, T.Nx, T.Nxp);
     return cudaGetLastError();
+}
+
+const char *check_site_name(int site)
+{
+    static const char *const names[CK_COUNT] = {
+        "none",
+        "TMA box x coordinate off its 16-byte boundary",
+        "bulk copy outside its shared-memory region or source array",
+        "stencil, ghost or RK-base column outside the staged row box",
+        "equilibrium factor index outside the tile's table",
+        "state store outside [0, V) x [0, Nxp)",
+        "symmetry-plane partner row outside the state",
+        "cluster exchange slot outside the receiving CTA's region",
+        "node-stage write outside the stage data or scratch capacity",
+        "persistent item neighbour outside the work list or of another instance"};
+    return site > 0 && site < CK_COUNT ? names[site] : "unknown site";
+}
+
+bool checked_build()
+{
+#ifdef LBC_CHECKED
+    return true;
+#else
+    return false;
+#endif
 }
 
 cudaError_t launch_ctl_bump(Ctl *ctl, int n, long long k, cudaStream_t st)

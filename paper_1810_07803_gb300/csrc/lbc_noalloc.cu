@@ -131,6 +131,8 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
     NA_TRY(cudaMemcpyAsync(&h_ctl, S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream));
     NA_TRY(cudaStreamSynchronize(stream));
 #undef NA_TRY
+    if (h_ctl.bounds)
+        return fail_na(LBC_EBOUNDS, std::string("device index check failed: ") + check_site_name(h_ctl.bounds));
     if (h_ctl.timeout) return fail_na(LBC_ETIMEOUT, "a bounded device wait gave up");
     if (h_ctl.nonfinite) return fail_na(LBC_ENONFINITE, "non-finite value in the state");
     return LBC_OK;

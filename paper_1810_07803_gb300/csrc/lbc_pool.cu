@@ -304,7 +304,7 @@ lbc_status lbc_pool_run(lbc_pool *P, double residual, long nsteps, int *finished
     const int na = (int)P->active.size();
     if (na == 0 || nsteps == 0) return LBC_OK;
     if (fault_injected("launch")) return fail(LBC_ECUDA, "stage launch: injected failure (LBC_FAULT=launch)");
-    const int probe = fault_wait_polls();
+    const int probe = fault_wait_polls(), site = fault_bounds_site();
     size_t smem = 0;
     for (int s : P->active) {
         Ctl &c = P->h_ctl[s];
@@ -316,6 +316,7 @@ lbc_status lbc_pool_run(lbc_pool *P, double residual, long nsteps, int *finished
         c.stop_step = 0;
         c.stopped = 0;
         c.probe = probe;
+        if (site) c.bounds = site;
         smem = std::max(smem, P->slot[s].smem);
     }
     POOL_TRY(cudaMemcpyAsync(P->d_ctl, P->h_ctl, P->cap * sizeof(Ctl), cudaMemcpyHostToDevice, P->stream));
@@ -330,7 +331,10 @@ lbc_status lbc_pool_run(lbc_pool *P, double residual, long nsteps, int *finished
         const int s = P->active[k];
         Slot &S = P->slot[s];
         const Ctl &c = P->h_ctl[s];
-        if (c.timeout) st = fail(LBC_ETIMEOUT, "a bounded device wait gave up");
+        if (c.bounds && st == LBC_OK)
+            st = fail(LBC_EBOUNDS, "instance " + std::to_string(s) + ": device index check failed: " +
+                                       check_site_name(c.bounds));
+        if (c.timeout && st == LBC_OK) st = fail(LBC_ETIMEOUT, "a bounded device wait gave up");
         if (c.nonfinite && st == LBC_OK) st = fail(LBC_ENONFINITE, "non-finite value in instance " + std::to_string(s));
         const long long start = S.steps;
         bool conv = false;

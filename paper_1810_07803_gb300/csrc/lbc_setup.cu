@@ -40,6 +40,14 @@ int fault_wait_polls()
     return n > 0 && n < (1L << 30) ? (int)n : 0;
 }
 
+int fault_bounds_site()
+{
+    const char *f = std::getenv("LBC_FAULT");
+    if (!f || std::strncmp(f, "bounds:", 7) != 0) return 0;
+    const long n = std::strtol(f + 7, nullptr, 10);
+    return n > 0 && n < CK_COUNT ? (int)n : 0;
+}
+
 lbc_status validate(const lbc_params &p, int &Nxe, int &Nye)
 {
     if (p.Qx < 1 || p.Qx > kMaxQ || p.Qy < 1 || p.Qy > kMaxQ) return fail(LBC_EINVAL, "Qx and Qy must be in [1, 64]");
@@ -461,6 +469,8 @@ using namespace lbc;
 extern "C" {
 
 const char *lbc_last_error(void) { return last_error(); }
+
+int lbc_checked_build(void) { return checked_build() ? 1 : 0; }
 
 lbc_status lbc_quadrature(int Q, int half_range, double *nodes, double *weights)
 {

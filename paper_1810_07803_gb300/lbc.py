@@ -2,6 +2,8 @@
 
 Every step of the solver runs in the CUDA kernels behind the C ABI; there is no
 Python or CPU fallback. If the library has not been built, `lib()` raises.
+With LBC_CHECKED=1 in the environment the range-checked build
+(liblbc_checked.so, build.build(checked=True)) is loaded instead.
 PyTorch, when present, supplies the CUDA stream (torch.cuda.current_stream()).
 """
 from __future__ import annotations
@@ -13,11 +15,12 @@ import re
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblbc.so")
+LIB_PATH = os.path.join(HERE, "liblbc_checked.so" if os.environ.get("LBC_CHECKED", "0") not in ("", "0") else "liblbc.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "lbc.h")
 
-OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENONFINITE, ETIMEOUT = range(7)
-STATUS_NAMES = ["LBC_OK", "LBC_EINVAL", "LBC_ENOMEM", "LBC_ECUDA", "LBC_ENOTCONV", "LBC_ENONFINITE", "LBC_ETIMEOUT"]
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENONFINITE, ETIMEOUT, EBOUNDS = range(8)
+STATUS_NAMES = ["LBC_OK", "LBC_EINVAL", "LBC_ENOMEM", "LBC_ECUDA", "LBC_ENOTCONV", "LBC_ENONFINITE", "LBC_ETIMEOUT",
+                "LBC_EBOUNDS"]
 FP64, FP32_STATE = 0, 1
 NMOM = 10
 MOMENT_NAMES = ("n", "u_x", "u_y", "T", "P_xx", "P_yy", "P_zz", "P_xy", "q_x", "q_y")
@@ -25,7 +28,7 @@ MOMENT_NAMES = ("n", "u_x", "u_y", "T", "P_xx", "P_yy", "P_zz", "P_xy", "q_x", "
 
 class LbcError(RuntimeError):
     def __init__(self, status: int, msg: str):
-        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
 
 
@@ -104,6 +107,8 @@ def lib():
         L.lbc_destroy.argtypes = [vp]
         L.lbc_destroy.restype = None
         L.lbc_last_error.restype = C.c_char_p
+        L.lbc_checked_build.argtypes = []
+        L.lbc_checked_build.restype = C.c_int
         L.lbc_quadrature.argtypes = [C.c_int, C.c_int, dp, dp]
         L.lbc_equilibrium.argtypes = [C.POINTER(Params), C.c_double, C.c_double, C.c_double, dp, dp]
         L.lbc_step_noalloc.argtypes = [C.POINTER(Params), C.c_void_p, C.c_long, vp]
@@ -192,6 +197,11 @@ def measure_fp64_peak() -> float:
     t = C.c_double()
     _check(lib().lbc_measure_fp64_peak(C.byref(t)))
     return t.value
+
+
+def checked_build() -> bool:
+    """Whether the loaded library is the range-checked build (lbc_checked_build)."""
+    return bool(lib().lbc_checked_build())
 
 
 def current_stream_handle():

@@ -26,6 +26,21 @@ def test_exports_every_declared_symbol():
         assert hasattr(raw, n), n
 
 
+def test_build_variant_flag():
+    assert lbc.lib().lbc_checked_build() == (1 if lbc.LIB_PATH == build.LIB_CHECKED else 0)
+
+
+def test_checked_build_exports_every_declared_symbol_and_says_so():
+    """The range-checked variant (kernels compiled with LBC_CHECKED) links, exports the same
+    functions and reports itself as the checked build (a host call: no GPU needed)."""
+    path = build.build(checked=True)
+    raw = C.CDLL(path)
+    for n in lbc.declared_functions():
+        assert hasattr(raw, n), n
+    raw.lbc_checked_build.restype = C.c_int
+    assert raw.lbc_checked_build() == 1
+
+
 @pytest.mark.parametrize("bad,msg", [
     (dict(Qx=0), "Qx"), (dict(Qy=65), "Qx and Qy"), (dict(Nx=4), "Nx"), (dict(delta=-1.0), "delta"),
     (dict(T_left=0.0), "temperatures"), (dict(stretch_A=1.0), "stretch_A"), (dict(Nexp_x=4), "Nexp_x"),

@@ -67,6 +67,40 @@ def test_bounded_wait_in_a_batch(monkeypatch):
     ref.close()
 
 
+@pytest.mark.parametrize("kind", ["solver", "batch"])
+def test_injected_bounds_flag_reports_and_halts(monkeypatch, kind):
+    """LBC_FAULT=bounds:S uploads control blocks that carry a failed-check site, as a range
+    check of the checked build records it: the next read reports LBC_EBOUNDS naming the
+    site, stepping is refused until a state is installed, and the results then continue
+    bit for bit."""
+    ps = [dict(SMALL, precision="fp32"), dict(SMALL, delta=2.0, precision="fp32")]
+    make = (lambda: lbc.Solver(ps[0])) if kind == "solver" else (lambda: lbc.Batch(ps))
+    ref = make()
+    ref.step(4)
+    b = make()
+    rest = b.get_state() if kind == "solver" else [b.get_state(i) for i in range(2)]
+    monkeypatch.setenv("LBC_FAULT", "bounds:5")
+    with pytest.raises(lbc.LbcError) as e:
+        b.run_to_steady(1e-10, 5)
+    assert e.value.status == lbc.EBOUNDS
+    assert "state store" in str(e.value)
+    monkeypatch.delenv("LBC_FAULT")
+    with pytest.raises(lbc.LbcError) as e:   # refused until a state is installed
+        b.step(1)
+    assert e.value.status == lbc.EBOUNDS
+    if kind == "solver":
+        b.set_state(rest)
+        b.step(4)
+        assert np.array_equal(b.get_state(), ref.get_state())
+    else:
+        b.set_states(rest)
+        b.step(4)
+        for i in range(2):
+            assert np.array_equal(b.get_state(i), ref.get_state(i))
+    b.close()
+    ref.close()
+
+
 def test_injected_allocation_failure(monkeypatch):
     monkeypatch.setenv("LBC_FAULT", "alloc")
     with pytest.raises(lbc.LbcError) as e:
