@@ -225,9 +225,10 @@ lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, doubl
  * instance is exactly that of lbc_create).
  *
  * Each tile of 31 nodes of each instance is one work item; its velocity set is
- * split over `cluster` chunk CTAs that form one thread-block cluster. Work
- * items are scheduled longest first; instances of any size, order and
- * parameters mix freely. All instances of a batch share one precision.
+ * split over `cluster` chunk CTAs (one thread-block cluster in the cluster
+ * form, see below). Work items are scheduled longest first; instances of any
+ * size, order and parameters mix freely. All instances of a batch share one
+ * precision.
  *
  * lbc_batch_create: params[n] (copied), n >= 1; cluster = chunk CTAs per tile
  *   in [1, 16], or 0 to choose by a wave model of the whole batch.
@@ -253,9 +254,25 @@ lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, doubl
  * lbc_batch_shape: the launch shape (cluster size, work items, dynamic shared
  *   memory bytes of one stage CTA).
  * lbc_batch_autotune: for a batch whose instances have taken no step, times
- *   trial_steps steps for every feasible cluster size and keeps the fastest;
- *   the instances are at their initial (rest) state afterwards. *cluster
- *   (may be NULL) receives the choice. Synchronises the stream.
+ *   trial_steps steps for every feasible cluster size in both kernel forms
+ *   (below) and keeps the fastest; the instances are at their initial (rest)
+ *   state afterwards. *cluster (may be NULL) receives the choice. Synchronises
+ *   the stream.
+ * Kernel forms of the batched stage launch (same arithmetic in the same order,
+ * identical results): in the cluster form the chunk CTAs of a tile form one
+ * thread-block cluster, exchange their moment partials through distributed
+ * shared memory and each builds the next-stage data (moments, relaxation data,
+ * equilibrium factors) of a share of the tile's nodes; in the solo form the
+ * chunk CTAs are independent, write their partials to device memory and the
+ * tile's last CTA to finish builds the data of all its nodes while the others
+ * have left. lbc_batch_create picks the solo form when its work list fills the
+ * device at least once, else the cluster form.
+ * lbc_batch_form: *solo = 1 for the solo form, 0 for the cluster form (and for
+ *   a single-instance batch). Errors: LBC_EINVAL (NULL argument).
+ * lbc_batch_set_form: forces the form (solo != 0: solo) of the per-stage
+ *   launches, keeping the cluster size (the persistent form below always runs
+ *   the cluster form); synchronises the stream. Errors: LBC_EINVAL
+ *   (single-instance batch), LBC_ECUDA.
  */
 typedef struct lbc_batch lbc_batch;
 lbc_status lbc_batch_create(const lbc_params *params, int n, int cluster, void *cuda_stream, lbc_batch **out);
@@ -270,6 +287,8 @@ lbc_status lbc_batch_moments_all(lbc_batch *b, double *out);
 lbc_status lbc_batch_info(const lbc_batch *b, int i, int *Nx, int *V, double *dt, long *steps_taken);
 lbc_status lbc_batch_shape(const lbc_batch *b, int *cluster, int *nwork, size_t *smem_bytes);
 lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster);
+lbc_status lbc_batch_form(const lbc_batch *b, int *solo);
+lbc_status lbc_batch_set_form(lbc_batch *b, int solo);
 /* As lbc_batch_step with eager launches, timing each stage launch with CUDA
  * events on the batch's stream; *stage_ms receives the sum of the 3 nsteps
  * stage-kernel durations (for roofline reports). Synchronises the stream. */

@@ -60,6 +60,7 @@ struct lbc_batch {
     int *h_bad = nullptr;         // pinned
     bool steady_mode = false;     // the device control blocks hold run-to-steady settings
     bool poisoned = false;        // some instance holds a NaN/Inf
+    bool solo = false;            // batch kernel form: solo (tile's last CTA builds the node data) or cluster
     bool timed_out = false;       // a bounded device wait gave up: stepping is refused until set_state
     int bounds_site = 0;          // range-checked build: a device index check failed (refused the same way)
     cudaGraphExec_t graph = nullptr;
@@ -88,7 +89,7 @@ cudaError_t launch_steps_t(lbc_batch *b, int nsteps, cudaStream_t st)
         for (int stage = 0; stage < 3; ++stage) {
             cudaError_t e = b->single ? launch_stage<R>(b->inst[0], b->smem, stage, k, st)
                                       : launch_stage_batch<R>(b->d_inst, b->d_work, b->nwork, b->cluster, b->smem,
-                                                              stage, k, b->ext, st);
+                                                              stage, k, b->ext, b->solo, st);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -316,7 +317,7 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
     } else {
         std::vector<DevTables> Ts(n);
         for (int i = 0; i < n; ++i) Ts[i] = b->inst[i].T;
-        st = choose_batch_shape(b->fp32, Ts, cluster_in, b->cluster, b->smem);
+        st = choose_batch_shape(b->fp32, Ts, cluster_in, -1, b->solo, b->cluster, b->smem);
         for (int i = 0; i < n && st == LBC_OK; ++i) b->inst[i].T = Ts[i];
     }
     if (st != LBC_OK) return cleanup(st);
@@ -677,17 +678,26 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
     float best = 1e30f;
     int best_c = b->cluster;
     size_t best_smem = b->smem;
+    bool best_solo = b->solo;
+    const int keep_c = b->cluster;
+    const size_t keep_smem = b->smem;
+    const bool keep_solo = b->solo;
     std::vector<DevTables> best_T;
     lbc_status st = LBC_OK;
-    for (int C = 1; C <= kMaxCluster && st == LBC_OK; ++C) {
+    // both kernel forms where the per-stage launches run (the persistent form has one)
+    for (int trial = 0; trial < 2 * kMaxCluster && st == LBC_OK; ++trial) {
+        const int C = 1 + trial % kMaxCluster, form = b->persistent ? 0 : trial / kMaxCluster;
+        if (b->persistent && trial >= kMaxCluster) break;
         std::vector<DevTables> Ts(b->n);
         for (int i = 0; i < b->n; ++i) Ts[i] = keep[i].T;
         int c = 0;
         size_t smem = 0;
-        if (choose_batch_shape(b->fp32, Ts, C, c, smem) != LBC_OK) continue;
+        bool solo = false;
+        if (choose_batch_shape(b->fp32, Ts, C, form, solo, c, smem) != LBC_OK) continue;
         for (int i = 0; i < b->n; ++i) b->inst[i].T = Ts[i];
         b->cluster = c;
         b->smem = smem;
+        b->solo = solo;
         if (b->persistent && persistent_shape(b) != LBC_OK) continue;
         st = upload_descriptors(b);
         if (st != LBC_OK) break;
@@ -699,17 +709,21 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
         float ms = 0;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
         if (e != cudaSuccess) { st = fail(LBC_ECUDA, std::string("autotune: ") + cudaGetErrorString(e)); break; }
-        if (ms < best) { best = ms; best_c = c; best_smem = smem; best_T = Ts; }
+        if (ms < best) { best = ms; best_c = c; best_smem = smem; best_solo = solo; best_T = Ts; }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (best_T.empty()) {   // nothing measured: keep the model's choice
         b->inst = keep;
+        b->cluster = keep_c;
+        b->smem = keep_smem;
+        b->solo = keep_solo;
         st = st == LBC_OK ? fail(LBC_EINVAL, "no cluster size could be timed") : st;
     } else {
         for (int i = 0; i < b->n; ++i) b->inst[i].T = best_T[i];
         b->cluster = best_c;
         b->smem = best_smem;
+        b->solo = best_solo;
     }
     if (b->persistent && st == LBC_OK) st = persistent_shape(b);
     if (b->graph) {
@@ -800,6 +814,36 @@ lbc_status lbc_batch_shape(const lbc_batch *b, int *cluster, int *nwork, size_t 
 
 lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster) { return batch_autotune(b, trial_steps, cluster); }
 
+lbc_status lbc_batch_form(const lbc_batch *b, int *solo)
+{
+    if (!b || !solo) return fail(LBC_EINVAL, "NULL argument");
+    *solo = (!b->single && b->solo) ? 1 : 0;
+    return LBC_OK;
+}
+
+lbc_status lbc_batch_set_form(lbc_batch *b, int solo)
+{
+    if (!b) return fail(LBC_EINVAL, "NULL batch");
+    if (b->single) return fail(LBC_EINVAL, "a single-instance batch has the cluster form only");
+    std::vector<DevTables> Ts(b->n);
+    for (int i = 0; i < b->n; ++i) Ts[i] = b->inst[i].T;
+    bool f = false;
+    int c = 0;
+    size_t smem = 0;
+    lbc_status st = choose_batch_shape(b->fp32, Ts, b->cluster, solo ? 1 : 0, f, c, smem);
+    if (st != LBC_OK) return st;
+    LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));   // no launch of the old form in flight
+    for (int i = 0; i < b->n; ++i) b->inst[i].T = Ts[i];
+    b->cluster = c;
+    b->smem = smem;
+    b->solo = f;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return upload_descriptors(b);
+}
+
 lbc_status lbc_batch_set_persistent(lbc_batch *b, int on)
 {
     if (!b) return fail(LBC_EINVAL, "NULL batch");
@@ -834,10 +878,12 @@ lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms)
             if (e == cudaSuccess)
                 e = b->fp32 ? (b->single ? launch_stage<float>(b->inst[0], b->smem, stage, (int)k, b->stream)
                                          : launch_stage_batch<float>(b->d_inst, b->d_work, b->nwork, b->cluster,
-                                                                     b->smem, stage, (int)k, b->ext, b->stream))
+                                                                     b->smem, stage, (int)k, b->ext, b->solo,
+                                                                     b->stream))
                             : (b->single ? launch_stage<double>(b->inst[0], b->smem, stage, (int)k, b->stream)
                                          : launch_stage_batch<double>(b->d_inst, b->d_work, b->nwork, b->cluster,
-                                                                      b->smem, stage, (int)k, b->ext, b->stream));
+                                                                      b->smem, stage, (int)k, b->ext, b->solo,
+                                                                      b->stream));
             if (e == cudaSuccess) e = cudaEventRecord(ev[j + 1], b->stream);
         }
     if (e == cudaSuccess) e = launch_ctl_bump(b->d_ctl, b->n, nsteps, b->stream);

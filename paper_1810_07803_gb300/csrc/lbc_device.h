@@ -159,9 +159,12 @@ bool checked_build();                     // host: whether the kernels carry the
 // Mutable device state; arrays marked (R) hold the state precision.
 struct DevState {
     void *F[3];            // (R) [V][Nxp][2] deviation from the rest state, (phi, chi) adjacent per node
-    void *part;            // (R) [nchunk][kNumRaw][Nxp] raw moment sums (about p = 0) of the deviation per
-                           //     velocity chunk (set-up and lbc_moments only; the stage kernel exchanges its
-                           //     partials inside the tile's cluster)
+    void *part;            // (R) [nchunk][kNumRaw][Nxp] raw moment sums of the deviation per velocity chunk:
+                           //     about p = 0 at set-up and in lbc_moments; about the input stage's mean
+                           //     velocity in the solo form of the stage kernel (the cluster form exchanges
+                           //     its partials inside the tile's cluster)
+    unsigned *tcnt;        // [ntile] solo form: chunk CTAs of the tile done with the current stage (the
+                           //     last resets it to 0)
     void *eqm[3];          // (R) [Nxp][kEqM] moments and relaxation data of buffer b
     void *eqg[3];          // (R) [ntile][2Qx + Qy][kLanes] equilibrium factors of buffer b
     unsigned long long *resid;   // [kResidRing] per-step residual (bits of a double >= 0)
@@ -212,9 +215,11 @@ inline int chunk_rows(int V, int cluster) { return (V + kSubV * cluster - 1) / (
 // cluster size for one instance (T.nchunk) and its chunk rows (T.vchunk).
 // LBC_ECUDA without a device; LBC_EINVAL if no cluster shape fits.
 lbc_status choose_launch_shape(bool fp32, DevTables &T);
-// Cluster size and stage shared memory of a batch (sets every T.nchunk, T.vchunk);
-// cluster_in > 0 forces the cluster size.
-lbc_status choose_batch_shape(bool fp32, std::vector<DevTables> &Ts, int cluster_in, int &cluster, size_t &smem);
+// Cluster size (chunk CTAs per tile), form and stage shared memory of a batch (sets every
+// T.nchunk, T.vchunk); cluster_in > 0 forces the size; solo_in 1 / 0 forces the solo / cluster
+// form, -1 chooses.
+lbc_status choose_batch_shape(bool fp32, std::vector<DevTables> &Ts, int cluster_in, int solo_in, bool &solo,
+                              int &cluster, size_t &smem);
 // Dynamic shared memory of the stage kernel for T's launch shape.
 size_t stage_launch_smem(bool fp32, const DevTables &T);
 // Errors and parameter checks shared by every entry point.
@@ -240,21 +245,24 @@ size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cl
 template <typename R>
 size_t equilibrium_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int ntab);
 // Clusters of `cluster` stage CTAs that can be resident at once (0: not launchable),
-// for the single-instance (batch = false) or the batch stage kernel.
+// for the single-instance (batch = false) or the batch stage kernel; solo: the batch
+// kernel's solo form (no clusters), resident CTAs / cluster.
 template <typename R>
-cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, int *nclusters);
+cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, bool solo, int *nclusters);
 template <typename R>
 cudaError_t configure_kernels();   // per-device kernel attributes; call before capture
 // One RK stage of one instance: grid (ntile, nchunk), cluster dims (1, nchunk, 1);
 // the descriptor travels as a kernel parameter.
 template <typename R>
 cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStream_t st);
-// One RK stage of every work item: grid (nwork, cluster), cluster dims (1, cluster, 1);
+// One RK stage of every work item: grid (nwork, cluster), cluster dims (1, cluster, 1) in the
+// cluster form, no clusters in the solo form (solo: the tile's last chunk CTA builds the next
+// stage's data of all its nodes; DevState::tcnt counts them in);
 // work[i] = (instance, tile) with descriptors in device memory, instance < 0 for an empty slot.
 // ext: some instance uses the half channel or local steps (the kernel form that has them).
 template <typename R>
 cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, int cluster, size_t smem, int stage,
-                               int rel, bool ext, cudaStream_t st);
+                               int rel, bool ext, bool solo, cudaStream_t st);
 // Persistent form: nsteps RK-3 steps of every work item in one cooperative launch of nclusters
 // clusters (grid (nclusters, cluster)); cnt: kPersistHdr + nwork + n device counters (zeroed here);
 // the steps' residual slots are zeroed first. Work items of an instance must be its tiles in order.
@@ -296,7 +304,7 @@ inline size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 // Device bytes of one instance's state (partials sized for the largest cluster, so
 // a launch shape can change without reallocating).
 struct StateSizes {
-    size_t f, eqm, eqg, part, resid, mom, mass, carry, acc, total;
+    size_t f, eqm, eqg, part, tcnt, resid, mom, mass, carry, acc, total;
     StateSizes(const DevTables &T, bool fp32)
     {
         const size_t esz = fp32 ? sizeof(float) : sizeof(double);
@@ -304,12 +312,13 @@ struct StateSizes {
         eqm = round256((size_t)T.Nxp * kEqM * esz);
         eqg = round256((size_t)T.ntile * (2 * T.Qx + T.Qy) * kLanes * esz);
         part = round256((size_t)kMaxCluster * kNumRaw * T.Nxp * esz);
+        tcnt = round256((size_t)T.ntile * sizeof(unsigned));
         resid = kResidRing * sizeof(unsigned long long);
         mom = round256((size_t)LBC_NMOM * T.Nxp * sizeof(double));
         mass = round256((kMassHdr + 2 * (size_t)T.Nxp) * sizeof(double));
         carry = T.comp ? f : 0;
         acc = T.comp ? f : 0;
-        total = 3 * (f + eqm + eqg) + part + resid + mom + mass + carry + acc;
+        total = 3 * (f + eqm + eqg) + part + tcnt + resid + mom + mass + carry + acc;
     }
     // Points the state arrays of S into `base` (total bytes); S.ctl is set by the caller.
     void carve(char *base, DevState &S) const
@@ -319,6 +328,7 @@ struct StateSizes {
         for (int k = 0; k < 3; ++k) { S.eqm[k] = p; p += eqm; }
         for (int k = 0; k < 3; ++k) { S.eqg[k] = p; p += eqg; }
         S.part = p; p += part;
+        S.tcnt = reinterpret_cast<unsigned *>(p); p += tcnt;
         S.resid = reinterpret_cast<unsigned long long *>(p); p += resid;
         S.mom_out = reinterpret_cast<double *>(p); p += mom;
         S.mass = reinterpret_cast<double *>(p); p += mass;

@@ -738,8 +738,9 @@ struct Layout {
         total = o + 128;   // slack for aligning the dynamic base
     }
     __host__ __device__ static size_t al(size_t x) { return (x + 127) / 128 * 128; }
-    // nodes per CTA in the cluster's equilibrium step
-    __host__ __device__ static int node_cap(int cluster) { return (kTile + cluster - 1) / cluster; }
+    // node capacity of the equilibrium scratch: a whole tile (the solo form's last CTA takes all
+    // of its nodes; the cluster form's CTAs take ceil(kTile / cluster) of them)
+    __host__ __device__ static int node_cap(int) { return kTile; }
 };
 
 // TVD RK-3 (Shu & Osher): stage k's output is ca f^n + cb (y_k + dt L(y_k)).
@@ -763,8 +764,17 @@ __device__ __forceinline__ void kahan1(float &s, float &c, float x)
 // One RK stage of tile `tile` of instance I, for the CTA's velocity chunk
 // blockIdx.y (body of both stage kernels below). kExt compiles in the half
 // channel's symmetry plane and the local steps with mass renormalisation
-// (instances without them give the same results in either form).
-template <typename R, bool kExt, int kStage>
+// (instances without them give the same results in either form). The chunk
+// CTAs of a tile combine their moment partials in one of two ways:
+//  - cluster form (kSolo false): the tile's chunk CTAs form a thread-block
+//    cluster and exchange partials through distributed shared memory; each
+//    builds the next-stage data of nodes rank, rank + nchunk, ...;
+//  - solo form (kSolo true): plain CTAs write their partials to global memory
+//    (DevState::part) and count themselves in (DevState::tcnt); the tile's
+//    last CTA to finish sums the partials over the chunks, in chunk order, and
+//    builds the next-stage data of all the tile's nodes while the others have
+//    already left. Same arithmetic in the same order: identical results.
+template <typename R, bool kExt, int kStage, bool kSolo>
 __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, bool persist = false)
 {
     constexpr int stage = kStage;   // RK stage 0, 1, 2: a compile-time constant in every form
@@ -785,6 +795,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     R *s_eqm = reinterpret_cast<R *>(smem + L.eqm);       // [kTile][kEqM]
     R *s_vrow = reinterpret_cast<R *>(smem + L.vrow);     // [vchunk][kVRow]
     R *s_xch = reinterpret_cast<R *>(smem + L.xch);       // [nchunk][nn_max][kNumRaw]
+    __shared__ int s_last;                                // solo form: this CTA is the tile's last
     double *s_misc = reinterpret_cast<double *>(smem + L.misc);   // wsum[8], nwL, nwR
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -865,11 +876,28 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    cluster_arrive_relaxed();   // this CTA runs: the others may write into its shared memory after their wait
+    // solo form: the tile's chunk CTAs count themselves in once their stores (state, partials) are
+    // done; the last of them resets the count for the next launch and goes on to the node step
+    auto solo_count_in = [&]() -> bool {
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned k = atomicAdd(&S.tcnt[tile], 1u);
+            s_last = k + 1u == (unsigned)T.nchunk;
+            if (s_last) S.tcnt[tile] = 0u;
+        }
+        __syncthreads();
+        return s_last != 0;
+    };
+    if constexpr (!kSolo) cluster_arrive_relaxed();   // this CTA runs: the others may write into its shared memory after their wait
     if (bad) {   // range-checked build: give up before any copy, taking part in the cluster barriers
-        cluster_wait();
-        cluster_arrive();
-        cluster_wait();
+        if constexpr (kSolo) {
+            solo_count_in();
+        } else {
+            cluster_wait();
+            cluster_arrive();
+            cluster_wait();
+        }
         if (persist && tid < kPipe + 2) mbar_inval(&bar[tid]);
         return;
     }
@@ -1401,8 +1429,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     const int nn = (kTile - rank + nch - 1) / nch;          // nodes rank, rank + nch, ... of the tile
     const int nnmax = (kTile + nch - 1) / nch;
     unsigned char *scr = smem + L.pipe;                     // EqScratch
-    if (!timed_out && tid < nn) {   // the equilibrium step's per-node data, towards L1 during the exchange
-        const int sp = c0 + rank + tid * nch;
+    if (!timed_out && tid < (kSolo ? kTile : nn)) {   // the node step's per-node data, towards L1
+        const int sp = kSolo ? c0 + tid : c0 + rank + tid * nch;
         if (sp < T.Nx) {
             prefetch_l1(Tabs<R>::ijd(T) + sp);
             prefetch_l1(Tabs<R>::dtn(T) + sp);
@@ -1425,9 +1453,13 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
             mbar_wait(bar_data, 0);
         }
         __syncthreads();
-        cluster_wait();
-        cluster_arrive();
-        cluster_wait();
+        if constexpr (kSolo) {
+            solo_count_in();   // keeps the tile's count consistent for the next launch
+        } else {
+            cluster_wait();
+            cluster_arrive();
+            cluster_wait();
+        }
         if (persist && tid < kPipe + 2) mbar_inval(&bar[tid]);   // the next item initialises them again
         return;
     }
@@ -1458,6 +1490,48 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
             atomicMax(&S.resid[step % kResidRing], (unsigned long long)__double_as_longlong((double)rr));
     }
     __syncthreads();
+    // local steps: the mass deviations of f^{n+1} (buffer 0) for the next step's parity
+    double *dm = renorm ? S.mass + kMassHdr + (size_t)((step + 1) & 1) * T.Nxp : nullptr;
+    if constexpr (kSolo) {
+        // ---- (4') the chunk's partials (summed over warps) to global memory [nchunk][kNumRaw][Nxp] ----
+        R *part = static_cast<R *>(S.part);
+        for (int idx = tid; idx < kTile * kNumRaw; idx += kThreads) {
+            const int m = idx / kTile, c = idx - m * kTile;   // consecutive threads: consecutive nodes
+            if (c0 + c < T.Nx) {
+                CSum<R> t;
+                for (int w2 = 0; w2 < kWarps; ++w2) t.add(s_red[(w2 * kNumRaw + m) * kLanes + c]);
+                if (LBC_CHECK(ctl, chunk < kMaxCluster && c0 + c < T.Nxp, CK_XCH))
+                    part[((size_t)chunk * kNumRaw + m) * T.Nxp + c0 + c] = t.value();
+            }
+        }
+        const bool last = solo_count_in();
+        if (!last) {   // the table copy into this CTA's shared memory must land before it leaves
+            if (tid == 0) mbar_wait(bar_tab, 0);
+            return;
+        }
+        __threadfence();
+        // ---- (5') the tile's last CTA: every chunk's partials (L2), the next stage's data of all nodes ----
+        R *raw = reinterpret_cast<R *>(scr + E.raw);
+        R *shf = reinterpret_cast<R *>(scr + E.shf);
+        for (int idx = tid; idx < kTile * kNumRaw; idx += kThreads) {
+            const int i = idx / kNumRaw, m = idx - i * kNumRaw;
+            CSum<R> t;
+            if (c0 + i < T.Nx)
+                for (int ch = 0; ch < nch; ++ch) t.add(__ldcg(&part[((size_t)ch * kNumRaw + m) * T.Nxp + c0 + i]));
+            raw[idx] = t.value();
+        }
+        if (tid < kLanes) {   // warp 0, lane = node: the sums are about the input stage's mean velocity
+            shf[tid] = ux_c;
+            shf[kLanes + tid] = uy_c;
+        }
+        const bool late = __syncthreads_or(!mbar_wait(bar_tab, 0));
+        if (late) {
+            if (tid == 0) atomicExch(&ctl->timeout, 1);
+            return;
+        }
+        node_equilibrium<R>(T, S, out, tile, 0, 1, kTile, kTile, scr, dm, nullptr);
+        return;
+    }
     cluster_wait();   // every CTA of the cluster has started (pairs with the arrive at the top)
     for (int idx = tid; idx < kTile * kNumRaw; idx += kThreads) {
         const int c = idx / kNumRaw, m = idx - c * kNumRaw;
@@ -1490,8 +1564,6 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
         if (tid == 0) atomicExch(&ctl->timeout, 1);
         return;
     }
-    // local steps: the mass deviations of f^{n+1} (buffer 0) for the next step's parity
-    double *dm = renorm ? S.mass + kMassHdr + (size_t)((step + 1) & 1) * T.Nxp : nullptr;
     node_equilibrium<R>(T, S, out, tile, rank, nch, nn, ncap, scr, dm, nullptr);
     if (persist) {   // the item's mbarriers are done with: the next item initialises them again
         __syncthreads();
@@ -1504,20 +1576,20 @@ template <typename R, bool kExt, int kStage>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
 stage_kernel(const __grid_constant__ Inst I, int rel)
 {
-    stage_body<R, kExt, kStage>(I, blockIdx.x, rel);
+    stage_body<R, kExt, kStage, false>(I, blockIdx.x, rel);
 }
 
 // Batch: descriptors in device memory, one cluster per work item (instance, tile).
 // Three CTAs per SM in FP32: the descriptor fields live in registers here (in the
 // single-instance kernel they are constant-bank operands), and measured on GB300
 // the unspilled 3-CTA form is faster than a spilling 4-CTA form.
-template <typename R, bool kExt, int kStage>
+template <typename R, bool kExt, int kStage, bool kSolo>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
 stage_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int rel)
 {
     const int2 wk = work[blockIdx.x];
-    if (wk.x < 0) return;   // empty work slot: the whole cluster leaves
-    stage_body<R, kExt, kStage>(insts[wk.x], wk.y, rel);
+    if (wk.x < 0) return;   // empty work slot: the whole cluster (or every chunk CTA) leaves
+    stage_body<R, kExt, kStage, kSolo>(insts[wk.x], wk.y, rel);
 }
 
 // ---- persistent form: one launch for a group of steps of every work item ----
@@ -1633,9 +1705,9 @@ persistent_stage_kernel(const Inst *__restrict__ insts, const int2 *__restrict__
         const int2 wk = work[w];
         if (wk.x >= 0) {
             const Inst &I = insts[wk.x];
-            if (stage == 0) stage_body<R, kExt, 0>(I, wk.y, rel, true);
-            else if (stage == 1) stage_body<R, kExt, 1>(I, wk.y, rel, true);
-            else stage_body<R, kExt, 2>(I, wk.y, rel, true);
+            if (stage == 0) stage_body<R, kExt, 0, false>(I, wk.y, rel, true);
+            else if (stage == 1) stage_body<R, kExt, 1, false>(I, wk.y, rel, true);
+            else stage_body<R, kExt, 2, false>(I, wk.y, rel, true);
         }
         // completion: this CTA's writes fenced, then counted (the tile's stage item is done when
         // every CTA of its cluster has counted)
@@ -1808,13 +1880,16 @@ cudaError_t configure_kernels()
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const void *stage_fns[12] = {
-        (const void *)stage_kernel<R, false, 0>,       (const void *)stage_kernel<R, false, 1>,
-        (const void *)stage_kernel<R, false, 2>,       (const void *)stage_kernel<R, true, 0>,
-        (const void *)stage_kernel<R, true, 1>,        (const void *)stage_kernel<R, true, 2>,
-        (const void *)stage_batch_kernel<R, false, 0>, (const void *)stage_batch_kernel<R, false, 1>,
-        (const void *)stage_batch_kernel<R, false, 2>, (const void *)stage_batch_kernel<R, true, 0>,
-        (const void *)stage_batch_kernel<R, true, 1>,  (const void *)stage_batch_kernel<R, true, 2>};
+    const void *stage_fns[18] = {
+        (const void *)stage_kernel<R, false, 0>,              (const void *)stage_kernel<R, false, 1>,
+        (const void *)stage_kernel<R, false, 2>,              (const void *)stage_kernel<R, true, 0>,
+        (const void *)stage_kernel<R, true, 1>,               (const void *)stage_kernel<R, true, 2>,
+        (const void *)stage_batch_kernel<R, false, 0, false>, (const void *)stage_batch_kernel<R, false, 1, false>,
+        (const void *)stage_batch_kernel<R, false, 2, false>, (const void *)stage_batch_kernel<R, true, 0, false>,
+        (const void *)stage_batch_kernel<R, true, 1, false>,  (const void *)stage_batch_kernel<R, true, 2, false>,
+        (const void *)stage_batch_kernel<R, false, 0, true>,  (const void *)stage_batch_kernel<R, false, 1, true>,
+        (const void *)stage_batch_kernel<R, false, 2, true>,  (const void *)stage_batch_kernel<R, true, 0, true>,
+        (const void *)stage_batch_kernel<R, true, 1, true>,   (const void *)stage_batch_kernel<R, true, 2, true>};
     // dynamic shared memory up to the opt-in limit less the kernel's static shared memory
     auto allow = [&](const void *fn) {
         cudaFuncAttributes fa = {};
@@ -1874,10 +1949,11 @@ cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStr
     }
 }
 
-// One cluster per work item (instance, tile): its `cluster` chunk CTAs (cluster dimension y).
+// Work item (instance, tile) x its `cluster` chunk CTAs (grid dimension y): one thread-block
+// cluster per work item in the cluster form, independent CTAs in the solo form.
 template <typename R>
 cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, int cluster, size_t smem, int stage,
-                               int rel, bool ext, cudaStream_t st)
+                               int rel, bool ext, bool solo, cudaStream_t st)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nwork, (unsigned)cluster, 1);
@@ -1890,14 +1966,20 @@ cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, i
     at[0].val.clusterDim.y = (unsigned)cluster;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
-    switch (stage + 3 * ext) {
-    case 0: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 0>, insts, work, rel);
-    case 1: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 1>, insts, work, rel);
-    case 2: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 2>, insts, work, rel);
-    case 3: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 0>, insts, work, rel);
-    case 4: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 1>, insts, work, rel);
-    case 5: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 2>, insts, work, rel);
+    cfg.numAttrs = solo ? 0 : 1;
+    switch (stage + 3 * ext + 6 * solo) {
+    case 0: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 0, false>, insts, work, rel);
+    case 1: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 1, false>, insts, work, rel);
+    case 2: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 2, false>, insts, work, rel);
+    case 3: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 0, false>, insts, work, rel);
+    case 4: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 1, false>, insts, work, rel);
+    case 5: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 2, false>, insts, work, rel);
+    case 6: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 0, true>, insts, work, rel);
+    case 7: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 1, true>, insts, work, rel);
+    case 8: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 2, true>, insts, work, rel);
+    case 9: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 0, true>, insts, work, rel);
+    case 10: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 1, true>, insts, work, rel);
+    case 11: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 2, true>, insts, work, rel);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1952,9 +2034,19 @@ cudaError_t persistent_active_clusters(size_t smem, int cluster, int *nclusters)
 }
 
 template <typename R>
-cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, int *nclusters)
+cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, bool solo, int *nclusters)
 {
     *nclusters = 0;
+    if (solo) {   // independent CTAs: the CTAs the device holds at once, in groups of `cluster`
+        int dev = 0, nsm = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<R, false, 0, true>, kThreads,
+                                                              smem);
+        if (e == cudaSuccess) *nclusters = per_sm * nsm / cluster;
+        return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1, cluster, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
@@ -1967,7 +2059,7 @@ cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, int *ncl
     cfg.attrs = at;
     cfg.numAttrs = 1;
     // both forms of a kernel have the same launch bounds and shared memory: the plain one stands for both
-    return batch ? cudaOccupancyMaxActiveClusters(nclusters, stage_batch_kernel<R, false, 0>, &cfg)
+    return batch ? cudaOccupancyMaxActiveClusters(nclusters, stage_batch_kernel<R, false, 0, false>, &cfg)
                  : cudaOccupancyMaxActiveClusters(nclusters, stage_kernel<R, false, 0>, &cfg);
 }
 
@@ -2055,11 +2147,11 @@ cudaError_t launch_last_residuals(const Inst *insts, const int *slots, int n, do
     template size_t stage_smem_bytes<R>(int, int, int, int, int, int, int, int);                                     \
     template cudaError_t configure_kernels<R>();                                                                \
     template cudaError_t launch_stage<R>(const Inst &, size_t, int, int, cudaStream_t);                          \
-    template cudaError_t launch_stage_batch<R>(const Inst *, const int2 *, int, int, size_t, int, int, bool,       \
+    template cudaError_t launch_stage_batch<R>(const Inst *, const int2 *, int, int, size_t, int, int, bool, bool, \
                                                cudaStream_t);                                                    \
     template cudaError_t launch_tile_equilibrium<R>(const DevTables &, const DevState &, int, cudaStream_t);     \
     template cudaError_t launch_moments_partial<R>(const DevTables &, const DevState &, int, cudaStream_t);      \
-    template cudaError_t stage_active_clusters<R>(size_t, int, bool, int *);                                          \
+    template cudaError_t stage_active_clusters<R>(size_t, int, bool, bool, int *);                                    \
     template cudaError_t launch_persistent<R>(const Inst *, const int2 *, int, int, int, int, size_t, int, bool,     \
                                               unsigned *, cudaStream_t);                                          \
     template cudaError_t persistent_active_clusters<R>(size_t, int, int *);                                           \

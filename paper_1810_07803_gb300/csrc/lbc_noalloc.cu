@@ -98,6 +98,7 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
     for (int k = 0; k < 3; ++k) S.eqm[k] = cv.take((size_t)T.Nxp * kEqM * esz);
     for (int k = 0; k < 3; ++k) S.eqg[k] = cv.take((size_t)T.ntile * (2 * p.Qx + p.Qy) * kLanes * esz);
     S.part = cv.take((size_t)T.nchunk * kNumRaw * T.Nxp * esz);
+    S.tcnt = static_cast<unsigned *>(cv.take((size_t)T.ntile * sizeof(unsigned)));   // (cluster form: unused)
     S.resid = static_cast<unsigned long long *>(cv.take(kResidRing * sizeof(unsigned long long)));
     S.ctl = static_cast<Ctl *>(cv.take(sizeof(Ctl)));
     S.mom_out = static_cast<double *>(cv.take((size_t)LBC_NMOM * T.Nxp * sizeof(double)));

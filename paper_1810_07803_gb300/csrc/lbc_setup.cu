@@ -361,11 +361,11 @@ size_t stage_smem(bool fp32, const DevTables &T, int vchunk, int cluster)
                 : stage_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, vchunk, cluster, T.tab_n);
 }
 
-int active_clusters(bool fp32, size_t smem, int cluster, bool batch)
+int active_clusters(bool fp32, size_t smem, int cluster, bool batch, bool solo = false)
 {
     int ncl = 0;
-    cudaError_t e = fp32 ? stage_active_clusters<float>(smem, cluster, batch, &ncl)
-                         : stage_active_clusters<double>(smem, cluster, batch, &ncl);
+    cudaError_t e = fp32 ? stage_active_clusters<float>(smem, cluster, batch, solo, &ncl)
+                         : stage_active_clusters<double>(smem, cluster, batch, solo, &ncl);
     if (e != cudaSuccess) {
         cudaGetLastError();   // an unschedulable cluster shape is not an error of the solver
         return 0;
@@ -426,34 +426,64 @@ lbc_status choose_launch_shape(bool fp32, DevTables &T)
 // tile): the size that minimises a wave model of the whole work list, total
 // rows (plus a per-CTA overhead) over the CTAs the device holds at once, plus
 // the longest single CTA. cluster_in > 0 forces the size (if it fits).
-lbc_status choose_batch_shape(bool fp32, std::vector<DevTables> &Ts, int cluster_in, int &cluster, size_t &smem)
+// solo_in: 1 the solo form (independent CTAs, no cluster scheduling constraint),
+// 0 the cluster form, -1 the solo form when its work list fills the device at
+// least once (its tiles' last CTAs then overlap the other tiles' streaming), else
+// the cluster form (whose node step is spread over the cluster).
+lbc_status choose_batch_shape(bool fp32, std::vector<DevTables> &Ts, int cluster_in, int solo_in, bool &solo,
+                              int &cluster, size_t &smem)
 {
     int optin = 0;
     for (const DevTables &T : Ts) {
         lbc_status st = device_limits(fp32, T, optin);
         if (st != LBC_OK) return st;
     }
-    double best = 1e300;
-    cluster = 0;
-    smem = 0;
-    for (int C = 1; C <= kMaxCluster; ++C) {
-        if (cluster_in > 0 && C != cluster_in) continue;
-        size_t smax = 0;
-        double rows = 0, longest = 0;
-        bool fits = true;
-        for (const DevTables &T : Ts) {
-            const int vch = chunk_rows(T.V, C);
-            if (vch > kMaxVChunk) { fits = false; break; }
-            smax = std::max(smax, stage_smem(fp32, T, vch, C));
-            rows += (double)T.ntile * C * (vch + kCtaOverheadRows);
-            longest = std::max(longest, vch + kCtaOverheadRows);
+    struct Shape {
+        int C = 0;
+        size_t smem = 0;
+        double ctas = 0, resident = 0;
+    };
+    auto model = [&](bool form_solo) {
+        Shape best;
+        double best_cost = 1e300;
+        for (int C = 1; C <= kMaxCluster; ++C) {
+            if (cluster_in > 0 && C != cluster_in) continue;
+            size_t smax = 0;
+            double rows = 0, longest = 0, tiles = 0;
+            bool fits = true;
+            for (const DevTables &T : Ts) {
+                const int vch = chunk_rows(T.V, C);
+                if (vch > kMaxVChunk) { fits = false; break; }
+                smax = std::max(smax, stage_smem(fp32, T, vch, C));
+                rows += (double)T.ntile * C * (vch + kCtaOverheadRows);
+                longest = std::max(longest, vch + kCtaOverheadRows);
+                tiles += T.ntile;
+            }
+            if (!fits || smax > (size_t)optin) continue;
+            const int ncl = active_clusters(fp32, smax, C, true, form_solo);
+            if (ncl <= 0) continue;
+            const double cost = rows / ((double)ncl * C) + longest;
+            if (cost < best_cost - 1e-9) {
+                best_cost = cost;
+                best.C = C;
+                best.smem = smax;
+                best.ctas = tiles * C;
+                best.resident = (double)ncl * C;
+            }
         }
-        if (!fits || smax > (size_t)optin) continue;
-        const int ncl = active_clusters(fp32, smax, C, true);
-        if (ncl <= 0) continue;
-        const double cost = rows / ((double)ncl * C) + longest;
-        if (cost < best - 1e-9) { best = cost; cluster = C; smem = smax; }
+        return best;
+    };
+    Shape pick;
+    if (solo_in >= 0) {
+        solo = solo_in > 0;
+        pick = model(solo);
+    } else {
+        const Shape s1 = model(true);
+        solo = s1.C > 0 && s1.ctas >= s1.resident;
+        pick = solo ? s1 : model(false);
     }
+    cluster = pick.C;
+    smem = pick.smem;
     if (cluster == 0) return fail(LBC_EINVAL, "no schedulable cluster shape for this batch");
     for (DevTables &T : Ts) {
         T.nchunk = cluster;

@@ -123,6 +123,8 @@ def lib():
         L.lbc_batch_info.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), dp, C.POINTER(C.c_long)]
         L.lbc_batch_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.lbc_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+        L.lbc_batch_form.argtypes = [vp, C.POINTER(C.c_int)]
+        L.lbc_batch_set_form.argtypes = [vp, C.c_int]
         L.lbc_batch_step_timed.argtypes = [vp, C.c_long, dp]
         L.lbc_batch_set_persistent.argtypes = [vp, C.c_int]
         ip = C.POINTER(C.c_int)
@@ -351,6 +353,17 @@ class Batch:
         c = C.c_int()
         _check(lib().lbc_batch_autotune(self._h, int(trial_steps), C.byref(c)))
         return c.value
+
+    @property
+    def solo(self) -> bool:
+        """Whether the per-stage launches run the solo form (lbc_batch_form)."""
+        f = C.c_int()
+        _check(lib().lbc_batch_form(self._h, C.byref(f)))
+        return bool(f.value)
+
+    def set_form(self, solo: bool):
+        """Forces the solo (True) or the cluster (False) form (lbc_batch_set_form)."""
+        _check(lib().lbc_batch_set_form(self._h, int(bool(solo))))
 
     def set_persistent(self, on: bool = True):
         """Step as the persistent form (one launch per group of steps; lbc_batch_set_persistent)."""

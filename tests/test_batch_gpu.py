@@ -209,3 +209,81 @@ def test_set_states_with_local_steps_and_compensated_instances():
         assert np.array_equal(a.moments(i), b.moments(i)), i
     a.close()
     b.close()
+
+
+SQ2 = math.sqrt(2.0)
+
+
+def extended_mix(precision):
+    """The mix plus instances of the extended kernel form (local steps, half channel, compensated)."""
+    ps = with_precision(MIX, precision) + [
+        dict(Nx=40, Qx=5, Qy=5, stretch_A=0.95, delta=0.3, u_left=-0.1, u_right=0.1, local_dt=1, precision=precision),
+        dict(Nx=24, Qx=6, Qy=7, stretch_A=0.98, delta=1.0, u_left=-SQ2, u_right=SQ2, half_channel=1, local_dt=1,
+             precision=precision)]
+    if precision == "fp32":
+        ps.append(dict(workloads.c1(), precision="fp32", compensated=1))
+    return ps
+
+
+def assert_same_states(a, b, precision):
+    for i in range(a.n):
+        x, y = a.get_state(i), b.get_state(i)
+        if precision == "fp64":
+            assert np.max(np.abs(x - y)) <= 1e-14 * np.max(np.abs(x)), i
+        else:
+            assert np.array_equal(x, y), i
+        assert a.steps(i) == b.steps(i)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("cluster", [1, 3, 5])
+def test_solo_form_equals_cluster_form(precision, cluster):
+    """The solo form (independent chunk CTAs; the tile's last CTA sums the chunk partials from
+    device memory and builds the node data) computes the cluster form's sums in the same order:
+    bit for bit in FP32; the FP64 node arithmetic is compiled separately in each form (the
+    compiler may fuse its multiply-adds differently), compared to 1e-14 relative."""
+    for ps in (with_precision(MIX, precision), extended_mix(precision)):
+        a = lbc.Batch(ps, cluster=cluster)
+        a.set_form(False)
+        b = lbc.Batch(ps, cluster=cluster)
+        b.set_form(True)
+        assert not a.solo and b.solo
+        for n in (1, 2, 64, 5):   # eager launches and a captured group of 64 steps
+            a.step(n)
+            b.step(n)
+        assert_same_states(a, b, precision)
+        a.close()
+        b.close()
+
+
+def test_solo_form_run_to_steady_matches_cluster_form():
+    ps = [dict(workloads.c1(), delta=d) for d in (0.5, 3.0)] + with_precision(MIX[:2], "fp64")
+    a = lbc.Batch(ps, cluster=2)
+    a.set_form(False)
+    b = lbc.Batch(ps, cluster=2)
+    b.set_form(True)
+    ka, ra = a.run_to_steady(1e-9, 20000, raise_notconv=False)
+    kb, rb = b.run_to_steady(1e-9, 20000, raise_notconv=False)
+    assert list(ka) == list(kb)
+    np.testing.assert_allclose(np.asarray(rb), np.asarray(ra), rtol=1e-9)
+    assert_same_states(a, b, "fp64")
+    a.close()
+    b.close()
+
+
+def test_solo_form_at_the_benchmark_size():
+    """Four C2 solves (the benchmark's batch, which fills the device: the default is the solo
+    form) from a perturbed state, three steps in each form: bit for bit."""
+    ps = [workloads.c2(d, precision="fp32") for d in workloads.C2_DELTAS]
+    a = lbc.Batch(ps, cluster=3)
+    assert a.solo
+    b = lbc.Batch(ps, cluster=3)
+    b.set_form(False)
+    states = [workloads.perturbed_state(a.V[i], a.Nx[i], a.get_state(i), seed=7 + i) for i in range(a.n)]
+    a.set_states(states)
+    b.set_states(states)
+    a.step(3)
+    b.step(3)
+    assert_same_states(a, b, "fp32")
+    a.close()
+    b.close()

@@ -146,3 +146,26 @@ def test_injected_admission_refusal_queues(monkeypatch):
     pool.run(1e-8, 4)
     assert pool.info(slot)[3] == 4
     pool.close()
+
+
+def test_bounded_wait_in_the_solo_form(monkeypatch):
+    """A timed-out stage in the solo form still counts its CTAs in, so the tiles' counts stay
+    consistent: after a state is installed the batch continues bit for bit."""
+    ps = [dict(SMALL, delta=d, precision="fp32") for d in (0.5, 2.0)]
+    b = lbc.Batch(ps, cluster=2)
+    b.set_form(True)
+    rest = [b.get_state(i) for i in range(len(ps))]
+    monkeypatch.setenv("LBC_FAULT", "wait:16")
+    with pytest.raises(lbc.LbcError) as e:
+        b.run_to_steady(1e-10, 5)
+    assert e.value.status == lbc.ETIMEOUT
+    monkeypatch.delenv("LBC_FAULT")
+    b.set_states(rest)
+    b.step(3)
+    ref = lbc.Batch(ps, cluster=2)
+    ref.set_form(True)
+    ref.step(3)
+    for i in range(len(ps)):
+        assert np.array_equal(b.get_state(i), ref.get_state(i))
+    b.close()
+    ref.close()
