@@ -375,29 +375,33 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // ---- stage data of a set of nodes ----
 constexpr int kEqLB = 16;   // orders per block of the projection: lanes = 2 signs x 16 orders
 
-// Shared scratch of node_equilibrium for up to `ncap` nodes. The first `red`
-// bytes are left to the stage kernel's warp partials, so that the equilibrium
-// tables can be copied into `tab` while those are being reduced. Each warp
-// works through its nodes one at a time in its own `wk` slice: projection
-// weights r^{+-} [2][K], coefficients c^{+-} [cstride], and a block of kEqLB
-// rows h_l(sqrt(T') Y_k) [kEqLB][kpad].
+// Shared scratch of node_equilibrium for up to `ncap` nodes. The front region
+// holds first the stage kernel's warp partials (`red`: the equilibrium tables
+// are copied into `tab`, behind it, while those are being reduced) and then,
+// once the partials are consumed, the warps' projection slices (`wk`): each
+// warp works through its nodes nb at a time (two independent chains in flight
+// when the projection rule fits one lane per node), one slice per node:
+// projection weights r^{+-} [2][K], coefficients c^{+-} [cstride], and a block
+// of kEqLB rows h_l(sqrt(T') Y_k) [kEqLB][kpad].
 template <typename R>
 struct EqScratch {
     size_t red, tab, raw, shf, sc, bb, wk, wbytes, total;
-    int cstride, kpad;
+    int cstride, kpad, nb;
     __host__ __device__ EqScratch(int K, int N, int Ny, int Qx, int Qy, int ntab, int ncap = kTile)
     {
         cstride = 2 * (N + 1);
         kpad = K | 1;   // odd row stride: the lanes of a dot read conflict-free rows
+        nb = K <= 32 ? 2 : 1;
+        wbytes = al16((size_t)(2 * K + cstride + kEqLB * kpad) * sizeof(R));
         red = (size_t)kWarps * kNumRaw * kLanes * sizeof(R);
-        tab = al16(red);
+        wk = 0;
+        const size_t slices = (size_t)nb * kWarps * wbytes;
+        tab = al16(red > slices ? red : slices);
         raw = al16(tab + (size_t)EqTab(N, Ny, K, Qx, Qy, ntab).len * sizeof(R));
         shf = al16(raw + (size_t)ncap * kNumRaw * sizeof(R));
         sc = al16(shf + (size_t)2 * kLanes * sizeof(R));
         bb = al16(sc + (size_t)ncap * 8 * sizeof(R));
-        wk = al16(bb + (size_t)ncap * (Ny + 1) * sizeof(R));
-        wbytes = al16((size_t)(2 * K + cstride + kEqLB * kpad) * sizeof(R));
-        total = wk + kWarps * wbytes;
+        total = al16(bb + (size_t)ncap * (Ny + 1) * sizeof(R));
     }
     __host__ __device__ static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
 };
@@ -449,31 +453,41 @@ __device__ __forceinline__ void raw_to_moments_r(const R *r, R sx, R sy, R *m)
     m[9] = R(0.5) * hy + R(0.5) * (r[R_GY] - by * pzz);
 }
 
-// Hermite coefficients of g_x of one node by the Gauss-sum projection (a whole warp):
+// Hermite coefficients of g_x of NB nodes by the Gauss-sum projection (a whole warp):
 // c^{+-}_l = sum_k r_k^{+-} h_l(sqrt(T') Y_k), r_k^{+-} = W_k exp(+-a Y_k - a^2/2), over the K
-// nodes of the projection rule, for l <= N, into cw[2][N+1]. Lanes run the recurrence of
+// nodes of the projection rule, for l <= N, into cw[b][2][N+1]. Lanes run the recurrence of
 // the orthonormal h_l at projection nodes lane + 32 u (u < NU, K <= 32 NU) in blocks of kEqLB
-// orders; lane (sign, l) of a block takes one compensated dot product (Dot2 in FP32).
-// rp [2][K] and Hw [kEqLB][kpad] are this warp's scratch.
-template <typename R, int NU>
-__device__ __forceinline__ void project_coefficients(R sT, R a, R a2, int K, int N, int kpad, const R *Yk,
+// orders; lane (sign, l) of a block takes one compensated dot product (Dot2 in FP32) per node.
+// The NB nodes' chains are independent (latency hidden by each other) and share the table
+// reads; every node runs the same operations. x[b] = (sqrt(T'), a, a^2/2) of node b; rp[b]
+// [2][K] and Hw[b] [kEqLB][kpad] are this warp's scratch for node b.
+template <typename R, int NU, int NB>
+__device__ __forceinline__ void project_coefficients(const R *const *x, int K, int N, int kpad, const R *Yk,
                                                      const R *Wk, const R *alpha, const R *sbeta,
-                                                     const R *isbeta, R h0, R *rp, R *cw, R *Hw)
+                                                     const R *isbeta, R h0, R *const *rp, R *const *cw,
+                                                     R *const *Hw)
 {
     const int lane = threadIdx.x & 31;
     const int sgn = lane / kEqLB, lo = lane - sgn * kEqLB;
-    R zt[NU], h[NU], hp[NU];
+    R zt[NB][NU], h[NB][NU], hp[NB][NU];
 #pragma unroll
     for (int u = 0; u < NU; ++u) {
         const int k = lane + 32 * u;
-        zt[u] = R(0);
-        h[u] = h0;
-        hp[u] = R(0);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            zt[b][u] = R(0);
+            h[b][u] = h0;
+            hp[b][u] = R(0);
+        }
         if (k < K) {
             const R Y = Yk[k], W = Wk[k];
-            rp[k] = W * exp(a * Y - a2);
-            rp[K + k] = W * exp(-a * Y - a2);
-            zt[u] = sT * Y;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const R a = x[b][1], a2 = x[b][2];
+                rp[b][k] = W * exp(a * Y - a2);
+                rp[b][K + k] = W * exp(-a * Y - a2);
+                zt[b][u] = x[b][0] * Y;
+            }
         }
     }
     for (int lb = 0; lb <= N; lb += kEqLB) {
@@ -484,22 +498,68 @@ __device__ __forceinline__ void project_coefficients(R sT, R a, R a2, int K, int
 #pragma unroll
             for (int u = 0; u < NU; ++u) {
                 const int k = lane + 32 * u;
-                if (k < K) Hw[(l - lb) * kpad + k] = h[u];
-                const R hn = ((zt[u] - al) * h[u] - sb * hp[u]) * isb1;
-                hp[u] = h[u];
-                h[u] = hn;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    if (k < K) Hw[b][(l - lb) * kpad + k] = h[b][u];
+                    const R hn = ((zt[b][u] - al) * h[b][u] - sb * hp[b][u]) * isb1;
+                    hp[b][u] = h[b][u];
+                    h[b][u] = hn;
+                }
             }
         }
         __syncwarp();
         if (lb + lo <= le) {
-            const R *r = rp + sgn * K, *hh = Hw + lo * kpad;
-            Dot<R> d;
+            Dot<R> d[NB];
 #pragma unroll 4
-            for (int k = 0; k < K; ++k) d.add(r[k], hh[k]);
-            cw[sgn * (N + 1) + lb + lo] = d.value();
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) d[b].add(rp[b][sgn * K + k], Hw[b][lo * kpad + k]);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) cw[b][sgn * (N + 1) + lb + lo] = d[b].value();
         }
         __syncwarp();
     }
+}
+
+// Projection and g_x factors of nodes i (and i2 when `pair`) of a warp: its slices of the
+// scratch (L.nb per warp, the first NB of them used), then the factors
+// g_x/w at (node, sign a) = sum_l h_l(z_a) c_l^{sign}.
+template <typename R, int NU, int NB>
+__device__ __forceinline__ void equilibrium_nodes(const DevTables &T, const DevState &S, const EqScratch<R> &L, int i,
+                                                  int i2, bool pair, int K, int N, int Qx, const R *Yk,
+                                                  const R *Wk, const R *alpha, const R *sbeta, const R *isbeta,
+                                                  R h0, const R *hz, const R *sc, unsigned char *scratch, R *eqg,
+                                                  int cfirst, int cstep)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int node[2] = {i, i2};
+    const R *x[NB];
+    R *rp[NB], *cw[NB], *Hw[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        x[b] = sc + node[b] * 8;
+        rp[b] = reinterpret_cast<R *>(scratch + L.wk + (L.nb * warp + b) * L.wbytes);   // [2][K] r^+, r^-
+        cw[b] = rp[b] + 2 * K;                                                         // [2][N+1] c^+, c^-
+        Hw[b] = cw[b] + L.cstride;                                                     // [kEqLB][kpad]
+    }
+    project_coefficients<R, NU, NB>(x, K, N, L.kpad, Yk, Wk, alpha, sbeta, isbeta, h0, rp, cw, Hw);
+    for (int ig = lane; ig < 2 * Qx; ig += 32) {   // g_x factors (sign, a)
+        const int ii = ig < Qx ? ig : ig - Qx, off = ig < Qx ? 0 : N + 1;
+        R acc[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[b] = R(0);
+#pragma unroll 4
+        for (int l = 0; l <= N; ++l) {
+            const R hv = hz[l * Qx + ii];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) acc[b] = fma(hv, cw[b][off + l], acc[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if ((b == 0 || pair) && LBC_CHECK(S.ctl, cfirst + node[b] * cstep < kLanes, CK_EQ))
+                eqg[(size_t)ig * kLanes + cfirst + node[b] * cstep] = acc[b];
+    }
+    __syncwarp();   // the next nodes reuse this warp's slices
 }
 
 // Stage data of the nodes c = cfirst + i cstep (i < nn <= ncap) of tile `tile`
@@ -520,7 +580,7 @@ template <typename R>
 __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf, int tile, int cfirst, int cstep,
                                  int nn, int ncap, unsigned char *scratch, double *dm_a, double *dm_b)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, c0 = tile * kTile;
+    const int tid = threadIdx.x, warp = tid >> 5, c0 = tile * kTile;
     const int N = T.Nxe, K = T.K, G = 2 * T.Qx + T.Qy, Ny = T.Nye, Qx = T.Qx, Qy = T.Qy;
     const EqScratch<R> L(K, N, Ny, Qx, Qy, T.tab_n, ncap);
     const EqTab E(N, Ny, K, Qx, Qy, T.tab_n);
@@ -631,25 +691,20 @@ __device__ void node_equilibrium(const DevTables &T, const DevState &S, int buf,
     const R *Yk = tab + E.Yk, *Wk = tab + E.Wk;
     const R *alpha = tab + E.alpha, *sbeta = tab + E.sbeta, *isbeta = tab + E.isbeta;
     const R h0 = Tabs<R>::sc(T, SC_H0);
-    R *rp = reinterpret_cast<R *>(scratch + L.wk + warp * L.wbytes);   // [2][K] r^+, r^-
-    R *cw = rp + 2 * K;                                                // [2][N+1] c^+, c^-
-    R *Hw = cw + L.cstride;                                            // [kEqLB][kpad]
-    for (int i = warp; i < nn; i += kWarps) {
-        const R *x = sc + i * 8;
-        if (K <= 32)
-            project_coefficients<R, 1>(x[0], x[1], x[2], K, N, L.kpad, Yk, Wk, alpha, sbeta, isbeta, h0, rp, cw, Hw);
-        else
-            project_coefficients<R, 2>(x[0], x[1], x[2], K, N, L.kpad, Yk, Wk, alpha, sbeta, isbeta, h0, rp, cw, Hw);
-        R *col = eqg + cfirst + i * cstep;
-        for (int ig = lane; ig < 2 * Qx; ig += 32) {   // g_x factors (sign, a)
-            const int ii = ig < Qx ? ig : ig - Qx;
-            const R *cc = cw + (ig < Qx ? 0 : N + 1);
-            R acc = R(0);
-#pragma unroll 4
-            for (int l = 0; l <= N; ++l) acc = fma(hz[l * Qx + ii], cc[l], acc);
-            if (LBC_CHECK(S.ctl, cfirst + i * cstep < kLanes, CK_EQ)) col[(size_t)ig * kLanes] = acc;
+    if (L.nb == 2) {
+        // two nodes per warp (i, i + kWarps) with independent chains; a lone node alone
+        for (int i = warp; i < nn; i += 2 * kWarps) {
+            if (i + kWarps < nn)
+                equilibrium_nodes<R, 1, 2>(T, S, L, i, i + kWarps, true, K, N, Qx, Yk, Wk, alpha, sbeta, isbeta, h0,
+                                           hz, sc, scratch, eqg, cfirst, cstep);
+            else
+                equilibrium_nodes<R, 1, 1>(T, S, L, i, i, false, K, N, Qx, Yk, Wk, alpha, sbeta, isbeta, h0, hz, sc,
+                                           scratch, eqg, cfirst, cstep);
         }
-        __syncwarp();   // the next node reuses this warp's slice
+    } else {
+        for (int i = warp; i < nn; i += kWarps)
+            equilibrium_nodes<R, 2, 1>(T, S, L, i, i, false, K, N, Qx, Yk, Wk, alpha, sbeta, isbeta, h0, hz, sc,
+                                       scratch, eqg, cfirst, cstep);
     }
 }
 
@@ -877,14 +932,20 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     }
     __syncthreads();
     // solo form: the tile's chunk CTAs count themselves in once their stores (state, partials) are
-    // done; the last of them resets the count for the next launch and goes on to the node step
+    // done; the last of them resets the count for the next launch and goes on to the node step.
+    // One thread fences for the CTA: the barrier orders every thread's stores before its fence,
+    // which is cumulative (release before the count; acquire after it on the last CTA, whose
+    // threads then read the other CTAs' partials from L2).
     auto solo_count_in = [&]() -> bool {
-        __threadfence();
         __syncthreads();
         if (tid == 0) {
+            __threadfence();
             const unsigned k = atomicAdd(&S.tcnt[tile], 1u);
             s_last = k + 1u == (unsigned)T.nchunk;
-            if (s_last) S.tcnt[tile] = 0u;
+            if (s_last) {
+                S.tcnt[tile] = 0u;
+                __threadfence();
+            }
         }
         __syncthreads();
         return s_last != 0;
@@ -1509,7 +1570,6 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
             if (tid == 0) mbar_wait(bar_tab, 0);
             return;
         }
-        __threadfence();
         // ---- (5') the tile's last CTA: every chunk's partials (L2), the next stage's data of all nodes ----
         R *raw = reinterpret_cast<R *>(scr + E.raw);
         R *shf = reinterpret_cast<R *>(scr + E.shf);
