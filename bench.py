@@ -475,7 +475,7 @@ def main():
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": workload_config(),
         "launch": {"cluster": cluster, "form": "one batched stage launch per RK stage for the four solves",
-                   "state": args.precision},
+                   "kernel_form": "solo" if batch.solo else "cluster", "state": args.precision},
         "e2e": {"value": units * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "path": "per step: lbc_batch_set_states(pinned host f64, every solve) + lbc_batch_step(1) + "
