@@ -61,6 +61,7 @@ struct lbc_batch {
     bool steady_mode = false;     // the device control blocks hold run-to-steady settings
     bool poisoned = false;        // some instance holds a NaN/Inf
     bool solo = false;            // batch kernel form: solo (tile's last CTA builds the node data) or cluster
+    bool full = false;            // solo form with full 256-row chunks (choose_full_chunk_shape)
     bool timed_out = false;       // a bounded device wait gave up: stepping is refused until set_state
     int bounds_site = 0;          // range-checked build: a device index check failed (refused the same way)
     cudaGraphExec_t graph = nullptr;
@@ -678,26 +679,32 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
     float best = 1e30f;
     int best_c = b->cluster;
     size_t best_smem = b->smem;
-    bool best_solo = b->solo;
+    bool best_solo = b->solo, best_full = b->full;
     const int keep_c = b->cluster;
     const size_t keep_smem = b->smem;
-    const bool keep_solo = b->solo;
+    const bool keep_solo = b->solo, keep_full = b->full;
     std::vector<DevTables> best_T;
     lbc_status st = LBC_OK;
-    // both kernel forms where the per-stage launches run (the persistent form has one)
-    for (int trial = 0; trial < 2 * kMaxCluster && st == LBC_OK; ++trial) {
+    // both kernel forms where the per-stage launches run (the persistent form has one), and
+    // the solo form with full chunks (the last trial)
+    for (int trial = 0; trial <= 2 * kMaxCluster && st == LBC_OK; ++trial) {
         const int C = 1 + trial % kMaxCluster, form = b->persistent ? 0 : trial / kMaxCluster;
         if (b->persistent && trial >= kMaxCluster) break;
         std::vector<DevTables> Ts(b->n);
         for (int i = 0; i < b->n; ++i) Ts[i] = keep[i].T;
         int c = 0;
         size_t smem = 0;
-        bool solo = false;
-        if (choose_batch_shape(b->fp32, Ts, C, form, solo, c, smem) != LBC_OK) continue;
+        bool solo = trial == 2 * kMaxCluster;
+        if (solo) {
+            if (choose_full_chunk_shape(b->fp32, Ts, c, smem) != LBC_OK) continue;
+        } else if (choose_batch_shape(b->fp32, Ts, C, form, solo, c, smem) != LBC_OK) {
+            continue;
+        }
         for (int i = 0; i < b->n; ++i) b->inst[i].T = Ts[i];
         b->cluster = c;
         b->smem = smem;
         b->solo = solo;
+        b->full = trial == 2 * kMaxCluster;
         if (b->persistent && persistent_shape(b) != LBC_OK) continue;
         st = upload_descriptors(b);
         if (st != LBC_OK) break;
@@ -709,7 +716,7 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
         float ms = 0;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
         if (e != cudaSuccess) { st = fail(LBC_ECUDA, std::string("autotune: ") + cudaGetErrorString(e)); break; }
-        if (ms < best) { best = ms; best_c = c; best_smem = smem; best_solo = solo; best_T = Ts; }
+        if (ms < best) { best = ms; best_c = c; best_smem = smem; best_solo = solo; best_full = b->full; best_T = Ts; }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
@@ -718,12 +725,14 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
         b->cluster = keep_c;
         b->smem = keep_smem;
         b->solo = keep_solo;
+        b->full = keep_full;
         st = st == LBC_OK ? fail(LBC_EINVAL, "no cluster size could be timed") : st;
     } else {
         for (int i = 0; i < b->n; ++i) b->inst[i].T = best_T[i];
         b->cluster = best_c;
         b->smem = best_smem;
         b->solo = best_solo;
+        b->full = best_full;
     }
     if (b->persistent && st == LBC_OK) st = persistent_shape(b);
     if (b->graph) {
@@ -817,7 +826,7 @@ lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster) { ret
 lbc_status lbc_batch_form(const lbc_batch *b, int *solo)
 {
     if (!b || !solo) return fail(LBC_EINVAL, "NULL argument");
-    *solo = (!b->single && b->solo) ? 1 : 0;
+    *solo = (!b->single && b->solo) ? (b->full ? 2 : 1) : 0;
     return LBC_OK;
 }
 
@@ -827,16 +836,19 @@ lbc_status lbc_batch_set_form(lbc_batch *b, int solo)
     if (b->single) return fail(LBC_EINVAL, "a single-instance batch has the cluster form only");
     std::vector<DevTables> Ts(b->n);
     for (int i = 0; i < b->n; ++i) Ts[i] = b->inst[i].T;
-    bool f = false;
+    if (solo < 0 || solo > 2) return fail(LBC_EINVAL, "form must be 0, 1 or 2");
+    bool f = solo == 2;
     int c = 0;
     size_t smem = 0;
-    lbc_status st = choose_batch_shape(b->fp32, Ts, b->cluster, solo ? 1 : 0, f, c, smem);
+    lbc_status st = solo == 2 ? choose_full_chunk_shape(b->fp32, Ts, c, smem)
+                              : choose_batch_shape(b->fp32, Ts, b->cluster, solo ? 1 : 0, f, c, smem);
     if (st != LBC_OK) return st;
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));   // no launch of the old form in flight
     for (int i = 0; i < b->n; ++i) b->inst[i].T = Ts[i];
     b->cluster = c;
     b->smem = smem;
     b->solo = f;
+    b->full = solo == 2;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;

@@ -220,6 +220,8 @@ lbc_status choose_launch_shape(bool fp32, DevTables &T);
 // form, -1 chooses.
 lbc_status choose_batch_shape(bool fp32, std::vector<DevTables> &Ts, int cluster_in, int solo_in, bool &solo,
                               int &cluster, size_t &smem);
+// Solo-form shape with kMaxVChunk-row chunks (the last one of each instance shorter).
+lbc_status choose_full_chunk_shape(bool fp32, std::vector<DevTables> &Ts, int &cluster, size_t &smem);
 // Dynamic shared memory of the stage kernel for T's launch shape.
 size_t stage_launch_smem(bool fp32, const DevTables &T);
 // Errors and parameter checks shared by every entry point.

@@ -355,15 +355,21 @@ class Batch:
         return c.value
 
     @property
-    def solo(self) -> bool:
-        """Whether the per-stage launches run the solo form (lbc_batch_form)."""
+    def form(self) -> int:
+        """0 cluster form, 1 solo form, 2 solo form with 256-row chunks (lbc_batch_form)."""
         f = C.c_int()
         _check(lib().lbc_batch_form(self._h, C.byref(f)))
-        return bool(f.value)
+        return f.value
 
-    def set_form(self, solo: bool):
-        """Forces the solo (True) or the cluster (False) form (lbc_batch_set_form)."""
-        _check(lib().lbc_batch_set_form(self._h, int(bool(solo))))
+    @property
+    def solo(self) -> bool:
+        """Whether the per-stage launches run the solo form."""
+        return self.form != 0
+
+    def set_form(self, solo):
+        """Forces the cluster (False / 0), solo (True / 1) or full-chunk solo (2) form
+        (lbc_batch_set_form)."""
+        _check(lib().lbc_batch_set_form(self._h, int(solo)))
 
     def set_persistent(self, on: bool = True):
         """Step as the persistent form (one launch per group of steps; lbc_batch_set_persistent)."""

@@ -287,3 +287,23 @@ def test_solo_form_at_the_benchmark_size():
     assert_same_states(a, b, "fp32")
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_full_chunk_form_matches_oracle(precision, tol):
+    """The solo form with 256-row chunks (form 2: each instance's last chunk shorter, empty
+    chunk CTAs where an instance has fewer chunks than the batch): every instance against the
+    oracle, including one whose velocity set spans two chunks (320 rows: 256 + 64)."""
+    ps = with_precision(MIX, precision) + [
+        dict(Nx=80, Qx=16, Qy=10, stretch_A=0.9, delta=1.5, u_left=-0.2, u_right=0.1, T_left=0.9, T_right=1.2,
+             precision=precision)]
+    b = lbc.Batch(ps)
+    b.set_form(2)
+    assert b.form == 2 and b.shape()[0] == 2
+    b.step(12)
+    for i, p in enumerate(ps):
+        o = Oracle(p)
+        o.run(12)
+        e = moment_errors(b.moments(i), o.moments())
+        assert np.all(e < tol), (i, dict(zip(lbc.MOMENT_NAMES, e)))
+    b.close()
