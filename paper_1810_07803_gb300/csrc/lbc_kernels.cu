@@ -1227,12 +1227,16 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
                         }
                         if (active && okq && LBC_CHECK(ctl, v < T.V && s < Nxp, CK_STORE)) {
                             st2(Fout_s + 2 * (size_t)Nxp * v, mk2(ol, oh));
-                            const float fw = w * ol, gw = w * oh;
-                            ps[0] = ps[0] + mk2(fw, gw);                                  // (S0, CZ)
-                            ps[1] = fma2(mk2(xx, xy), bc2(fw), ps[1]);                    // (SX, SY)
-                            ps[2] = fma2(mk2(xx, xy), bc2(gw), ps[2]);                    // (GX, GY)
-                            ps[3] = fma2(mk2(xx2, xy * xy), bc2(fw), ps[3]);              // (SXX, SYY)
-                            ps[4] = fma2(mk2(e2 * xx, e2 * xy), bc2(fw), ps[4]);          // (R3X, R3Y)
+                            // the pairs as the packed operations produce them: (fw, gw) = w (phi, chi)
+                            const f2 fg = mk2(ol, oh) * bc2(w);
+                            float fw, gw;
+                            un2(fg, fw, gw);
+                            const f2 pxy = mk2(xx, xy);
+                            ps[0] = ps[0] + fg;                                           // (S0, CZ)
+                            ps[1] = fma2(bc2(xx), fg, ps[1]);                             // (SX, GX)
+                            ps[2] = fma2(bc2(xy), fg, ps[2]);                             // (SY, GY)
+                            ps[3] = fma2(pxy * pxy, bc2(fw), ps[3]);                      // (SXX, SYY)
+                            ps[4] = fma2(bc2(e2) * pxy, bc2(fw), ps[4]);                  // (R3X, R3Y)
                             psxy = fmaf(xx * xy, fw, psxy);
                         }
                     }
@@ -1536,8 +1540,13 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
         for (int m = 0; m < 5; ++m) pk[m] = pk[m] - pkc[m];
         acc[R_SXY] -= sxyc;
         un2(pk[0], acc[R_S0], acc[R_CZ]);
-        un2(pk[1], acc[R_SX], acc[R_SY]);
-        un2(pk[2], acc[R_GX], acc[R_GY]);
+        if constexpr (kLean) {   // the plain loop pairs its sums by coordinate: (SX, GX), (SY, GY)
+            un2(pk[1], acc[R_SX], acc[R_GX]);
+            un2(pk[2], acc[R_SY], acc[R_GY]);
+        } else {
+            un2(pk[1], acc[R_SX], acc[R_SY]);
+            un2(pk[2], acc[R_GX], acc[R_GY]);
+        }
         un2(pk[3], acc[R_SXX], acc[R_SYY]);
         un2(pk[4], acc[R_R3X], acc[R_R3Y]);
     }
