@@ -49,9 +49,9 @@ def parse():
     ap.add_argument("--no-steady", action="store_true", help="skip the steady-solves leg")
     ap.add_argument("--no-single", action="store_true", help="skip the single-solve leg")
     ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-form leg")
-    ap.add_argument("--form", choices=["auto", "cluster", "solo", "full"], default="auto",
+    ap.add_argument("--form", choices=["auto", "cluster", "solo", "full", "split", "splitfull"], default="auto",
                     help="kernel form of the batched launch when --cluster fixes the shape (full: solo form "
-                         "with 256-row chunks, cluster size following)")
+                         "with 256-row chunks, cluster size following; split: a node-step launch per stage)")
     ap.add_argument("--cluster", type=int, default=0,
                     help="chunk CTAs per tile of the batched launch (0: autotune; fix it to profile a shape)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
@@ -395,7 +395,7 @@ def main():
     batch = lbc.Batch(params, cluster=args.cluster)
     # cells per CTA: chosen by timing every feasible cluster size, unless fixed
     if args.cluster != 0 and args.form != "auto":
-        batch.set_form({"cluster": 0, "solo": 1, "full": 2}[args.form])
+        batch.set_form({"cluster": 0, "solo": 1, "full": 2, "split": 3, "splitfull": 4}[args.form])
     cluster = batch.autotune(3) if args.cluster == 0 else batch.shape()[0]
     nsol = batch.n
     V, Nx = batch.V[0], batch.Nx[0]
@@ -480,7 +480,7 @@ def main():
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": workload_config(),
         "launch": {"cluster": cluster, "form": "one batched stage launch per RK stage for the four solves",
-                   "kernel_form": ["cluster", "solo", "solo, 256-row chunks"][batch.form], "state": args.precision},
+                   "kernel_form": batch.FORMS[batch.form], "state": args.precision},
         "e2e": {"value": units * world / e2e_s, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "path": "per step: lbc_batch_set_states(pinned host f64, every solve) + lbc_batch_step(1) + "

@@ -254,9 +254,9 @@ lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, doubl
  * lbc_batch_shape: the launch shape (cluster size, work items, dynamic shared
  *   memory bytes of one stage CTA).
  * lbc_batch_autotune: for a batch whose instances have taken no step, times
- *   trial_steps steps for every feasible cluster size in both kernel forms
- *   (below), and the solo form with chunks of 256 velocity rows (each
- *   instance's last chunk shorter), and keeps the fastest; the instances are at their initial (rest)
+ *   trial_steps steps for every feasible cluster size in the three kernel
+ *   forms (below), and the solo and split forms with chunks of 256 velocity
+ *   rows (each instance's last chunk shorter), and keeps the fastest; the instances are at their initial (rest)
  *   state afterwards. *cluster (may be NULL) receives the choice. Synchronises
  *   the stream.
  * Kernel forms of the batched stage launch (same arithmetic in the same order,
@@ -268,15 +268,18 @@ lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, doubl
  * tile's last CTA to finish builds the data of all its nodes while the others
  * have left. lbc_batch_create picks the solo form when its work list fills the
  * device at least once, else the cluster form.
- * lbc_batch_form: *solo = 1 for the solo form, 2 for the solo form with
- *   256-row chunks, 0 for the cluster form (and for a single-instance batch).
+ * A third form, split, runs the solo form's independent chunk CTAs without the
+ * node step and builds every tile's next-stage data in a second launch per
+ * stage, spread over the whole GPU (same arithmetic, identical results).
+ * lbc_batch_form: *solo = 0 cluster form (also for a single-instance batch),
+ *   1 solo, 2 solo with 256-row chunks, 3 split, 4 split with 256-row chunks.
  *   Errors: LBC_EINVAL (NULL argument).
  * lbc_batch_set_form: forces the form of the per-stage launches (the persistent
- *   form below always runs the cluster form): 0 cluster, 1 solo, both keeping
- *   the cluster size; 2 solo with chunks of 256 velocity rows (each instance's
- *   last chunk shorter; the cluster size follows). Synchronises the stream.
- *   Errors: LBC_EINVAL (single-instance batch, form outside 0-2, a shape that
- *   does not fit), LBC_ECUDA.
+ *   form below always runs the cluster form), with the codes of lbc_batch_form:
+ *   0, 1 and 3 keep the cluster size; 2 and 4 use chunks of 256 velocity rows
+ *   (each instance's last chunk shorter; the cluster size follows).
+ *   Synchronises the stream. Errors: LBC_EINVAL (single-instance batch, form
+ *   outside 0-4, a shape that does not fit), LBC_ECUDA.
  */
 typedef struct lbc_batch lbc_batch;
 lbc_status lbc_batch_create(const lbc_params *params, int n, int cluster, void *cuda_stream, lbc_batch **out);

@@ -60,8 +60,11 @@ struct lbc_batch {
     int *h_bad = nullptr;         // pinned
     bool steady_mode = false;     // the device control blocks hold run-to-steady settings
     bool poisoned = false;        // some instance holds a NaN/Inf
-    bool solo = false;            // batch kernel form: solo (tile's last CTA builds the node data) or cluster
-    bool full = false;            // solo form with full 256-row chunks (choose_full_chunk_shape)
+    bool solo = false;            // batch kernel form without clusters: solo (the tile's last CTA builds the
+                                  // node data) or, with split, split (a node-step launch builds it)
+    bool split = false;
+    bool full = false;            // chunks of 256 rows (choose_full_chunk_shape)
+    size_t node_smem = 0;         // split form: dynamic shared memory of the node-step launch
     bool timed_out = false;       // a bounded device wait gave up: stepping is refused until set_state
     int bounds_site = 0;          // range-checked build: a device index check failed (refused the same way)
     cudaGraphExec_t graph = nullptr;
@@ -83,6 +86,8 @@ struct lbc_solver {
 
 namespace {
 
+int kernel_form(const lbc_batch *b) { return b->solo ? (b->split ? kFormSplit : kFormSolo) : kFormCluster; }
+
 template <typename R>
 cudaError_t launch_steps_t(lbc_batch *b, int nsteps, cudaStream_t st)
 {
@@ -90,7 +95,7 @@ cudaError_t launch_steps_t(lbc_batch *b, int nsteps, cudaStream_t st)
         for (int stage = 0; stage < 3; ++stage) {
             cudaError_t e = b->single ? launch_stage<R>(b->inst[0], b->smem, stage, k, st)
                                       : launch_stage_batch<R>(b->d_inst, b->d_work, b->nwork, b->cluster, b->smem,
-                                                              stage, k, b->ext, b->solo, st);
+                                                              stage, k, b->ext, kernel_form(b), b->node_smem, st);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -320,6 +325,12 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
         for (int i = 0; i < n; ++i) Ts[i] = b->inst[i].T;
         st = choose_batch_shape(b->fp32, Ts, cluster_in, -1, b->solo, b->cluster, b->smem);
         for (int i = 0; i < n && st == LBC_OK; ++i) b->inst[i].T = Ts[i];
+        for (int i = 0; i < n && st == LBC_OK; ++i) {   // the split form's node-step launch
+            const DevTables &T = b->inst[i].T;
+            const size_t eq = b->fp32 ? equilibrium_smem_bytes<float>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.tab_n)
+                                      : equilibrium_smem_bytes<double>(T.Qx, T.Qy, T.Nxe, T.Nye, T.K, T.tab_n);
+            b->node_smem = std::max(b->node_smem, eq + 128);   // + alignment of the dynamic base
+        }
     }
     if (st != LBC_OK) return cleanup(st);
 
@@ -679,32 +690,34 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
     float best = 1e30f;
     int best_c = b->cluster;
     size_t best_smem = b->smem;
-    bool best_solo = b->solo, best_full = b->full;
+    bool best_solo = b->solo, best_full = b->full, best_split = b->split;
     const int keep_c = b->cluster;
     const size_t keep_smem = b->smem;
-    const bool keep_solo = b->solo, keep_full = b->full;
+    const bool keep_solo = b->solo, keep_full = b->full, keep_split = b->split;
     std::vector<DevTables> best_T;
     lbc_status st = LBC_OK;
-    // both kernel forms where the per-stage launches run (the persistent form has one), and
-    // the solo form with full chunks (the last trial)
-    for (int trial = 0; trial <= 2 * kMaxCluster && st == LBC_OK; ++trial) {
-        const int C = 1 + trial % kMaxCluster, form = b->persistent ? 0 : trial / kMaxCluster;
-        if (b->persistent && trial >= kMaxCluster) break;
+    // every cluster size in the three forms of the per-stage launches (the persistent form has one
+    // form), and the solo and split forms with full chunks (the last two trials)
+    const int ntrials = b->persistent ? kMaxCluster : 3 * kMaxCluster + 2;
+    for (int trial = 0; trial < ntrials && st == LBC_OK; ++trial) {
+        const int C = 1 + trial % kMaxCluster, kind = trial / kMaxCluster;   // 0 cluster, 1 solo, 2 split, 3 full
         std::vector<DevTables> Ts(b->n);
         for (int i = 0; i < b->n; ++i) Ts[i] = keep[i].T;
         int c = 0;
         size_t smem = 0;
-        bool solo = trial == 2 * kMaxCluster;
-        if (solo) {
+        bool solo = kind > 0;
+        const bool full = kind == 3, split = kind == 2 || (full && trial == 3 * kMaxCluster + 1);
+        if (full) {
             if (choose_full_chunk_shape(b->fp32, Ts, c, smem) != LBC_OK) continue;
-        } else if (choose_batch_shape(b->fp32, Ts, C, form, solo, c, smem) != LBC_OK) {
+        } else if (choose_batch_shape(b->fp32, Ts, C, kind > 0 ? 1 : 0, solo, c, smem) != LBC_OK) {
             continue;
         }
         for (int i = 0; i < b->n; ++i) b->inst[i].T = Ts[i];
         b->cluster = c;
         b->smem = smem;
         b->solo = solo;
-        b->full = trial == 2 * kMaxCluster;
+        b->split = split;
+        b->full = full;
         if (b->persistent && persistent_shape(b) != LBC_OK) continue;
         st = upload_descriptors(b);
         if (st != LBC_OK) break;
@@ -716,7 +729,15 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
         float ms = 0;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
         if (e != cudaSuccess) { st = fail(LBC_ECUDA, std::string("autotune: ") + cudaGetErrorString(e)); break; }
-        if (ms < best) { best = ms; best_c = c; best_smem = smem; best_solo = solo; best_full = b->full; best_T = Ts; }
+        if (ms < best) {
+            best = ms;
+            best_c = c;
+            best_smem = smem;
+            best_solo = solo;
+            best_full = full;
+            best_split = split;
+            best_T = Ts;
+        }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
@@ -726,6 +747,7 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
         b->smem = keep_smem;
         b->solo = keep_solo;
         b->full = keep_full;
+        b->split = keep_split;
         st = st == LBC_OK ? fail(LBC_EINVAL, "no cluster size could be timed") : st;
     } else {
         for (int i = 0; i < b->n; ++i) b->inst[i].T = best_T[i];
@@ -733,6 +755,7 @@ lbc_status batch_autotune(lbc_batch *b, int trial_steps, int *cluster_out)
         b->smem = best_smem;
         b->solo = best_solo;
         b->full = best_full;
+        b->split = best_split;
     }
     if (b->persistent && st == LBC_OK) st = persistent_shape(b);
     if (b->graph) {
@@ -826,7 +849,7 @@ lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster) { ret
 lbc_status lbc_batch_form(const lbc_batch *b, int *solo)
 {
     if (!b || !solo) return fail(LBC_EINVAL, "NULL argument");
-    *solo = (!b->single && b->solo) ? (b->full ? 2 : 1) : 0;
+    *solo = (!b->single && b->solo) ? (b->split ? 3 : 1) + (b->full ? 1 : 0) : 0;
     return LBC_OK;
 }
 
@@ -836,19 +859,21 @@ lbc_status lbc_batch_set_form(lbc_batch *b, int solo)
     if (b->single) return fail(LBC_EINVAL, "a single-instance batch has the cluster form only");
     std::vector<DevTables> Ts(b->n);
     for (int i = 0; i < b->n; ++i) Ts[i] = b->inst[i].T;
-    if (solo < 0 || solo > 2) return fail(LBC_EINVAL, "form must be 0, 1 or 2");
-    bool f = solo == 2;
+    if (solo < 0 || solo > 4) return fail(LBC_EINVAL, "form must be in [0, 4]");
+    const bool full = solo == 2 || solo == 4;
+    bool f = full;
     int c = 0;
     size_t smem = 0;
-    lbc_status st = solo == 2 ? choose_full_chunk_shape(b->fp32, Ts, c, smem)
-                              : choose_batch_shape(b->fp32, Ts, b->cluster, solo ? 1 : 0, f, c, smem);
+    lbc_status st = full ? choose_full_chunk_shape(b->fp32, Ts, c, smem)
+                         : choose_batch_shape(b->fp32, Ts, b->cluster, solo ? 1 : 0, f, c, smem);
     if (st != LBC_OK) return st;
     LBC_CUDA_TRY(cudaStreamSynchronize(b->stream));   // no launch of the old form in flight
     for (int i = 0; i < b->n; ++i) b->inst[i].T = Ts[i];
     b->cluster = c;
     b->smem = smem;
     b->solo = f;
-    b->full = solo == 2;
+    b->full = full;
+    b->split = solo >= 3;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -890,11 +915,11 @@ lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms)
             if (e == cudaSuccess)
                 e = b->fp32 ? (b->single ? launch_stage<float>(b->inst[0], b->smem, stage, (int)k, b->stream)
                                          : launch_stage_batch<float>(b->d_inst, b->d_work, b->nwork, b->cluster,
-                                                                     b->smem, stage, (int)k, b->ext, b->solo,
+                                                                     b->smem, stage, (int)k, b->ext, kernel_form(b), b->node_smem,
                                                                      b->stream))
                             : (b->single ? launch_stage<double>(b->inst[0], b->smem, stage, (int)k, b->stream)
                                          : launch_stage_batch<double>(b->d_inst, b->d_work, b->nwork, b->cluster,
-                                                                      b->smem, stage, (int)k, b->ext, b->solo,
+                                                                      b->smem, stage, (int)k, b->ext, kernel_form(b), b->node_smem,
                                                                       b->stream));
             if (e == cudaSuccess) e = cudaEventRecord(ev[j + 1], b->stream);
         }

@@ -23,6 +23,9 @@ constexpr int kEqM = 16;           // per-node stage data: n ux uy T qx qy 1/tau
                                    // Pxx Pyy Pzz Pxy dt_s, 1 pad (64 B per FP32 node: 16-byte-aligned bulk copies)
 constexpr int kMassHdr = 32;       // doubles before the per-node mass deviations in DevState::mass
 constexpr int kMaxVChunk = 256;    // velocities per CTA at most (per-velocity data is staged in smem)
+// Forms of the batched stage launch (how a tile's chunk CTAs combine their moment partials).
+constexpr int kFormCluster = 0, kFormSolo = 1, kFormSplit = 2;
+constexpr int kNodePart = 16;      // split form: nodes per CTA of the node-step launch (two CTAs per tile)
 constexpr int kMaxCluster = 16;    // chunk CTAs of a tile form one thread-block cluster (non-portable size 16)
 constexpr int kMaxV = kMaxCluster * kMaxVChunk;   // largest velocity set 2 Qx Qy
 constexpr int kMaxTable = 256;     // entries of a viscosity table
@@ -258,13 +261,14 @@ cudaError_t configure_kernels();   // per-device kernel attributes; call before 
 template <typename R>
 cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStream_t st);
 // One RK stage of every work item: grid (nwork, cluster), cluster dims (1, cluster, 1) in the
-// cluster form, no clusters in the solo form (solo: the tile's last chunk CTA builds the next
-// stage's data of all its nodes; DevState::tcnt counts them in);
+// cluster form (kFormCluster), no clusters in the solo form (kFormSolo: the tile's last chunk CTA
+// builds the next stage's data of all its nodes; DevState::tcnt counts them in) and the split form
+// (kFormSplit: a second launch, node_smem bytes of shared memory per CTA, builds it);
 // work[i] = (instance, tile) with descriptors in device memory, instance < 0 for an empty slot.
 // ext: some instance uses the half channel or local steps (the kernel form that has them).
 template <typename R>
 cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, int cluster, size_t smem, int stage,
-                               int rel, bool ext, bool solo, cudaStream_t st);
+                               int rel, bool ext, int form, size_t node_smem, cudaStream_t st);
 // Persistent form: nsteps RK-3 steps of every work item in one cooperative launch of nclusters
 // clusters (grid (nclusters, cluster)); cnt: kPersistHdr + nwork + n device counters (zeroed here);
 // the steps' residual slots are zeroed first. Work items of an instance must be its tiles in order.

@@ -820,16 +820,19 @@ __device__ __forceinline__ void kahan1(float &s, float &c, float x)
 // blockIdx.y (body of both stage kernels below). kExt compiles in the half
 // channel's symmetry plane and the local steps with mass renormalisation
 // (instances without them give the same results in either form). The chunk
-// CTAs of a tile combine their moment partials in one of two ways:
-//  - cluster form (kSolo false): the tile's chunk CTAs form a thread-block
-//    cluster and exchange partials through distributed shared memory; each
-//    builds the next-stage data of nodes rank, rank + nchunk, ...;
-//  - solo form (kSolo true): plain CTAs write their partials to global memory
+// CTAs of a tile combine their moment partials in one of three ways (kForm):
+//  - cluster form: the tile's chunk CTAs form a thread-block cluster and
+//    exchange partials through distributed shared memory; each builds the
+//    next-stage data of nodes rank, rank + nchunk, ...;
+//  - solo form: plain CTAs write their partials to global memory
 //    (DevState::part) and count themselves in (DevState::tcnt); the tile's
 //    last CTA to finish sums the partials over the chunks, in chunk order, and
 //    builds the next-stage data of all the tile's nodes while the others have
-//    already left. Same arithmetic in the same order: identical results.
-template <typename R, bool kExt, int kStage, bool kSolo>
+//    already left;
+//  - split form: plain CTAs write their partials and leave; a second launch
+//    (node_step_kernel) builds every tile's next-stage data with the whole GPU.
+// Same arithmetic in the same order in every form: identical results.
+template <typename R, bool kExt, int kStage, int kForm>
 __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, bool persist = false)
 {
     constexpr int stage = kStage;   // RK stage 0, 1, 2: a compile-time constant in every form
@@ -950,11 +953,12 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
         __syncthreads();
         return s_last != 0;
     };
-    if constexpr (!kSolo) cluster_arrive_relaxed();   // this CTA runs: the others may write into its shared memory after their wait
+    constexpr bool kSolo = kForm == kFormSolo, kSplit = kForm == kFormSplit;
+    if constexpr (kForm == kFormCluster) cluster_arrive_relaxed();   // this CTA runs: the others may write into its shared memory after their wait
     if (bad) {   // range-checked build: give up before any copy, taking part in the cluster barriers
         if constexpr (kSolo) {
             solo_count_in();
-        } else {
+        } else if constexpr (!kSplit) {
             cluster_wait();
             cluster_arrive();
             cluster_wait();
@@ -1494,7 +1498,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     const int nn = (kTile - rank + nch - 1) / nch;          // nodes rank, rank + nch, ... of the tile
     const int nnmax = (kTile + nch - 1) / nch;
     unsigned char *scr = smem + L.pipe;                     // EqScratch
-    if (!timed_out && tid < (kSolo ? kTile : nn)) {   // the node step's per-node data, towards L1
+    if (!kSplit && !timed_out && tid < (kSolo ? kTile : nn)) {   // the node step's per-node data, towards L1
         const int sp = kSolo ? c0 + tid : c0 + rank + tid * nch;
         if (sp < T.Nx) {
             prefetch_l1(Tabs<R>::ijd(T) + sp);
@@ -1520,7 +1524,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
         __syncthreads();
         if constexpr (kSolo) {
             solo_count_in();   // keeps the tile's count consistent for the next launch
-        } else {
+        } else if constexpr (!kSplit) {
             cluster_wait();
             cluster_arrive();
             cluster_wait();
@@ -1530,7 +1534,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     }
 
     // ---- (4) the chunk's raw moment partials, sent to the CTAs that own the nodes ----
-    if (tid == 0) {   // the equilibrium tables, into the pipeline region that the loop no longer reads
+    if (!kSplit && tid == 0) {   // the equilibrium tables, into the pipeline region that the loop no longer reads
         mbar_expect_tx(bar_tab, tab_bytes);
         bulk_load(scr + E.tab, Tabs<R>::eqtab(T), tab_bytes, bar_tab);
     }
@@ -1562,7 +1566,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     __syncthreads();
     // local steps: the mass deviations of f^{n+1} (buffer 0) for the next step's parity
     double *dm = renorm ? S.mass + kMassHdr + (size_t)((step + 1) & 1) * T.Nxp : nullptr;
-    if constexpr (kSolo) {
+    if constexpr (kSolo || kSplit) {
         // ---- (4') the chunk's partials (summed over warps) to global memory [nchunk][kNumRaw][Nxp] ----
         R *part = static_cast<R *>(S.part);
         for (int idx = tid; idx < kTile * kNumRaw; idx += kThreads) {
@@ -1574,6 +1578,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
                     part[((size_t)chunk * kNumRaw + m) * T.Nxp + c0 + c] = t.value();
             }
         }
+        if constexpr (kSplit) return;   // the node step is a launch of its own
         const bool last = solo_count_in();
         if (!last) {   // the table copy into this CTA's shared memory must land before it leaves
             if (tid == 0) mbar_wait(bar_tab, 0);
@@ -1645,20 +1650,77 @@ template <typename R, bool kExt, int kStage>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2)
 stage_kernel(const __grid_constant__ Inst I, int rel)
 {
-    stage_body<R, kExt, kStage, false>(I, blockIdx.x, rel);
+    stage_body<R, kExt, kStage, kFormCluster>(I, blockIdx.x, rel);
 }
 
 // Batch: descriptors in device memory, one cluster per work item (instance, tile).
 // Three CTAs per SM in FP32: the descriptor fields live in registers here (in the
 // single-instance kernel they are constant-bank operands), and measured on GB300
 // the unspilled 3-CTA form is faster than a spilling 4-CTA form.
-template <typename R, bool kExt, int kStage, bool kSolo>
+template <typename R, bool kExt, int kStage, int kForm>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
 stage_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int rel)
 {
     const int2 wk = work[blockIdx.x];
     if (wk.x < 0) return;   // empty work slot: the whole cluster (or every chunk CTA) leaves
-    stage_body<R, kExt, kStage, kSolo>(insts[wk.x], wk.y, rel);
+    stage_body<R, kExt, kStage, kForm>(insts[wk.x], wk.y, rel);
+}
+
+// Split form, the RK stage's second launch: the next-stage data of nodes
+// blockIdx.y * kNodePart .. of a work item's tile, from the chunk partials the stage
+// launch left in DevState::part (summed over the chunks in chunk order, as the other
+// forms sum them) and the input stage's mean velocities (the shift of those sums),
+// by the node step of the other forms. Every tile's node step runs at once, spread
+// over the whole GPU, instead of in the stage launch's last CTAs.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+node_step_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ work, int rel, int stage)
+{
+    const int2 wk = work[blockIdx.x];
+    if (wk.x < 0) return;   // empty work slot
+    const Inst &I = insts[wk.x];
+    const DevTables &T = I.T;
+    const DevState &S = I.S;
+    const Ctl *ctl = S.ctl;
+    const long long step = ctl->base + rel;
+    // early stop: the stage launch's decision, taken again from the same data
+    const double stop_eps = ctl->stop_eps;
+    if (stop_eps > 0.0) {
+        if (__ldcg(&ctl->stopped)) return;
+        if (step - 1 >= ctl->check_from) {
+            const double rprev = __longlong_as_double((long long)__ldcg(&S.resid[(step - 1) % kResidRing]));
+            if (rprev < stop_eps) return;
+        }
+    }
+    extern __shared__ __align__(128) unsigned char smem_node[];
+    unsigned char *scr = smem_node + ((128 - (smem_addr(smem_node) & 127)) & 127);
+    const int tid = threadIdx.x, tile = wk.y, c0 = tile * kTile, cfirst = blockIdx.y * kNodePart;
+    const int nn = min(kNodePart, kTile - cfirst), nch = T.nchunk, in = stage, out = (stage + 1) % 3;
+    const EqScratch<R> E(T.K, T.Nxe, T.Nye, T.Qx, T.Qy, T.tab_n, kTile);
+    const int tlen = EqTab(T.Nxe, T.Nye, T.K, T.Qx, T.Qy, T.tab_n).len;
+    R *tab = reinterpret_cast<R *>(scr + E.tab);
+    for (int k = tid; k < tlen; k += kThreads) tab[k] = Tabs<R>::eqtab(T)[k];
+    R *raw = reinterpret_cast<R *>(scr + E.raw);
+    R *shf = reinterpret_cast<R *>(scr + E.shf);
+    const R *part = static_cast<const R *>(S.part);
+    for (int idx = tid; idx < nn * kNumRaw; idx += kThreads) {
+        const int i = idx / kNumRaw, m = idx - i * kNumRaw, s = c0 + cfirst + i;
+        CSum<R> t;
+        if (s < T.Nx)
+            for (int ch = 0; ch < nch; ++ch) t.add(part[((size_t)ch * kNumRaw + m) * T.Nxp + s]);
+        raw[idx] = t.value();
+    }
+    if (tid < kLanes) {   // lane = node of the tile: the input stage's mean velocity
+        const int s = c0 + tid;
+        const bool live = tid < kTile && s < T.Nx;
+        const R *e = static_cast<const R *>(S.eqm[in]) + (size_t)(live ? s : 0) * kEqM;
+        shf[tid] = live ? e[1] : R(0);
+        shf[kLanes + tid] = live ? e[2] : R(0);
+    }
+    __syncthreads();
+    // local steps: the mass deviations of f^{n+1} (buffer 0) for the next step's parity
+    double *dm = T.lts && stage == 2 ? S.mass + kMassHdr + (size_t)((step + 1) & 1) * T.Nxp : nullptr;
+    node_equilibrium<R>(T, S, out, tile, cfirst, 1, nn, kTile, scr, dm, nullptr);
 }
 
 // ---- persistent form: one launch for a group of steps of every work item ----
@@ -1774,9 +1836,9 @@ persistent_stage_kernel(const Inst *__restrict__ insts, const int2 *__restrict__
         const int2 wk = work[w];
         if (wk.x >= 0) {
             const Inst &I = insts[wk.x];
-            if (stage == 0) stage_body<R, kExt, 0, false>(I, wk.y, rel, true);
-            else if (stage == 1) stage_body<R, kExt, 1, false>(I, wk.y, rel, true);
-            else stage_body<R, kExt, 2, false>(I, wk.y, rel, true);
+            if (stage == 0) stage_body<R, kExt, 0, kFormCluster>(I, wk.y, rel, true);
+            else if (stage == 1) stage_body<R, kExt, 1, kFormCluster>(I, wk.y, rel, true);
+            else stage_body<R, kExt, 2, kFormCluster>(I, wk.y, rel, true);
         }
         // completion: this CTA's writes fenced, then counted (the tile's stage item is done when
         // every CTA of its cluster has counted)
@@ -1949,16 +2011,19 @@ cudaError_t configure_kernels()
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const void *stage_fns[18] = {
+    const void *stage_fns[24] = {
         (const void *)stage_kernel<R, false, 0>,              (const void *)stage_kernel<R, false, 1>,
         (const void *)stage_kernel<R, false, 2>,              (const void *)stage_kernel<R, true, 0>,
         (const void *)stage_kernel<R, true, 1>,               (const void *)stage_kernel<R, true, 2>,
-        (const void *)stage_batch_kernel<R, false, 0, false>, (const void *)stage_batch_kernel<R, false, 1, false>,
-        (const void *)stage_batch_kernel<R, false, 2, false>, (const void *)stage_batch_kernel<R, true, 0, false>,
-        (const void *)stage_batch_kernel<R, true, 1, false>,  (const void *)stage_batch_kernel<R, true, 2, false>,
-        (const void *)stage_batch_kernel<R, false, 0, true>,  (const void *)stage_batch_kernel<R, false, 1, true>,
-        (const void *)stage_batch_kernel<R, false, 2, true>,  (const void *)stage_batch_kernel<R, true, 0, true>,
-        (const void *)stage_batch_kernel<R, true, 1, true>,   (const void *)stage_batch_kernel<R, true, 2, true>};
+        (const void *)stage_batch_kernel<R, false, 0, kFormCluster>, (const void *)stage_batch_kernel<R, false, 1, kFormCluster>,
+        (const void *)stage_batch_kernel<R, false, 2, kFormCluster>, (const void *)stage_batch_kernel<R, true, 0, kFormCluster>,
+        (const void *)stage_batch_kernel<R, true, 1, kFormCluster>,  (const void *)stage_batch_kernel<R, true, 2, kFormCluster>,
+        (const void *)stage_batch_kernel<R, false, 0, kFormSolo>,  (const void *)stage_batch_kernel<R, false, 1, kFormSolo>,
+        (const void *)stage_batch_kernel<R, false, 2, kFormSolo>,  (const void *)stage_batch_kernel<R, true, 0, kFormSolo>,
+        (const void *)stage_batch_kernel<R, true, 1, kFormSolo>,   (const void *)stage_batch_kernel<R, true, 2, kFormSolo>,
+        (const void *)stage_batch_kernel<R, false, 0, kFormSplit>, (const void *)stage_batch_kernel<R, false, 1, kFormSplit>,
+        (const void *)stage_batch_kernel<R, false, 2, kFormSplit>, (const void *)stage_batch_kernel<R, true, 0, kFormSplit>,
+        (const void *)stage_batch_kernel<R, true, 1, kFormSplit>,  (const void *)stage_batch_kernel<R, true, 2, kFormSplit>};
     // dynamic shared memory up to the opt-in limit less the kernel's static shared memory
     auto allow = [&](const void *fn) {
         cudaFuncAttributes fa = {};
@@ -1973,6 +2038,8 @@ cudaError_t configure_kernels()
     for (const void *fn : persist_fns) allow(fn);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tile_equilibrium_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(node_step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     return e;
 }
 
@@ -2018,11 +2085,12 @@ cudaError_t launch_stage(const Inst &I, size_t smem, int stage, int rel, cudaStr
     }
 }
 
-// Work item (instance, tile) x its `cluster` chunk CTAs (grid dimension y): one thread-block
-// cluster per work item in the cluster form, independent CTAs in the solo form.
+// Work item (instance, tile) x its `cluster` chunk CTAs: grid (nwork, cluster), with one thread-block
+// cluster per work item in the cluster form and independent CTAs in the solo and split forms; the
+// split form then launches the node step, grid (nwork, ceil(kTile / kNodePart)), node_smem bytes.
 template <typename R>
 cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, int cluster, size_t smem, int stage,
-                               int rel, bool ext, bool solo, cudaStream_t st)
+                               int rel, bool ext, int form, size_t node_smem, cudaStream_t st)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nwork, (unsigned)cluster, 1);
@@ -2035,22 +2103,33 @@ cudaError_t launch_stage_batch(const Inst *insts, const int2 *work, int nwork, i
     at[0].val.clusterDim.y = (unsigned)cluster;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = solo ? 0 : 1;
-    switch (stage + 3 * ext + 6 * solo) {
-    case 0: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 0, false>, insts, work, rel);
-    case 1: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 1, false>, insts, work, rel);
-    case 2: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 2, false>, insts, work, rel);
-    case 3: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 0, false>, insts, work, rel);
-    case 4: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 1, false>, insts, work, rel);
-    case 5: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 2, false>, insts, work, rel);
-    case 6: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 0, true>, insts, work, rel);
-    case 7: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 1, true>, insts, work, rel);
-    case 8: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 2, true>, insts, work, rel);
-    case 9: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 0, true>, insts, work, rel);
-    case 10: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 1, true>, insts, work, rel);
-    case 11: return cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 2, true>, insts, work, rel);
-    default: return cudaErrorInvalidValue;
+    cfg.numAttrs = form == kFormCluster ? 1 : 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (stage + 3 * ext + 6 * form) {
+    case 0: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 0, kFormCluster>, insts, work, rel); break;
+    case 1: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 1, kFormCluster>, insts, work, rel); break;
+    case 2: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 2, kFormCluster>, insts, work, rel); break;
+    case 3: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 0, kFormCluster>, insts, work, rel); break;
+    case 4: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 1, kFormCluster>, insts, work, rel); break;
+    case 5: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 2, kFormCluster>, insts, work, rel); break;
+    case 6: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 0, kFormSolo>, insts, work, rel); break;
+    case 7: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 1, kFormSolo>, insts, work, rel); break;
+    case 8: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 2, kFormSolo>, insts, work, rel); break;
+    case 9: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 0, kFormSolo>, insts, work, rel); break;
+    case 10: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 1, kFormSolo>, insts, work, rel); break;
+    case 11: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 2, kFormSolo>, insts, work, rel); break;
+    case 12: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 0, kFormSplit>, insts, work, rel); break;
+    case 13: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 1, kFormSplit>, insts, work, rel); break;
+    case 14: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, false, 2, kFormSplit>, insts, work, rel); break;
+    case 15: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 0, kFormSplit>, insts, work, rel); break;
+    case 16: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 1, kFormSplit>, insts, work, rel); break;
+    case 17: e = cudaLaunchKernelEx(&cfg, stage_batch_kernel<R, true, 2, kFormSplit>, insts, work, rel); break;
+    default: break;
     }
+    if (e != cudaSuccess || form != kFormSplit) return e;
+    node_step_kernel<R><<<dim3((unsigned)nwork, (unsigned)((kTile + kNodePart - 1) / kNodePart), 1), kThreads, node_smem,
+                          st>>>(insts, work, rel, stage);
+    return cudaGetLastError();
 }
 
 // Persistent form: nsteps RK-3 steps of every work item in one cooperative launch of
@@ -2111,7 +2190,7 @@ cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, bool sol
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<R, false, 0, true>, kThreads,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_batch_kernel<R, false, 0, kFormSolo>, kThreads,
                                                               smem);
         if (e == cudaSuccess) *nclusters = per_sm * nsm / cluster;
         return e;
@@ -2128,7 +2207,7 @@ cudaError_t stage_active_clusters(size_t smem, int cluster, bool batch, bool sol
     cfg.attrs = at;
     cfg.numAttrs = 1;
     // both forms of a kernel have the same launch bounds and shared memory: the plain one stands for both
-    return batch ? cudaOccupancyMaxActiveClusters(nclusters, stage_batch_kernel<R, false, 0, false>, &cfg)
+    return batch ? cudaOccupancyMaxActiveClusters(nclusters, stage_batch_kernel<R, false, 0, kFormCluster>, &cfg)
                  : cudaOccupancyMaxActiveClusters(nclusters, stage_kernel<R, false, 0>, &cfg);
 }
 
@@ -2216,7 +2295,8 @@ cudaError_t launch_last_residuals(const Inst *insts, const int *slots, int n, do
     template size_t stage_smem_bytes<R>(int, int, int, int, int, int, int, int);                                     \
     template cudaError_t configure_kernels<R>();                                                                \
     template cudaError_t launch_stage<R>(const Inst &, size_t, int, int, cudaStream_t);                          \
-    template cudaError_t launch_stage_batch<R>(const Inst *, const int2 *, int, int, size_t, int, int, bool, bool, \
+    template cudaError_t launch_stage_batch<R>(const Inst *, const int2 *, int, int, size_t, int, int, bool, int,  \
+                                               size_t, \
                                                cudaStream_t);                                                    \
     template cudaError_t launch_tile_equilibrium<R>(const DevTables &, const DevState &, int, cudaStream_t);     \
     template cudaError_t launch_moments_partial<R>(const DevTables &, const DevState &, int, cudaStream_t);      \

@@ -111,7 +111,7 @@ cudaError_t pool_steps(lbc_pool *P, long nsteps, size_t smem)
     for (long k = 0; k < nsteps; ++k)
         for (int stage = 0; stage < 3; ++stage) {
             cudaError_t e = launch_stage_batch<R>(P->d_inst, P->d_work, P->nwork, P->cluster, smem, stage, (int)k,
-                                                  P->ext, false, P->stream);
+                                                  P->ext, kFormCluster, 0, P->stream);
             if (e != cudaSuccess) return e;
         }
     return launch_ctl_bump(P->d_ctl, P->cap, nsteps, P->stream);

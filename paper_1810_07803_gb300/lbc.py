@@ -354,9 +354,11 @@ class Batch:
         _check(lib().lbc_batch_autotune(self._h, int(trial_steps), C.byref(c)))
         return c.value
 
+    FORMS = ("cluster", "solo", "solo, 256-row chunks", "split", "split, 256-row chunks")
+
     @property
     def form(self) -> int:
-        """0 cluster form, 1 solo form, 2 solo form with 256-row chunks (lbc_batch_form)."""
+        """Kernel form of the per-stage launches (lbc_batch_form): an index into FORMS."""
         f = C.c_int()
         _check(lib().lbc_batch_form(self._h, C.byref(f)))
         return f.value
@@ -367,8 +369,8 @@ class Batch:
         return self.form != 0
 
     def set_form(self, solo):
-        """Forces the cluster (False / 0), solo (True / 1) or full-chunk solo (2) form
-        (lbc_batch_set_form)."""
+        """Forces a kernel form (lbc_batch_set_form): an index into FORMS, or a bool
+        (False: cluster, True: solo)."""
         _check(lib().lbc_batch_set_form(self._h, int(solo)))
 
     def set_persistent(self, on: bool = True):

@@ -237,17 +237,19 @@ def assert_same_states(a, b, precision):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("cluster", [1, 3, 5])
-def test_solo_form_equals_cluster_form(precision, cluster):
+@pytest.mark.parametrize("form", [1, 3])
+def test_solo_and_split_forms_equal_cluster_form(precision, cluster, form):
     """The solo form (independent chunk CTAs; the tile's last CTA sums the chunk partials from
-    device memory and builds the node data) computes the cluster form's sums in the same order:
-    bit for bit in FP32; the FP64 node arithmetic is compiled separately in each form (the
-    compiler may fuse its multiply-adds differently), compared to 1e-14 relative."""
+    device memory and builds the node data) and the split form (a second launch builds every
+    tile's node data) compute the cluster form's sums in the same order: bit for bit in FP32;
+    the FP64 node arithmetic is compiled separately in each form (the compiler may fuse its
+    multiply-adds differently), compared to 1e-14 relative."""
     for ps in (with_precision(MIX, precision), extended_mix(precision)):
         a = lbc.Batch(ps, cluster=cluster)
         a.set_form(False)
         b = lbc.Batch(ps, cluster=cluster)
-        b.set_form(True)
-        assert not a.solo and b.solo
+        b.set_form(form)
+        assert not a.solo and b.form == form
         for n in (1, 2, 64, 5):   # eager launches and a captured group of 64 steps
             a.step(n)
             b.step(n)
@@ -256,12 +258,13 @@ def test_solo_form_equals_cluster_form(precision, cluster):
         b.close()
 
 
-def test_solo_form_run_to_steady_matches_cluster_form():
+@pytest.mark.parametrize("form", [1, 3])
+def test_solo_and_split_forms_run_to_steady_match_cluster_form(form):
     ps = [dict(workloads.c1(), delta=d) for d in (0.5, 3.0)] + with_precision(MIX[:2], "fp64")
     a = lbc.Batch(ps, cluster=2)
     a.set_form(False)
     b = lbc.Batch(ps, cluster=2)
-    b.set_form(True)
+    b.set_form(form)
     ka, ra = a.run_to_steady(1e-9, 20000, raise_notconv=False)
     kb, rb = b.run_to_steady(1e-9, 20000, raise_notconv=False)
     assert list(ka) == list(kb)
@@ -271,26 +274,28 @@ def test_solo_form_run_to_steady_matches_cluster_form():
     b.close()
 
 
-def test_solo_form_at_the_benchmark_size():
+def test_forms_at_the_benchmark_size():
     """Four C2 solves (the benchmark's batch, which fills the device: the default is the solo
-    form) from a perturbed state, three steps in each form: bit for bit."""
+    form) from a perturbed state, three steps in the solo, split and cluster forms: bit for bit."""
     ps = [workloads.c2(d, precision="fp32") for d in workloads.C2_DELTAS]
     a = lbc.Batch(ps, cluster=3)
     assert a.solo
-    b = lbc.Batch(ps, cluster=3)
-    b.set_form(False)
     states = [workloads.perturbed_state(a.V[i], a.Nx[i], a.get_state(i), seed=7 + i) for i in range(a.n)]
     a.set_states(states)
-    b.set_states(states)
     a.step(3)
-    b.step(3)
-    assert_same_states(a, b, "fp32")
+    for form in (0, 3):
+        b = lbc.Batch(ps, cluster=3)
+        b.set_form(form)
+        b.set_states(states)
+        b.step(3)
+        assert_same_states(a, b, "fp32")
+        b.close()
     a.close()
-    b.close()
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_full_chunk_form_matches_oracle(precision, tol):
+@pytest.mark.parametrize("form", [2, 4])
+def test_full_chunk_forms_match_oracle(precision, tol, form):
     """The solo form with 256-row chunks (form 2: each instance's last chunk shorter, empty
     chunk CTAs where an instance has fewer chunks than the batch): every instance against the
     oracle, including one whose velocity set spans two chunks (320 rows: 256 + 64)."""
@@ -298,8 +303,8 @@ def test_full_chunk_form_matches_oracle(precision, tol):
         dict(Nx=80, Qx=16, Qy=10, stretch_A=0.9, delta=1.5, u_left=-0.2, u_right=0.1, T_left=0.9, T_right=1.2,
              precision=precision)]
     b = lbc.Batch(ps)
-    b.set_form(2)
-    assert b.form == 2 and b.shape()[0] == 2
+    b.set_form(form)
+    assert b.form == form and b.shape()[0] == 2
     b.step(12)
     for i, p in enumerate(ps):
         o = Oracle(p)

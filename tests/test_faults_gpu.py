@@ -148,12 +148,14 @@ def test_injected_admission_refusal_queues(monkeypatch):
     pool.close()
 
 
-def test_bounded_wait_in_the_solo_form(monkeypatch):
+@pytest.mark.parametrize("form", [1, 3])
+def test_bounded_wait_in_the_solo_and_split_forms(monkeypatch, form):
     """A timed-out stage in the solo form still counts its CTAs in, so the tiles' counts stay
-    consistent: after a state is installed the batch continues bit for bit."""
+    consistent; in the split form the node-step launch runs on whatever the stage left. Either
+    way, after a state is installed the batch continues bit for bit."""
     ps = [dict(SMALL, delta=d, precision="fp32") for d in (0.5, 2.0)]
     b = lbc.Batch(ps, cluster=2)
-    b.set_form(True)
+    b.set_form(form)
     rest = [b.get_state(i) for i in range(len(ps))]
     monkeypatch.setenv("LBC_FAULT", "wait:16")
     with pytest.raises(lbc.LbcError) as e:
@@ -163,7 +165,7 @@ def test_bounded_wait_in_the_solo_form(monkeypatch):
     b.set_states(rest)
     b.step(3)
     ref = lbc.Batch(ps, cluster=2)
-    ref.set_form(True)
+    ref.set_form(form)
     ref.step(3)
     for i in range(len(ps)):
         assert np.array_equal(b.get_state(i), ref.get_state(i))
