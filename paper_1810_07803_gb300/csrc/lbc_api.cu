@@ -915,12 +915,12 @@ lbc_status lbc_batch_step_timed(lbc_batch *b, long nsteps, double *stage_ms)
             if (e == cudaSuccess)
                 e = b->fp32 ? (b->single ? launch_stage<float>(b->inst[0], b->smem, stage, (int)k, b->stream)
                                          : launch_stage_batch<float>(b->d_inst, b->d_work, b->nwork, b->cluster,
-                                                                     b->smem, stage, (int)k, b->ext, kernel_form(b), b->node_smem,
-                                                                     b->stream))
+                                                                     b->smem, stage, (int)k, b->ext, kernel_form(b),
+                                                                     b->node_smem, b->stream))
                             : (b->single ? launch_stage<double>(b->inst[0], b->smem, stage, (int)k, b->stream)
                                          : launch_stage_batch<double>(b->d_inst, b->d_work, b->nwork, b->cluster,
-                                                                      b->smem, stage, (int)k, b->ext, kernel_form(b), b->node_smem,
-                                                                      b->stream));
+                                                                      b->smem, stage, (int)k, b->ext, kernel_form(b),
+                                                                      b->node_smem, b->stream));
             if (e == cudaSuccess) e = cudaEventRecord(ev[j + 1], b->stream);
         }
     if (e == cudaSuccess) e = launch_ctl_bump(b->d_ctl, b->n, nsteps, b->stream);
