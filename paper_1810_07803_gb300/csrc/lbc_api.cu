@@ -367,8 +367,9 @@ lbc_status batch_create(const lbc_params *params, int n, int cluster_in, void *c
         StateSizes(T, b->fp32).carve(sb + soff[i], S);
         S.ctl = b->d_ctl + i;
         StateMaps &M = b->inst[i].M;
-        for (int k = 0; k < 3 && st == LBC_OK; ++k) st = encode_state_map(&M.in[k], S.F[k], b->fp32, T.V, T.Nxp, kRowLen);
-        if (st == LBC_OK) st = encode_state_map(&M.f0, S.F[0], b->fp32, T.V, T.Nxp, kF0Len);
+        for (int k = 0; k < 3 && st == LBC_OK; ++k) st = encode_state_map(&M.in[k], S.F[k], b->fp32, T.V, T.Nxp, kRowLen,
+                                                          slot_rows(k, b->fp32));
+        if (st == LBC_OK) st = encode_state_map(&M.f0, S.F[0], b->fp32, T.V, T.Nxp, kF0Len, kSubV);
         if (st != LBC_OK) return cleanup(st);
     }
     e = cudaMallocHost(&b->h_ctl, n * sizeof(Ctl));

@@ -18,6 +18,9 @@ constexpr int kF0Len = 36;         // TMA box width of an RK base row (31 nodes,
 constexpr int kWarps = 8;          // warps per CTA
 constexpr int kThreads = kWarps * 32;
 constexpr int kSubV = 32;          // velocity rows per pipeline slot (four per warp)
+constexpr int kSubV0 = 64;         // the first RK stage in FP32, which stages no RK base: eight per warp
+// Rows per pipeline slot of RK stage `stage` (and the TMA box height of state buffer `stage`).
+__host__ __device__ constexpr int slot_rows(int stage, bool fp32) { return stage == 0 && fp32 ? kSubV0 : kSubV; }
 constexpr int kPipe = 2;           // pipeline slots (one computed while the other lands)
 constexpr int kEqM = 16;           // per-node stage data: n ux uy T qx qy 1/tau cS 1/(5T) 1/(J deta)
                                    // Pxx Pyy Pzz Pxy dt_s, 1 pad (64 B per FP32 node: 16-byte-aligned bulk copies)
@@ -243,7 +246,7 @@ const char *last_error();
 // Validates p (defaults already applied) and resolves the expansion orders.
 lbc_status validate(const lbc_params &p, int &Nxe, int &Nye);
 // TMA descriptor of a state buffer viewed as [V rows][2 Nxp columns], box 2 box_nodes x kSubV.
-lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_nodes);
+lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_nodes, int box_rows);
 
 template <typename R>
 size_t stage_smem_bytes(int Qx, int Qy, int N, int Ny, int K, int vchunk, int cluster, int ntab);

@@ -10,7 +10,8 @@
 //  (2) on a tile whose stencil reaches a wall, computes the wall density n_w
 //      from the outgoing WENO-5 wall flux (Eqs. diffuse, diffuse_nw);
 //  (3) streams the chunk's velocity rows through a TMA pipeline (kPipe slots
-//      of kSubV rows, mbarrier completion): WENO-5 faces upwind by sign p_x,
+//      of kSubV rows, kSubV0 in the first FP32 stage; mbarrier completion):
+//      WENO-5 faces upwind by sign p_x,
 //      Shakhov target (Sec. II) with 1/tau of Eq. tau, TVD RK-3 combination,
 //      store, and the new stage's raw moments over the chunk's velocities;
 //  (4) publishes its per-chunk moment partials in shared memory; after a
@@ -782,6 +783,9 @@ struct Layout {
         fin = o;
         f0 = fin + (size_t)kPipe * 2 * kSubV * kRowLen * sizeof(R);
         size_t m = f0 + (size_t)kPipe * 2 * kSubV * kF0Len * sizeof(R) - pipe;
+        // the first stage's wider slots (FP32) cover the RK-base region, which that stage leaves unused
+        const size_t fin0 = (size_t)kPipe * 2 * slot_rows(0, sizeof(R) == 4) * kRowLen * sizeof(R);
+        m = m > fin0 ? m : fin0;
         const size_t eq_bytes = EqScratch<R>(K, N, Ny, Qx, Qy, ntab, node_cap(cluster)).total;
         m = m > eq_bytes ? m : eq_bytes;
         o = al(o + m);
@@ -836,6 +840,7 @@ template <typename R, bool kExt, int kStage, int kForm>
 __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, bool persist = false)
 {
     constexpr int stage = kStage;   // RK stage 0, 1, 2: a compile-time constant in every form
+    constexpr int kSub = slot_rows(kStage, sizeof(R) == 4);   // rows per pipeline slot
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     const DevTables &T = I.T;
     const DevState &S = I.S;
@@ -847,8 +852,8 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     uint64_t *bar_data = bar + kPipe, *bar_tab = bar + kPipe + 1;
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(bar + kPipe + 2);   // [kPipe] warps done with a slot
     int *s_abort = reinterpret_cast<int *>(s_cnt + kPipe);              // a warp gave up waiting
-    R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][kSubV][2 kRowLen]: (phi, chi) per node
-    R *s_f0 = reinterpret_cast<R *>(smem + L.f0);         // [kPipe][kSubV][2 kF0Len]
+    R *s_fin = reinterpret_cast<R *>(smem + L.fin);       // [kPipe][kSub][2 kRowLen]: (phi, chi) per node
+    R *s_f0 = reinterpret_cast<R *>(smem + L.f0);         // [kPipe][kSub][2 kF0Len]
     R *s_g = reinterpret_cast<R *>(smem + L.g);           // [2Qx + Qy][kLanes]
     R *s_eqm = reinterpret_cast<R *>(smem + L.eqm);       // [kTile][kEqM]
     R *s_vrow = reinterpret_cast<R *>(smem + L.vrow);     // [vchunk][kVRow]
@@ -886,10 +891,10 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     // this CTA's velocity rows [vbeg, vend): may be empty for a small instance in a wide cluster
     const int vbeg = min(V, chunk * T.vchunk);
     const int vend = min(V, vbeg + T.vchunk);
-    const int nsub = (vend - vbeg + kSubV - 1) / kSubV;
+    const int nsub = (vend - vbeg + kSub - 1) / kSub;
     const int nloc = min(kTile, T.Nx - c0);   // nodes of this tile inside the channel
     const uint32_t tx_bytes =
-        (uint32_t)((2 * kSubV * kRowLen + (stage > 0 ? 2 * kSubV * kF0Len : 0)) * sizeof(R));
+        (uint32_t)((2 * kSub * kRowLen + (stage > 0 ? 2 * kSub * kF0Len : 0)) * sizeof(R));
     const CUtensorMap *in_map = &M.in[in];
     // TMA x coordinates must be 16-byte aligned: start the boxes at multiples of 4 nodes
     const int x0 = ((c0 - 3) >> 2) << 2, off = c0 - 3 - x0;     // node s <-> column s - x0
@@ -917,13 +922,13 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     constexpr bool bad = false;
 #endif
 
-    // rows v0 .. v0 + kSubV - 1 of the stage input (nodes x0 .. x0 + kRowLen - 1) and of the
+    // rows v0 .. v0 + kSub - 1 of the stage input (nodes x0 .. x0 + kRowLen - 1) and of the
     // RK base (nodes xf ..), both fields; rows past V read as zeros
     auto issue = [&](int sub) {
-        int p = sub % kPipe, v0 = vbeg + sub * kSubV;
+        int p = sub % kPipe, v0 = vbeg + sub * kSub;
         mbar_expect_tx(&bar[p], tx_bytes);
-        tma_load_2d(s_fin + (size_t)p * kSubV * 2 * kRowLen, in_map, 2 * x0, v0, &bar[p]);
-        if (stage > 0) tma_load_2d(s_f0 + (size_t)p * kSubV * 2 * kF0Len, &M.f0, 2 * xf, v0, &bar[p]);
+        tma_load_2d(s_fin + (size_t)p * kSub * 2 * kRowLen, in_map, 2 * x0, v0, &bar[p]);
+        if (stage > 0) tma_load_2d(s_f0 + (size_t)p * kSub * 2 * kF0Len, &M.f0, 2 * xf, v0, &bar[p]);
     };
 
     if (tid == 0) {
@@ -1039,7 +1044,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     constexpr bool kLean = std::is_same<R, float>::value && !kExt;
     const R k1 = cb_of<R>(stage) * (R(1) - dt * nu_c), k2 = cb_of<R>(stage) * dt * nu_c;
     const R k3 = cb_of<R>(stage) * dt * ijd, shA = cS_c * qx_c, shB = cS_c * qy_c;
-    constexpr int NQ = kSubV / kWarps;      // rows per warp and slot: rows warp + kWarps q
+    constexpr int NQ = kSub / kWarps;      // rows per warp and slot: rows warp + kWarps q
     bool my_timeout = false;
 
     // half channel: the ghost nodes -1, -2, -3 of velocity v are nodes 0, 1, 2 of the opposite
@@ -1048,7 +1053,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
     R mg0 = R(0), mg1 = R(0);
     auto mirror_fetch = [&](int sub) {
         if (lane < 3 * NQ && sub < nsub) {
-            const int q = lane / 3, g = lane - 3 * q, v = vbeg + sub * kSubV + warp + kWarps * q;
+            const int q = lane / 3, g = lane - 3 * q, v = vbeg + sub * kSub + warp + kWarps * q;
             const int a = v / T.Qy, j = v - a * T.Qy;
             const int vm = (a < T.Qx ? a + T.Qx : a - T.Qx) * T.Qy + (T.Qy - 1 - j);
             if (v < vend && LBC_CHECK(ctl, vm >= 0 && vm < T.V && g < T.Nxp, CK_MIRROR)) {
@@ -1067,13 +1072,13 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
             my_timeout = true;
             break;
         }
-        R *fin = s_fin + (size_t)p * kSubV * 2 * kRowLen;
-        const R *f0 = s_f0 + (size_t)p * kSubV * 2 * kF0Len;
+        R *fin = s_fin + (size_t)p * kSub * 2 * kRowLen;
+        const R *f0 = s_f0 + (size_t)p * kSub * 2 * kF0Len;
         int kq[NQ];
         bool ok[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            kq[q] = sub * kSubV + warp + kWarps * q;
+            kq[q] = sub * kSub + warp + kWarps * q;
             ok[q] = vbeg + kq[q] < vend;
             if (!ok[q]) kq[q] = vend - vbeg - 1;   // the chunk's last velocity row; results are discarded
         }
@@ -1146,11 +1151,11 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
         if constexpr (kLean) {
             // plain FP32 form: (phi, chi) as packed pairs. Rows warp + kWarps q of the slot; a
             // row past the chunk computes on the chunk's last row and stores nothing.
-            const int vs = vbeg + sub * kSubV;                  // first row of the slot
+            const int vs = vbeg + sub * kSub;                  // first row of the slot
             const int v0 = vs + warp;                           // this warp's row q = 0
             const float *rowq = fin + (size_t)warp * 2 * kRowLen + 2 * (ck - 3);   // row q = 0, node ck - 3
             const float *b0 = f0 + (size_t)warp * 2 * kF0Len + 2 * (lane + offf);
-            const int vlast = min(vs + kSubV, vend) - 1, vhalf = T.Qx * T.Qy;
+            const int vlast = min(vs + kSub, vend) - 1, vhalf = T.Qx * T.Qy;
             f2 ps[5];
 #pragma unroll
             for (int m = 0; m < 5; ++m) ps[m] = bc2(0.f);
@@ -1251,7 +1256,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
             using Mix = std::integral_constant<int, 0>;
             using Yes = std::true_type;
             using No = std::false_type;
-            const bool full = vs + kSubV <= vend;
+            const bool full = vs + kSub <= vend;
             if (vlast < vhalf) {
                 if (full && !wall) rows(Pos(), Yes(), Yes());
                 else rows(Pos(), No(), No());
@@ -1275,7 +1280,7 @@ __device__ __forceinline__ void stage_body(const Inst &I, int tile, int rel, boo
             // left (nodes ck-3 .. ck+1), the others from the right (nodes ck+2 .. ck-2). A slot
             // whose rows all share a side loads its stencils at fixed offsets.
             f2 fl[NQ], dd[NQ];
-            const int vq0 = vbeg + sub * kSubV, vq1 = min(vq0 + kSubV, vend) - 1;
+            const int vq0 = vbeg + sub * kSub, vq1 = min(vq0 + kSub, vend) - 1;
             const int vhalf = T.Qx * T.Qy;
             const float *rowq = fin + (size_t)warp * 2 * kRowLen + 2 * (ck - 3);   // row warp, node ck - 3
             if (vq1 < vhalf) {

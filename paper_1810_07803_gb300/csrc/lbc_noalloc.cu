@@ -108,8 +108,8 @@ lbc_status run_noalloc(const lbc_params &p, int Nxe, int Nye, double *d_state, l
                                        std::to_string(kScratchBytes));
 
     StateMaps &M = I.M;
-    for (int k = 0; k < 3 && st == LBC_OK; ++k) st = encode_state_map(&M.in[k], S.F[k], fp32, V, T.Nxp, kRowLen);
-    if (st == LBC_OK) st = encode_state_map(&M.f0, S.F[0], fp32, V, T.Nxp, kF0Len);
+    for (int k = 0; k < 3 && st == LBC_OK; ++k) st = encode_state_map(&M.in[k], S.F[k], fp32, V, T.Nxp, kRowLen, slot_rows(k, fp32));
+    if (st == LBC_OK) st = encode_state_map(&M.f0, S.F[0], fp32, V, T.Nxp, kF0Len, kSubV);
     if (st != LBC_OK) return st;
 
 #define NA_TRY(call)                                                                                          \

@@ -240,8 +240,9 @@ lbc_status lbc_pool_add(lbc_pool *P, const lbc_params *params, int *slot_out)
     char *sb = static_cast<char *>(block) + tbytes;
     z.carve(sb, I.S);
     I.S.ctl = P->d_ctl + s;
-    for (int k = 0; k < 3 && st == LBC_OK; ++k) st = encode_state_map(&I.M.in[k], I.S.F[k], P->fp32, I.T.V, I.T.Nxp, kRowLen);
-    if (st == LBC_OK) st = encode_state_map(&I.M.f0, I.S.F[0], P->fp32, I.T.V, I.T.Nxp, kF0Len);
+    for (int k = 0; k < 3 && st == LBC_OK; ++k) st = encode_state_map(&I.M.in[k], I.S.F[k], P->fp32, I.T.V, I.T.Nxp, kRowLen,
+                                                                 slot_rows(k, P->fp32));
+    if (st == LBC_OK) st = encode_state_map(&I.M.f0, I.S.F[0], P->fp32, I.T.V, I.T.Nxp, kF0Len, kSubV);
     if (st != LBC_OK) {
         cudaFreeAsync(block, P->stream);
         return st;

@@ -326,7 +326,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_nodes)
+lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int Nxp, int box_nodes, int box_rows)
 {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -340,7 +340,7 @@ lbc_status encode_state_map(CUtensorMap *map, void *base, bool fp32, int V, int 
     const size_t esz = fp32 ? 4 : 8;
     cuuint64_t dims[2] = {(cuuint64_t)(2 * Nxp), (cuuint64_t)V};
     cuuint64_t strides[1] = {(cuuint64_t)(2 * Nxp) * esz};
-    cuuint32_t box[2] = {(cuuint32_t)(2 * box_nodes), (cuuint32_t)kSubV};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * box_nodes), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
