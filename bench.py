@@ -186,14 +186,15 @@ def cpu_baseline(seconds_target=8.0):
                                                                "rest start to r < 1e-10"}}
 
 
-def steady_leg(n=64, fp64_sample=8, residual=1e-10, fp32_cap=100_000, seed=5):
+def steady_leg(n=64, fp64_sample=8, residual=1e-10, fp32_cap=100_000, stall_window=8192, seed=5):
     """Steady solves/s at equal moment error: n small Couette solves (the serving workload's
     draw) as one batch with the compensated FP32 state, against the plain form, FP64 single
     solves one after the other, on the first fp64_sample of them; both with local pseudo-time
     steps. Each arm's moments are compared with the limit (an FP64 batch of the same solves run
     to r < 1e-12, not timed). These solves contract by ~0.1 % per step, so the FP64 arm needs
     r < 1e-10 to come within 1e-5 of the limit; the FP32 evaluation of the right-hand side keeps
-    the FP32 residual above ~1e-9, so the FP32 arm stops at r < 1e-10 or after fp32_cap steps,
+    the FP32 residual above ~1e-9, so each FP32 solve stops at r < 1e-10, at the stall rule (its
+    residual has set no new low, by 1 %, for stall_window steps) or after fp32_cap steps,
     and its error against the limit is the measure. Completion time of a batched solve = batch
     time x its steps / the most steps (p50/p99 over the n)."""
     import numpy as np
@@ -206,9 +207,10 @@ def steady_leg(n=64, fp64_sample=8, residual=1e-10, fp32_cap=100_000, seed=5):
     limit = [ref.moments(i) for i in range(n)]
     ref.close()
     b = lbc.Batch([dict(r, precision="fp32", compensated=1) for r in reqs], cluster=1)
+    b.set_stall_window(stall_window)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ks, _ = b.run_to_steady(residual, fp32_cap, raise_notconv=False)
+    ks, rs = b.run_to_steady(residual, fp32_cap, raise_notconv=False)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     done = tb * np.asarray(ks, dtype=float) / max(ks)
@@ -228,6 +230,9 @@ def steady_leg(n=64, fp64_sample=8, residual=1e-10, fp32_cap=100_000, seed=5):
             "p50_s": float(np.percentile(done, 50)), "p99_s": float(np.percentile(done, 99)),
             "moment_error_batched_fp32": err32, "moment_error_plain_fp64": err64, "residual": residual,
             "fp32_steps_cap": fp32_cap, "fp32_at_cap": int(sum(k >= fp32_cap for k in ks)),
+            "fp32_stall_window": stall_window,
+            "fp32_stalled": int(sum(k < fp32_cap and r >= residual for k, r in zip(ks, rs))),
+            "fp32_steps_p50_max": [float(np.percentile(ks, 50)), int(max(ks))],
             "reference": "each solve's FP64 steady state to r < 1e-12 (max over moments of the normalised error)",
             "workload": f"{n} small Couette solves (Nx 32-160, Qx, Qy 4-8, delta 0.3-3; seed {seed}), local steps; "
                         f"batched arm: compensated FP32 state; plain FP64 timed on {fp64_sample} of them"}

@@ -58,7 +58,8 @@ typedef enum {
     LBC_ENOTCONV = 4,    /* lbc_run_to_steady hit max_steps */
     LBC_ENONFINITE = 5,  /* NaN/Inf in the state; the solver is poisoned */
     LBC_ETIMEOUT = 6,    /* a bounded device wait gave up */
-    LBC_EBOUNDS = 7      /* range-checked build only: a device index check failed (message names it) */
+    LBC_EBOUNDS = 7,     /* range-checked build only: a device index check failed (message names it) */
+    LBC_ESTALLED = 8     /* run to steady: a residual stopped falling above the threshold (stall window) */
 } lbc_status;
 
 typedef enum { LBC_MU_POWER = 0, LBC_MU_TABLE = 1 } lbc_mu_law;
@@ -171,10 +172,27 @@ lbc_status lbc_step(lbc_solver *s, long nsteps);
  * r < residual. steps_done / final_residual (either may be NULL) receive the
  * number of steps taken by this call and the last step's residual.
  * Errors: LBC_ENOTCONV (max_steps reached; state advanced by max_steps),
- * LBC_ENONFINITE, LBC_ECUDA, LBC_EINVAL.
+ * LBC_ESTALLED (the stall rule below ended the run), LBC_ENONFINITE, LBC_ECUDA,
+ * LBC_EINVAL.
  */
 lbc_status lbc_run_to_steady(lbc_solver *s, double residual, long max_steps,
                              long *steps_done, double *final_residual);
+
+/*
+ * Stall rule of lbc_run_to_steady / lbc_batch_run_to_steady (no counterpart in the
+ * paper, which runs to a fixed residual; off by default). window > 0 steps: the
+ * residual is sampled every 64 steps, and an instance none of whose samples over
+ * its last `window` steps is below 0.99 times its lowest sample before them has
+ * stalled: its residual has stopped setting new lows (an FP32 state's residual
+ * wanders near 1e-9, the rounding noise of its stage inputs). It stops at the
+ * sample, its state and steps_done are those of that sample, and final_residual
+ * is its residual there (>= the threshold). A residual that still contracts sets
+ * new lows however slowly (rate^window < 0.99); one that oscillates with a period
+ * longer than the window, or rises for a whole window, is taken for stalled, so
+ * the window is the caller's bound on such stretches. window = 0: off.
+ * Errors: LBC_EINVAL (NULL handle, window < 0).
+ */
+lbc_status lbc_set_stall_window(lbc_solver *s, long window);
 
 /*
  * Moments of the current state (Sec. II definitions), FP64, per node:
@@ -240,7 +258,9 @@ lbc_status lbc_equilibrium(const lbc_params *params, double ux, double uy, doubl
  *   instance that converged stops while the others go on. steps_done[n] and
  *   final_residual[n] (caller-owned, either may be NULL) receive each
  *   instance's steps taken by this call and its last step's residual.
- *   LBC_ENOTCONV if any instance reached max_steps (the others' results hold).
+ *   LBC_ENOTCONV if any instance reached max_steps (the others' results hold);
+ *   else LBC_ESTALLED if the stall rule (lbc_set_stall_window; per batch:
+ *   lbc_batch_set_stall_window) stopped any instance, the others converged.
  * lbc_batch_moments / get_state / set_state / info: as the single-solver calls,
  *   for instance i in [0, n).
  * lbc_batch_set_states: states[i] (caller-owned host [2][V_i][Nx_i] float64, or
@@ -296,6 +316,8 @@ lbc_status lbc_batch_shape(const lbc_batch *b, int *cluster, int *nwork, size_t 
 lbc_status lbc_batch_autotune(lbc_batch *b, int trial_steps, int *cluster);
 lbc_status lbc_batch_form(const lbc_batch *b, int *solo);
 lbc_status lbc_batch_set_form(lbc_batch *b, int solo);
+/* The stall rule of lbc_set_stall_window for every instance of the batch. */
+lbc_status lbc_batch_set_stall_window(lbc_batch *b, long window);
 /* As lbc_batch_step with eager launches, timing each stage launch with CUDA
  * events on the batch's stream; *stage_ms receives the sum of the 3 nsteps
  * stage-kernel durations (for roofline reports). Synchronises the stream. */

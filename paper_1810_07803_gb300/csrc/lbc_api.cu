@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "lbc_device.h"
+#include "lbc_stall.h"
 
 using namespace lbc;
 
@@ -59,6 +60,7 @@ struct lbc_batch {
     double *h_last = nullptr;     // pinned [n]
     int *h_bad = nullptr;         // pinned
     bool steady_mode = false;     // the device control blocks hold run-to-steady settings
+    long stall_window = 0;        // run-to-steady stall rule (lbc_batch_set_stall_window); 0: off
     bool poisoned = false;        // some instance holds a NaN/Inf
     bool solo = false;            // batch kernel form without clusters: solo (the tile's last CTA builds the
                                   // node data) or, with split, split (a node-step launch builds it)
@@ -412,6 +414,9 @@ lbc_status batch_run_to_steady(lbc_batch *b, double residual, long max_steps, lo
     b->steady_mode = true;
     lbc_status st = upload_ctl(b, 0, n);
     if (st != LBC_OK) return st;
+    const long window = b->stall_window;
+    std::vector<StallTrack> track(window > 0 ? n : 0);
+    std::vector<long> stall_at(n, 0);   // steps done when the instance was found stalled
     long done = 0;
     bool all = false;
     while (done < max_steps && !all) {
@@ -420,29 +425,46 @@ lbc_status batch_run_to_steady(lbc_batch *b, double residual, long max_steps, lo
         if (st != LBC_OK) return st;
         LBC_CUDA_TRY(launch_last_residuals(b->d_inst, nullptr, n, b->d_last, b->stream));
         LBC_CUDA_TRY(cudaMemcpyAsync(b->h_last, b->d_last, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
-        st = read_ctl(b);
+        st = read_ctl(b);   // synchronises: no launch of this call is in flight below
         if (st != LBC_OK) return st;
         done += k;
         all = true;
-        for (int i = 0; i < n; ++i) all = all && b->h_ctl[i].stopped;
+        for (int i = 0; i < n; ++i) {
+            Ctl &c = b->h_ctl[i];
+            if (window > 0 && !c.stopped && !track[i].stalled && !(b->h_last[i] < residual) &&
+                stall_sample(track[i], done, b->h_last[i], window)) {
+                track[i].stalled = true;
+                stall_at[i] = done;
+                c.stop_eps = INFINITY;   // any finite residual is below it: stops at its next step
+                st = upload_ctl(b, i, 1);
+                if (st != LBC_OK) return st;
+            }
+            all = all && (c.stopped || (window > 0 && track[i].stalled));
+        }
     }
-    bool converged = true;
+    int notconv = 0, stalled = 0;
     for (int i = 0; i < n; ++i) {
         const Ctl &c = b->h_ctl[i];
+        const bool stall = window > 0 && track[i].stalled;
         long taken = done;
         bool conv = false;
-        if (c.stopped) {
+        if (stall) {
+            taken = stall_at[i];   // it stops (or stopped) at the first step after the sample
+        } else if (c.stopped) {
             taken = (long)(c.stop_step - start[i]);
             conv = true;
         } else if (done > 0 && b->h_last[i] < residual) {
             conv = true;   // the last step launched fell below the threshold
         }
-        converged = converged && conv;
+        notconv += !conv && !stall;
+        stalled += stall;
         b->ih[i].steps = start[i] + taken;
         if (steps_done) steps_done[i] = taken;
         if (final_residual) final_residual[i] = done > 0 ? b->h_last[i] : INFINITY;
     }
-    if (!converged) return fail(LBC_ENOTCONV, "max_steps reached before the residual threshold");
+    if (notconv) return fail(LBC_ENOTCONV, "max_steps reached before the residual threshold");
+    if (stalled)
+        return fail(LBC_ESTALLED, std::to_string(stalled) + " instance(s) stalled above the residual threshold");
     return LBC_OK;
 }
 
@@ -882,6 +904,13 @@ lbc_status lbc_batch_set_form(lbc_batch *b, int solo)
     return upload_descriptors(b);
 }
 
+lbc_status lbc_batch_set_stall_window(lbc_batch *b, long window)
+{
+    if (!b || window < 0) return fail(LBC_EINVAL, "bad batch or stall window");
+    b->stall_window = window;
+    return LBC_OK;
+}
+
 lbc_status lbc_batch_set_persistent(lbc_batch *b, int on)
 {
     if (!b) return fail(LBC_EINVAL, "NULL batch");
@@ -988,6 +1017,12 @@ lbc_status lbc_run_to_steady(lbc_solver *s, double residual, long max_steps, lon
     NvtxRange nvtx_range("lbc_run_to_steady");
     if (!s) return fail(LBC_EINVAL, "bad solver, residual or max_steps");
     return batch_run_to_steady(s->b, residual, max_steps, steps_done, final_residual);
+}
+
+lbc_status lbc_set_stall_window(lbc_solver *s, long window)
+{
+    if (!s) return fail(LBC_EINVAL, "NULL solver");
+    return lbc_batch_set_stall_window(s->b, window);
 }
 
 lbc_status lbc_moments(lbc_solver *s, double *out, double *x)

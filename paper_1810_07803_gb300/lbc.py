@@ -18,9 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbc_checked.so" if os.environ.get("LBC_CHECKED", "0") not in ("", "0") else "liblbc.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "lbc.h")
 
-OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENONFINITE, ETIMEOUT, EBOUNDS = range(8)
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENONFINITE, ETIMEOUT, EBOUNDS, ESTALLED = range(9)
 STATUS_NAMES = ["LBC_OK", "LBC_EINVAL", "LBC_ENOMEM", "LBC_ECUDA", "LBC_ENOTCONV", "LBC_ENONFINITE", "LBC_ETIMEOUT",
-                "LBC_EBOUNDS"]
+                "LBC_EBOUNDS", "LBC_ESTALLED"]
 FP64, FP32_STATE = 0, 1
 NMOM = 10
 MOMENT_NAMES = ("n", "u_x", "u_y", "T", "P_xx", "P_yy", "P_zz", "P_xy", "q_x", "q_y")
@@ -100,6 +100,7 @@ def lib():
         L.lbc_create.argtypes = [C.POINTER(Params), vp, C.POINTER(vp)]
         L.lbc_step.argtypes = [vp, C.c_long]
         L.lbc_run_to_steady.argtypes = [vp, C.c_double, C.c_long, C.POINTER(C.c_long), dp]
+        L.lbc_set_stall_window.argtypes = [vp, C.c_long]
         L.lbc_moments.argtypes = [vp, dp, dp]
         L.lbc_get_state.argtypes = [vp, dp]
         L.lbc_set_state.argtypes = [vp, dp]
@@ -125,6 +126,7 @@ def lib():
         L.lbc_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         L.lbc_batch_form.argtypes = [vp, C.POINTER(C.c_int)]
         L.lbc_batch_set_form.argtypes = [vp, C.c_int]
+        L.lbc_batch_set_stall_window.argtypes = [vp, C.c_long]
         L.lbc_batch_step_timed.argtypes = [vp, C.c_long, dp]
         L.lbc_batch_set_persistent.argtypes = [vp, C.c_int]
         ip = C.POINTER(C.c_int)
@@ -254,11 +256,17 @@ class Solver:
         _check(lib().lbc_step(self._h, int(nsteps)))
 
     def run_to_steady(self, residual: float, max_steps: int):
-        """Returns (steps taken, last residual); raises LbcError(ENOTCONV) past max_steps."""
+        """Returns (steps taken, last residual); raises LbcError(ENOTCONV) past max_steps and
+        LbcError(ESTALLED) when the stall rule ends the run."""
         done = C.c_long()
         res = C.c_double()
         _check(lib().lbc_run_to_steady(self._h, residual, int(max_steps), C.byref(done), C.byref(res)))
         return done.value, res.value
+
+    def set_stall_window(self, window: int):
+        """Stall rule of run_to_steady (lbc_set_stall_window): stop once the residual has set
+        no new low (by 1 %) for `window` steps; 0 turns it off."""
+        _check(lib().lbc_set_stall_window(self._h, int(window)))
 
     def moments(self):
         out = np.zeros((NMOM, self.Nx))
@@ -335,13 +343,19 @@ class Batch:
         _check(lib().lbc_batch_step(self._h, int(nsteps)))
 
     def run_to_steady(self, residual: float, max_steps: int, raise_notconv: bool = True):
-        """Returns (steps taken, last residual) per instance."""
+        """Returns (steps taken, last residual) per instance. ENOTCONV (max_steps reached) and
+        ESTALLED (the stall rule stopped an instance) raise only with raise_notconv; an
+        instance that stopped above the threshold shows a last residual >= residual."""
         done = (C.c_long * self.n)()
         res = (C.c_double * self.n)()
         st = lib().lbc_batch_run_to_steady(self._h, residual, int(max_steps), done, res)
-        if st != OK and not (st == ENOTCONV and not raise_notconv):
+        if st != OK and not (st in (ENOTCONV, ESTALLED) and not raise_notconv):
             _check(st)
         return list(done), list(res)
+
+    def set_stall_window(self, window: int):
+        """Stall rule of run_to_steady for every instance (lbc_batch_set_stall_window)."""
+        _check(lib().lbc_batch_set_stall_window(self._h, int(window)))
 
     def step_timed(self, nsteps: int = 1) -> float:
         """Steps like step() and returns the summed duration (ms) of the stage launches."""
